@@ -1,0 +1,239 @@
+/*
+ * tdp.h -- C ABI of the B300 timing hot path for path-based timing-driven
+ * global placement ("Timing-Driven Global Placement by Efficient Critical
+ * Path Extraction", arXiv 2503.11674).
+ *
+ * One timing iteration is
+ *   sta_propagate            Section II-B, Eqs. (2)-(4), Eq. (8)
+ *   extract_critical_paths   Section III-B, report_timing_endpoint(n, k)
+ *   attraction_update_pairs  Section III-D, Eq. (w_ij)
+ *   attraction_loss_fwd/bwd  Eq. (9) and the PP sum of Section III-D
+ *
+ * Conventions shared by every entry point:
+ *  - All pointers are plain C pointers.  "_dev" arguments are CUDA device
+ *    pointers on the current device; "_host" / "_out" arguments are host
+ *    pointers.  No PyTorch or C++ type crosses this boundary.
+ *  - Floating-point device arrays ("void*") hold float for a graph built
+ *    with TDP_FP32 and double for TDP_FP64.  Units: um, fF, kOhm, ps.
+ *  - The caller owns every array it passes; the library only reads (or, for
+ *    outputs, writes) them during the call, in stream order.  The library
+ *    owns the graph, the timing arrays, the extracted paths and the pin-pair
+ *    set P with its weights; it frees them in sta_destroy.
+ *  - Work is queued on the CUDA stream given to sta_build.  A call returns
+ *    after queueing, except where a non-NULL host "_out" pointer asks for a
+ *    result, in which case it synchronises that stream first.
+ *  - Every call returns a tdp_status.  Nothing throws or aborts across the
+ *    boundary.  On a non-OK status tdp_last_error() describes the failure.
+ *    Calls made out of order return TDP_ERR_STATE and change nothing.
+ *  - A graph is not thread safe: one host thread at a time per graph.
+ */
+#ifndef TDP_H
+#define TDP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TDP_API __attribute__((visibility("default")))
+#else
+#define TDP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdp_graph tdp_graph;
+
+typedef enum {
+    TDP_OK = 0,
+    TDP_ERR_INVALID = 1,  /* bad argument or malformed netlist                 */
+    TDP_ERR_CYCLE = 2,    /* combinational loop in the netlist                  */
+    TDP_ERR_OOM = 3,      /* device or host allocation failed                   */
+    TDP_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed        */
+    TDP_ERR_STATE = 5     /* call out of order (e.g. extract before propagate)  */
+} tdp_status;
+
+typedef enum { TDP_FP32 = 0, TDP_FP64 = 1 } tdp_precision;
+
+/* cell_type values */
+enum { TDP_CELL_COMB = 0, TDP_CELL_FF = 1, TDP_CELL_PI = 2, TDP_CELL_PO = 3 };
+
+/*
+ * Netlist description (host arrays, read during sta_build only).
+ *
+ * Pins are numbered net-contiguously: net e owns pins net_ptr[e] ..
+ * net_ptr[e+1]-1 and its first pin is the driver (pin_dir 1); every other pin
+ * of the net is a sink (pin_dir 0).  Every pin belongs to exactly one net and
+ * every net has at least one sink.
+ *
+ * Cell types and their pins:
+ *   TDP_CELL_COMB  1..32 input pins and exactly one output pin;
+ *   TDP_CELL_FF    at most one input (D, an endpoint) and at most one output
+ *                  (Q, a startpoint);
+ *   TDP_CELL_PI    primary input port: one output (startpoint), no input;
+ *   TDP_CELL_PO    primary output port: one input (endpoint), no output.
+ *
+ * Delay model (Eq. (8) with R and C linear in wire length): the wire from a
+ * net's driver to sink s has Manhattan length L between the pin positions
+ * (cell position plus pin offset), Elmore delay
+ *   t_s = r L (c L / 2 + pin_cap[s]),
+ * and the net's load is C_load = sum over sinks of (c L + pin_cap[s]).  The
+ * driving cell's delay d = d0 + cell_rdrv * C_load applies to every input
+ * arc of a combinational cell, and is the launch (clock-to-Q) delay of a
+ * flip-flop or primary input.  Single corner, late only, ideal clock at
+ * t = 0, setup time 0.
+ */
+typedef struct {
+    int32_t n_cells, n_pins, n_nets;
+    const int32_t *pin_cell;   /* [n_pins]   owning cell of every pin           */
+    const int32_t *net_ptr;    /* [n_nets+1] CSR of pins by net, driver first    */
+    const uint8_t *pin_dir;    /* [n_pins]   1 driver, 0 sink                    */
+    const int32_t *cell_type;  /* [n_cells]  TDP_CELL_*                          */
+    const float *pin_dx;       /* [n_pins]   pin offset from the cell, um        */
+    const float *pin_dy;       /* [n_pins]                                       */
+    const float *pin_cap;      /* [n_pins]   fF (sinks; ignored on drivers)      */
+    const float *cell_rdrv;    /* [n_cells]  drive resistance, kOhm              */
+    const uint8_t *cell_fixed; /* [n_cells]  1: the cell gets zero gradient      */
+    double r_per_um;           /* wire resistance, kOhm/um                       */
+    double c_per_um;           /* wire capacitance, fF/um                        */
+    double d0_ps;              /* intrinsic cell delay, ps                       */
+} tdp_netlist_desc;
+
+/*
+ * Build the device timing graph (Section II-B): validate the netlist,
+ * levelize the combinational cells, lay the CSR-by-level arrays out in device
+ * memory and allocate all timing state for the given precision.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream); all later
+ * work of this graph is queued on it.
+ * Errors: TDP_ERR_INVALID (malformed description), TDP_ERR_CYCLE
+ * (combinational loop), TDP_ERR_OOM, TDP_ERR_CUDA.  *out is NULL on error.
+ */
+TDP_API tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision precision, void *cuda_stream,
+                     tdp_graph **out);
+
+/* Free every device and host resource of the graph (NULL is a no-op). */
+TDP_API void sta_destroy(tdp_graph *g);
+
+/*
+ * Static timing analysis at placement (x, y) (Section II-B; Eq. (2)
+ * slack; Eqs. (3)-(4) WNS / TNS; Eq. (8) net delay).
+ * x_dev, y_dev: [n_cells] cell positions (float or double by precision).
+ * Computes Elmore net delays and cell delays, arrival times forward and
+ * required times backward over the levels, the slack of every pin, and
+ * WNS = min slack over violated endpoints, TNS = sum of their slacks (both
+ * 0 when no endpoint violates), reduced in FP64.
+ * wns_out / tns_out: host doubles, or NULL to skip the synchronisation.
+ */
+TDP_API tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void *y_dev,
+                         double clock_period_ps, double *wns_out, double *tns_out);
+
+/*
+ * Copy per-pin arrival, required time and slack (float/double [n_pins]) of the
+ * last sta_propagate into caller device buffers; any pointer may be NULL.
+ * Errors: TDP_ERR_STATE before the first sta_propagate.
+ */
+TDP_API tdp_status sta_get_timing(tdp_graph *g, void *arr_dev, void *req_dev, void *slack_dev);
+
+/*
+ * Copy the net delays of the last sta_propagate: Elmore delay of every pin
+ * (0 on drivers) [n_pins], and per net the load C_load and the delay d of its
+ * driving cell [n_nets] (Eq. (8)).  Any pointer may be NULL.
+ */
+TDP_API tdp_status sta_get_net_delays(tdp_graph *g, void *tnet_dev, void *cload_dev, void *dcell_dev);
+
+/*
+ * report_timing_endpoint(n, K) (Section III-B): sort the failing endpoints
+ * by (slack, pin) ascending, take the n most critical (n < 0: all of them),
+ * and extract for each its K lowest-slack startpoint-to-endpoint paths
+ * (rank 1 is the worst path).  With keep_nonneg == 0 only paths of negative
+ * slack are kept, so an endpoint may return fewer than K; with
+ * keep_nonneg != 0 up to K paths are kept whatever their slack.  Equal-slack
+ * paths are ordered by their pin sequences read from the endpoint
+ * backwards (lexicographic, smaller first); argmax ties take the lowest pin.
+ * 1 <= K <= 32.  n_paths_out: host int64 or NULL (no synchronisation).
+ * The paths stay valid until the next extract_critical_paths or
+ * sta_propagate.  Errors: TDP_ERR_STATE before sta_propagate.
+ */
+TDP_API tdp_status extract_critical_paths(tdp_graph *g, int32_t n_endpoints, int32_t K,
+                                  int32_t keep_nonneg, int64_t *n_paths_out);
+
+/*
+ * Sizes of the last extraction (synchronises): number of failing endpoints,
+ * number of paths, total number of pins over all paths.
+ */
+TDP_API tdp_status sta_get_paths_size(tdp_graph *g, int32_t *n_viol_out, int64_t *n_paths_out,
+                              int64_t *n_path_pins_out);
+
+/*
+ * Materialise the extracted paths into caller device buffers, endpoints in
+ * (slack, pin) order and paths by rank within an endpoint:
+ *   viol_dev    int32[n_viol]      failing endpoints, most critical first;
+ *   ep_dev      int32[n_paths]     endpoint pin of every path;
+ *   slack_dev   float/double[n_paths] path slack (T - path delay);
+ *   pin_ptr_dev int64[n_paths+1]   offsets into pins_dev;
+ *   pins_dev    int32[n_path_pins] pins of each path, startpoint first.
+ * Any pointer may be NULL.  Sizes come from sta_get_paths_size.
+ */
+TDP_API tdp_status sta_get_paths(tdp_graph *g, int32_t *viol_dev, int32_t *ep_dev, void *slack_dev,
+                         int64_t *pin_ptr_dev, int32_t *pins_dev);
+
+/*
+ * Eq. (w_ij) (Section III-D): traverse the extracted paths, worst first.
+ * Every net arc (driver -> sink s) on a path is a pin pair, identified by s.
+ * A pair not yet in P enters P with weight w0; a pair already in P gains
+ * w1 * slack / WNS, slack being the path's slack and WNS the last
+ * sta_propagate's.  Contributions of all paths through a pair add up
+ * (path sharing); the result does not depend on the order of the paths.
+ * P and the weights persist across calls until attraction_reset_pairs.
+ * n_pairs_out: host int64 (|P| after the update) or NULL.
+ * Errors: TDP_ERR_STATE before extract_critical_paths.
+ */
+TDP_API tdp_status attraction_update_pairs(tdp_graph *g, double w0, double w1, int64_t *n_pairs_out);
+
+/* Empty the pin-pair set P. */
+TDP_API tdp_status attraction_reset_pairs(tdp_graph *g);
+
+/*
+ * Replace P by the n_pairs sink pins in pins_host (each a sink pin, no
+ * duplicates) with weights w_host (host arrays, read during the call).
+ * Used to restore a saved state.  Errors: TDP_ERR_INVALID.
+ */
+TDP_API tdp_status attraction_set_pairs(tdp_graph *g, int64_t n_pairs, const int32_t *pins_host,
+                                const double *w_host);
+
+/*
+ * Copy P into caller device buffers: pins_dev int32[|P|] (sink pins,
+ * ascending) and w_dev float/double[|P|]; n_pairs_out (host) receives |P|
+ * (synchronises).  Either buffer may be NULL to query the size only.
+ */
+TDP_API tdp_status attraction_get_pairs(tdp_graph *g, int32_t *pins_dev, void *w_dev,
+                                int64_t *n_pairs_out);
+
+/*
+ * Pin-to-pin attraction loss (Eq. (9) and PP of Section III-D):
+ *   loss = beta * sum over (driver, s) in P of w_s * Q(driver, s),
+ *   Q(i, j) = (x_i - x_j)^2 + (y_i - y_j)^2 on pin coordinates.
+ * x_dev, y_dev: [n_cells]; loss_dev: one device double (overwritten).
+ * Terms in the graph's precision, the total in FP64; deterministic.
+ */
+TDP_API tdp_status attraction_loss_fwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
+                               double *loss_dev);
+
+/*
+ * Adjoint of attraction_loss_fwd: gx_dev, gy_dev [n_cells] are overwritten
+ * with grad_scale * dloss/dx, dloss/dy, where grad_scale is the device
+ * double *grad_scale_dev (NULL means 1).  Per sink s in P the pin gradient is
+ * 2 beta w_s (p_s - p_driver); the driver receives minus the sum over its
+ * sinks; a cell receives the sum of its pins' gradients, accumulated in FP64
+ * in a fixed order (no floating-point atomics); fixed cells receive 0.
+ */
+TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
+                               const double *grad_scale_dev, void *gx_dev, void *gy_dev);
+
+/* Message for the last non-OK status returned on this host thread. */
+TDP_API const char *tdp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDP_H */

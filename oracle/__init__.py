@@ -55,7 +55,7 @@ def _load():
                                P, P, P, P, P, P, P, P, P]
         lib.or_topk.restype = C.c_int
         lib.or_topk.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, C.c_double,
-                                C.c_int, C.c_int, C.c_int, C.POINTER(_Paths)]
+                                C.c_int, C.c_int, C.c_int, P, C.c_int, C.POINTER(_Paths)]
         lib.or_free_paths.restype = None
         lib.or_free_paths.argtypes = [C.POINTER(_Paths)]
         lib.or_update_pairs.restype = C.c_int
@@ -116,19 +116,26 @@ def clock_period(nl, factor: float, x=None, y=None) -> float:
     return factor * (-sta(nl, x, y, 0.0)["wns"])
 
 
-def topk(nl, timing: dict, n_endpoints: int = -1, K: int = 1, keep_nonneg: bool = False) -> dict:
+def topk(nl, timing: dict, n_endpoints: int = -1, K: int = 1, keep_nonneg: bool = False,
+         endpoints=None) -> dict:
     """report_timing_endpoint(n, K) of Section III-B on the FP64 timing.
 
     Returns the violating endpoints sorted by (slack, pin) and, per path,
     ``ep, rank, slack`` and its pins (startpoint first) as ``pin_ptr/pins``.
+    ``endpoints`` (optional) restricts the search to the given endpoint pins.
     """
     lib = _load()
     pc, npt, ct = _i32(nl.pin_cell), _i32(nl.net_ptr), _i32(nl.cell_type)
     res = _Paths()
+    if endpoints is None:
+        epl, n_list = np.zeros(1, dtype=np.int32), -1
+    else:
+        epl = _i32(endpoints)
+        n_list = len(epl)
     st = lib.or_topk(nl.n_cells, nl.n_pins, nl.n_nets, _p(pc), _p(npt), _p(ct),
                      _p(_f64(timing["tnet"])), _p(_f64(timing["dnet"])),
                      _p(_f64(timing["arr"])), float(timing["T"]), int(n_endpoints), int(K),
-                     int(bool(keep_nonneg)), C.byref(res))
+                     int(bool(keep_nonneg)), _p(epl), int(n_list), C.byref(res))
     if st != OR_OK:
         raise RuntimeError(f"oracle topk failed with status {st}")
     n, m, nv = res.n_paths, res.n_pins_total, res.n_viol

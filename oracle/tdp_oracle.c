@@ -353,9 +353,14 @@ static int cmp_ep(const void *a, const void *b) {
  * delay of any path from a startpoint to v.  States are expanded best first,
  * so complete paths leave the queue in order of increasing slack.
  */
+/*
+ * ep_list / n_list: when n_list >= 0, search exactly these endpoints (in the
+ * given order) instead of the n most critical failing ones.
+ */
 int or_topk(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell, const int32_t *net_ptr,
             const int32_t *cell_type, const double *tnet, const double *dnet, const double *arr,
-            double T, int n_endpoints, int K, int keep_nonneg, or_paths_t *out) {
+            double T, int n_endpoints, int K, int keep_nonneg, const int32_t *ep_list, int n_list,
+            or_paths_t *out) {
     memset(out, 0, sizeof(*out));
     nl_t nl;
     int st = nl_init(&nl, n_cells, n_pins, n_nets, pin_cell, net_ptr, cell_type);
@@ -386,8 +391,9 @@ int or_topk(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell, const 
     search_t s;
     memset(&s, 0, sizeof(s));
     s.arr = arr;
+    if (n_list >= 0) n_use = n_list;
     for (int iv = 0; iv < n_use; ++iv) {
-        int e = viol[iv];
+        int e = n_list >= 0 ? ep_list[iv] : viol[iv];
         s.n = 0; s.hn = 0;
         if (push_state(&s, e, -1, 0.0)) goto oom_s;
         int found = 0;

@@ -1,0 +1,397 @@
+// sta_build / sta_destroy: validate the netlist, levelize the combinational
+// cells (the timing graph of Section II-B is a DAG once flip-flops cut it),
+// and lay the level-ordered CSR arrays out in device memory.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "tdp_internal.cuh"
+
+namespace tdp {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+template <typename T>
+static tdp_status upload(tdp_graph *g, T **dst, const std::vector<T> &src) {
+    TDP_TRY(dalloc(g, dst, src.size()));
+    if (!src.empty())
+        TDP_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
+    State<R> &s = state<R>(g);
+    Topo &t = g->topo;
+    using A = typename Acc<R>::T;
+    std::vector<R> v(d->pin_dx, d->pin_dx + t.n_pins);
+    TDP_TRY(upload(g, &s.pin_dx, v));
+    v.assign(d->pin_dy, d->pin_dy + t.n_pins);
+    TDP_TRY(upload(g, &s.pin_dy, v));
+    v.assign(d->pin_cap, d->pin_cap + t.n_pins);
+    TDP_TRY(upload(g, &s.pin_cap, v));
+    v.assign(d->cell_rdrv, d->cell_rdrv + t.n_cells);
+    TDP_TRY(upload(g, &s.cell_rdrv, v));
+    TDP_TRY(dalloc(g, &s.tnet, t.n_pins));
+    TDP_TRY(dalloc(g, &s.cload, t.n_nets));
+    TDP_TRY(dalloc(g, &s.dnet, t.n_nets));
+    TDP_TRY(dalloc(g, &s.arr, t.n_pins));
+    TDP_TRY(dalloc(g, &s.req, t.n_pins));
+    TDP_TRY(dalloc(g, &s.slack, t.n_pins));
+    TDP_TRY(dalloc(g, &s.T, 1));
+    TDP_TRY(dalloc(g, &s.wns_tns, 2));
+    TDP_TRY(dalloc(g, &s.red_part, 1024));
+    TDP_TRY(dalloc(g, &s.red_count, 1));
+    TDP_CUDA(cudaMemset(s.red_count, 0, sizeof(unsigned)));
+    TDP_CUDA(cudaMemset(s.tnet, 0, sizeof(R) * t.n_pins));
+    // static per-net path data of startpoints: no worst input, chain length 1
+    std::vector<int32_t> pred(t.n_nets, -1), plen(t.n_nets, 1);
+    TDP_TRY(upload(g, &s.pred_in, pred));
+    TDP_TRY(upload(g, &s.pred_net, pred));
+    TDP_TRY(upload(g, &s.plen, plen));
+    // extraction
+    TDP_TRY(dalloc(g, &s.sort_a, 2 * (size_t)std::max(t.n_ep, 1)));
+    TDP_TRY(dalloc(g, &s.sort_b, 2 * (size_t)std::max(t.n_ep, 1)));
+    TDP_TRY(dalloc(g, &s.nviol, 1));
+    TDP_TRY(dalloc(g, &s.viol, std::max(t.n_ep, 1)));
+    TDP_TRY(dalloc(g, &s.bcnt, t.n_nets));
+    TDP_CUDA(cudaMemset(s.bcnt, 0, t.n_nets));
+    TDP_TRY(dalloc(g, &s.p_count, std::max(t.n_ep, 1)));
+    TDP_TRY(dalloc(g, &s.n_paths, 1));
+    // pin pairs
+    TDP_TRY(dalloc(g, &s.sumq, t.n_pins));
+    TDP_TRY(dalloc(g, &s.maxq, t.n_pins));
+    TDP_TRY(dalloc(g, &s.touch, t.n_pins));
+    TDP_TRY(dalloc(g, &s.in_p, t.n_pins));
+    TDP_TRY(dalloc(g, &s.w, t.n_pins));
+    TDP_TRY(dalloc(g, &s.n_pairs, 1));
+    TDP_CUDA(cudaMemset(s.sumq, 0, sizeof(long long) * t.n_pins));
+    std::vector<long long> mq(t.n_pins, INT64_MIN);
+    TDP_CUDA(cudaMemcpy(s.maxq, mq.data(), sizeof(long long) * t.n_pins, cudaMemcpyHostToDevice));
+    TDP_CUDA(cudaMemset(s.touch, 0, t.n_pins));
+    TDP_CUDA(cudaMemset(s.in_p, 0, t.n_pins));
+    TDP_CUDA(cudaMemset(s.w, 0, sizeof(R) * t.n_pins));
+    TDP_CUDA(cudaMemset(s.n_pairs, 0, sizeof(long long)));
+    // loss
+    TDP_TRY(dalloc(g, &s.gslot, 2 * (size_t)t.n_pins));
+    TDP_TRY(dalloc(g, &s.loss_part, 1024));
+    TDP_TRY(dalloc(g, &s.loss_count, 1));
+    TDP_CUDA(cudaMemset(s.loss_count, 0, sizeof(unsigned)));
+    (void)sizeof(A);
+    return TDP_OK;
+}
+
+static bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
+
+static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
+    Topo &t = g->topo;
+    const int nc = d->n_cells, np = d->n_pins, nn = d->n_nets;
+    if (nc <= 0 || np <= 0 || nn <= 0) {
+        set_error("sta_build: n_cells, n_pins and n_nets must be positive");
+        return TDP_ERR_INVALID;
+    }
+    if (!d->pin_cell || !d->net_ptr || !d->pin_dir || !d->cell_type || !d->pin_dx ||
+        !d->pin_dy || !d->pin_cap || !d->cell_rdrv || !d->cell_fixed) {
+        set_error("sta_build: a netlist array pointer is NULL");
+        return TDP_ERR_INVALID;
+    }
+    if (!(std::isfinite(d->r_per_um) && d->r_per_um >= 0 && std::isfinite(d->c_per_um) &&
+          d->c_per_um >= 0 && std::isfinite(d->d0_ps) && d->d0_ps >= 0)) {
+        set_error("sta_build: r_per_um, c_per_um and d0_ps must be finite and >= 0");
+        return TDP_ERR_INVALID;
+    }
+    if (d->net_ptr[0] != 0 || d->net_ptr[nn] != np) {
+        set_error("sta_build: net_ptr must start at 0 and end at n_pins");
+        return TDP_ERR_INVALID;
+    }
+    std::vector<int32_t> pin_net(np);
+    int n_big = 0;
+    for (int e = 0; e < nn; ++e) {
+        int a = d->net_ptr[e], b = d->net_ptr[e + 1];
+        if (b - a < 2 || a < 0 || b > np) {
+            set_error("sta_build: net %d has %d pins (needs a driver and at least one sink)", e,
+                      b - a);
+            return TDP_ERR_INVALID;
+        }
+        if (b - a - 1 > kBigFanout) ++n_big;
+        for (int p = a; p < b; ++p) {
+            pin_net[p] = e;
+            if (d->pin_dir[p] != (p == a ? 1 : 0)) {
+                set_error("sta_build: pin %d of net %d: pin_dir must be 1 for the first pin and 0 "
+                          "for the others", p, e);
+                return TDP_ERR_INVALID;
+            }
+        }
+    }
+    for (int c = 0; c < nc; ++c) {
+        int ty = d->cell_type[c];
+        if (ty < TDP_CELL_COMB || ty > TDP_CELL_PO) {
+            set_error("sta_build: cell %d has unknown type %d", c, ty);
+            return TDP_ERR_INVALID;
+        }
+        if (!finite_nonneg(d->cell_rdrv[c])) {
+            set_error("sta_build: cell %d has a non-finite or negative drive resistance", c);
+            return TDP_ERR_INVALID;
+        }
+    }
+    std::vector<int32_t> n_in(nc, 0), n_out(nc, 0), out_pin(nc, -1);
+    for (int p = 0; p < np; ++p) {
+        int c = d->pin_cell[p];
+        if (c < 0 || c >= nc) {
+            set_error("sta_build: pin %d refers to cell %d out of range", p, c);
+            return TDP_ERR_INVALID;
+        }
+        if (!finite_nonneg(d->pin_cap[p]) || !std::isfinite(d->pin_dx[p]) ||
+            !std::isfinite(d->pin_dy[p])) {
+            set_error("sta_build: pin %d has a non-finite offset or capacitance", p);
+            return TDP_ERR_INVALID;
+        }
+        if (d->pin_dir[p]) {
+            n_out[c]++;
+            out_pin[c] = p;
+        } else {
+            n_in[c]++;
+        }
+    }
+    int n_comb = 0;
+    for (int c = 0; c < nc; ++c) {
+        int ty = d->cell_type[c];
+        bool ok = true;
+        if (ty == TDP_CELL_COMB) {
+            ok = n_in[c] >= 1 && n_in[c] <= kMaxFanin && n_out[c] == 1;
+            ++n_comb;
+        } else if (ty == TDP_CELL_FF) {
+            ok = n_in[c] <= 1 && n_out[c] <= 1;
+        } else if (ty == TDP_CELL_PI) {
+            ok = n_in[c] == 0 && n_out[c] == 1;
+        } else {
+            ok = n_in[c] == 1 && n_out[c] == 0;
+        }
+        if (!ok) {
+            set_error("sta_build: cell %d (type %d) has %d inputs and %d outputs", c, ty, n_in[c],
+                      n_out[c]);
+            return TDP_ERR_INVALID;
+        }
+    }
+    // cell -> pins CSR, ascending pin index
+    std::vector<int32_t> cp_ptr(nc + 1, 0), cp(np), slot(np);
+    for (int p = 0; p < np; ++p) cp_ptr[d->pin_cell[p] + 1]++;
+    for (int c = 0; c < nc; ++c) cp_ptr[c + 1] += cp_ptr[c];
+    {
+        std::vector<int32_t> fill(cp_ptr.begin(), cp_ptr.end() - 1);
+        for (int p = 0; p < np; ++p) {
+            int k = fill[d->pin_cell[p]]++;
+            cp[k] = p;
+            slot[p] = k;
+        }
+    }
+    // levelize combinational cells (Kahn); flip-flops and primary inputs are level 0
+    std::vector<int32_t> level(nc, 0), deps(nc, 0);
+    for (int c = 0; c < nc; ++c) {
+        if (d->cell_type[c] != TDP_CELL_COMB) continue;
+        level[c] = 1;
+        for (int k = cp_ptr[c]; k < cp_ptr[c + 1]; ++k) {
+            int p = cp[k];
+            if (d->pin_dir[p]) continue;
+            int dc = d->pin_cell[d->net_ptr[pin_net[p]]];
+            if (d->cell_type[dc] == TDP_CELL_COMB) deps[c]++;
+        }
+    }
+    std::vector<int32_t> queue;
+    queue.reserve(n_comb);
+    for (int c = 0; c < nc; ++c)
+        if (d->cell_type[c] == TDP_CELL_COMB && deps[c] == 0) queue.push_back(c);
+    for (size_t h = 0; h < queue.size(); ++h) {
+        int c = queue[h];
+        int e = pin_net[out_pin[c]];
+        for (int s = d->net_ptr[e] + 1; s < d->net_ptr[e + 1]; ++s) {
+            int c2 = d->pin_cell[s];
+            if (d->cell_type[c2] != TDP_CELL_COMB) continue;
+            level[c2] = std::max(level[c2], level[c] + 1);
+            if (--deps[c2] == 0) queue.push_back(c2);
+        }
+    }
+    if ((int)queue.size() != n_comb) {
+        set_error("sta_build: combinational loop (%d of %d combinational cells levelized)",
+                  (int)queue.size(), n_comb);
+        return TDP_ERR_CYCLE;
+    }
+    int D = 0;
+    for (int c = 0; c < nc; ++c)
+        if (d->cell_type[c] == TDP_CELL_COMB) D = std::max(D, level[c]);
+
+    // combinational cells by (level, id)
+    std::vector<int32_t> lvl_ptr(D + 1, 0);
+    for (int c = 0; c < nc; ++c)
+        if (d->cell_type[c] == TDP_CELL_COMB) lvl_ptr[level[c]]++;
+    for (int l = 1; l <= D; ++l) lvl_ptr[l] += lvl_ptr[l - 1];
+    // lvl_ptr[l] = number of cells with level <= l; cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
+    std::vector<int32_t> lv_cell(n_comb);
+    {
+        std::vector<int32_t> fill(D + 1, 0);
+        for (int l = 1; l <= D; ++l) fill[l] = lvl_ptr[l - 1];
+        for (int c = 0; c < nc; ++c)
+            if (d->cell_type[c] == TDP_CELL_COMB) lv_cell[fill[level[c]]++] = c;
+    }
+    std::vector<int32_t> lv_out(n_comb), lv_onet(n_comb), lv_in_ptr(n_comb + 1, 0);
+    std::vector<int32_t> lv_in_pin, lv_in_drv, lv_in_net;
+    for (int k = 0; k < n_comb; ++k) {
+        int c = lv_cell[k];
+        lv_out[k] = out_pin[c];
+        lv_onet[k] = pin_net[out_pin[c]];
+        for (int q = cp_ptr[c]; q < cp_ptr[c + 1]; ++q) {
+            int p = cp[q];
+            if (d->pin_dir[p]) continue;
+            lv_in_pin.push_back(p);
+            lv_in_drv.push_back(d->net_ptr[pin_net[p]]);
+            lv_in_net.push_back(pin_net[p]);
+        }
+        lv_in_ptr[k + 1] = (int32_t)lv_in_pin.size();
+    }
+    // per-pin kinds and sink links
+    std::vector<uint8_t> kind(np);
+    std::vector<int32_t> sink_out(np, -1), sink_onet(np, -1), ep;
+    for (int p = 0; p < np; ++p) {
+        int c = d->pin_cell[p];
+        int ty = d->cell_type[c];
+        if (d->pin_dir[p]) {
+            kind[p] = (ty == TDP_CELL_COMB) ? PK_COMB_OUT : PK_START;
+        } else if (ty == TDP_CELL_COMB) {
+            kind[p] = PK_COMB_IN;
+            sink_out[p] = out_pin[c];
+            sink_onet[p] = pin_net[out_pin[c]];
+        } else {
+            kind[p] = PK_ENDPOINT;
+            ep.push_back(p);
+        }
+    }
+    // nets grouped by driver level; small nets first within a level
+    std::vector<int32_t> net_level(nn);
+    for (int e = 0; e < nn; ++e) net_level[e] = level[d->pin_cell[d->net_ptr[e]]];
+    std::vector<int32_t> bl_ptr(D + 2, 0), bl_small(D + 1, 0), bl_net(nn), big;
+    for (int e = 0; e < nn; ++e) {
+        bl_ptr[net_level[e] + 1]++;
+        if (d->net_ptr[e + 1] - d->net_ptr[e] - 1 <= kBigFanout) bl_small[net_level[e]]++;
+        else big.push_back(e);
+    }
+    for (int l = 0; l <= D; ++l) bl_ptr[l + 1] += bl_ptr[l];
+    {
+        std::vector<int32_t> fs(D + 1), fb(D + 1);
+        for (int l = 0; l <= D; ++l) {
+            fs[l] = bl_ptr[l];
+            fb[l] = bl_ptr[l] + bl_small[l];
+        }
+        for (int e = 0; e < nn; ++e) {
+            int l = net_level[e];
+            bool small = d->net_ptr[e + 1] - d->net_ptr[e] - 1 <= kBigFanout;
+            bl_net[small ? fs[l]++ : fb[l]++] = e;
+        }
+    }
+    t.n_cells = nc;
+    t.n_pins = np;
+    t.n_nets = nn;
+    t.n_comb = n_comb;
+    t.n_in = (int32_t)lv_in_pin.size();
+    t.n_ep = (int32_t)ep.size();
+    t.depth = D;
+    t.n_big = (int32_t)big.size();
+    g->lv.lvl_ptr = lvl_ptr;
+    g->lv.bl_ptr = bl_ptr;
+    g->lv.bl_small = bl_small;
+    std::vector<int32_t> pc(d->pin_cell, d->pin_cell + np), nptr(d->net_ptr, d->net_ptr + nn + 1);
+    std::vector<uint8_t> fixed(d->cell_fixed, d->cell_fixed + nc);
+    TDP_TRY(upload(g, &t.pin_cell, pc));
+    TDP_TRY(upload(g, &t.pin_net, pin_net));
+    TDP_TRY(upload(g, &t.net_ptr, nptr));
+    TDP_TRY(upload(g, &t.pin_kind, kind));
+    TDP_TRY(upload(g, &t.sink_out, sink_out));
+    TDP_TRY(upload(g, &t.sink_onet, sink_onet));
+    TDP_TRY(upload(g, &t.net_level, net_level));
+    TDP_TRY(upload(g, &t.big_nets, big));
+    TDP_TRY(upload(g, &t.lv_out, lv_out));
+    TDP_TRY(upload(g, &t.lv_onet, lv_onet));
+    TDP_TRY(upload(g, &t.lv_in_ptr, lv_in_ptr));
+    TDP_TRY(upload(g, &t.lv_in_pin, lv_in_pin));
+    TDP_TRY(upload(g, &t.lv_in_drv, lv_in_drv));
+    TDP_TRY(upload(g, &t.lv_in_net, lv_in_net));
+    TDP_TRY(upload(g, &t.bl_net, bl_net));
+    TDP_TRY(upload(g, &t.ep, ep));
+    TDP_TRY(upload(g, &t.cp_ptr, cp_ptr));
+    TDP_TRY(upload(g, &t.cp, cp));
+    TDP_TRY(upload(g, &t.slot_of_pin, slot));
+    TDP_TRY(upload(g, &t.cell_fixed, fixed));
+    return TDP_OK;
+}
+
+}  // namespace tdp
+
+using namespace tdp;
+
+extern "C" const char *tdp_last_error(void) { return g_err; }
+
+extern "C" void sta_destroy(tdp_graph *g) {
+    if (!g) return;
+    if (g->sta_graph) cudaGraphExecDestroy(g->sta_graph);
+    if (g->bsweep_graph) cudaGraphExecDestroy(g->bsweep_graph);
+    for (void *p : g->allocs) cudaFree(p);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+}
+
+extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision precision,
+                                void *cuda_stream, tdp_graph **out) {
+    if (!out) {
+        set_error("sta_build: out is NULL");
+        return TDP_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (!netlist) {
+        set_error("sta_build: netlist is NULL");
+        return TDP_ERR_INVALID;
+    }
+    if (precision != TDP_FP32 && precision != TDP_FP64) {
+        set_error("sta_build: unknown precision %d", (int)precision);
+        return TDP_ERR_INVALID;
+    }
+    tdp_graph *g = new (std::nothrow) tdp_graph();
+    if (!g) {
+        set_error("sta_build: host allocation failed");
+        return TDP_ERR_OOM;
+    }
+    g->prec = precision;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    g->r = netlist->r_per_um;
+    g->c = netlist->c_per_um;
+    g->d0 = netlist->d0_ps;
+    tdp_status st = build_topology(g, netlist);
+    if (st == TDP_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            set_error("sta_build: cudaStreamCreate failed: %s", cudaGetErrorString(e));
+            st = TDP_ERR_CUDA;
+        }
+    }
+    if (st == TDP_OK)
+        st = precision == TDP_FP32 ? build_state<float>(g, netlist) : build_state<double>(g, netlist);
+    if (st == TDP_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            set_error("sta_build: %s", cudaGetErrorString(e));
+            st = TDP_ERR_CUDA;
+        }
+    }
+    if (st != TDP_OK) {
+        sta_destroy(g);
+        return st;
+    }
+    *out = g;
+    return TDP_OK;
+}

@@ -1,0 +1,640 @@
+// report_timing_endpoint(n, K) on the device (Section III-B).
+//
+// 1. k_viol_collect / k_tile_sort / k_merge_pass / k_sort_finish
+//      failing endpoints sorted by (slack, pin): the pin breaks every tie, so
+//      the (slack, pin) items are unique and the sorted order is unique.
+// 2. k_bsweep_level (one launch per level, captured in a CUDA graph)
+//      For every combinational output v with negative slack, the K-1 cheapest
+//      sidetracks on the worst-input chain from v back to its startpoint.
+//      A sidetrack enters a node u through an input pin i other than u's
+//      worst input; its cost delta = Arr(worst input) - Arr(i) >= 0 is the
+//      slack a path loses by taking it.  list(v) = merge(own sidetracks of v,
+//      list(worst-input driver of v)), so each list is one merge of two sorted
+//      lists.  Equal costs are ordered as the pin sequences of the resulting
+//      paths would be (read from the endpoint): v's own sidetracks through a
+//      lower pin than v's worst input come first, then the inherited entries,
+//      then v's sidetracks through a higher pin.
+// 3. k_topk: one warp per failing endpoint.  The worst path follows worst
+//      inputs from the endpoint; every other path is its parent path plus one
+//      sidetrack taken on the parent's last worst-input chain.  A candidate
+//      (parent p, index j) is entry j of the list at the head of p's chain;
+//      popping it makes a new path and pushes at most two candidates: (p, j+1)
+//      and (new path, 0).  Costs only grow along these links, so popping the
+//      cheapest candidate K-1 times yields the K lowest-slack paths in order;
+//      the frontier never holds more than K candidates, one per lane.
+#include <climits>
+
+#include "tdp_internal.cuh"
+
+namespace tdp {
+
+struct SortItem {
+    unsigned long long key;  // slack bits, order-preserving as an unsigned integer
+    unsigned long long pin;
+};
+
+__device__ __forceinline__ bool item_less(const SortItem &a, const SortItem &b) {
+    return a.key < b.key || (a.key == b.key && a.pin < b.pin);
+}
+
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename R>
+__global__ void k_viol_collect(Topo t, State<R> s, SortItem *items) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool v = false;
+    int p = -1;
+    double sl = 0.0;
+    if (i < t.n_ep) {
+        p = t.ep[i];
+        sl = (double)s.slack[p];
+        v = sl < 0.0;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, v);
+    if (!m) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(s.nviol, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (v) {
+        int off = __popc(m & ((1u << lane) - 1u));
+        items[base + off] = SortItem{ordered_bits(sl), (unsigned long long)p};
+    }
+}
+
+constexpr int kTile = 2048;
+
+// Bitonic sort of one tile of 2048 items in shared memory (1024 threads).
+__global__ void __launch_bounds__(1024) k_tile_sort(SortItem *items, const int *nviol) {
+    __shared__ SortItem sh[kTile];
+    const int n = *nviol;
+    const int base = blockIdx.x * kTile;
+    if (base >= n) return;
+    for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+        int i = base + k;
+        sh[k] = i < n ? items[i] : SortItem{~0ull, ~0ull};
+    }
+    __syncthreads();
+    for (int k = 2; k <= kTile; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k) == 0;
+                    SortItem a = sh[i], b = sh[ixj];
+                    if (item_less(b, a) == up) {
+                        sh[i] = b;
+                        sh[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+        int i = base + k;
+        if (i < n) items[i] = sh[k];
+    }
+}
+
+// One merge pass: runs of length `run` are merged pairwise.  Items are
+// unique, so an item's output position is its index in its own run plus the
+// number of smaller items in the partner run.
+__global__ void k_merge_pass(const SortItem *in, SortItem *out, const int *nviol, int run) {
+    const int n = *nviol;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SortItem me = in[i];
+    const int r = i / run;
+    const int pbeg = (r ^ 1) * run;
+    const int pend = min(pbeg + run, n);
+    const int pair_base = (r & ~1) * run;
+    int cnt = 0;
+    if (pbeg < n) {
+        int lo = pbeg, hi = pend;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (item_less(in[mid], me)) lo = mid + 1;
+            else hi = mid;
+        }
+        cnt = lo - pbeg;
+    }
+    out[pair_base + (i - r * run) + cnt] = me;
+}
+
+template <typename R>
+__global__ void k_sort_finish(State<R> s, const SortItem *items) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *s.nviol) s.viol[i] = (int)items[i].pin;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_bsweep_level(Topo t, State<R> s, int lo, int hi, int L,
+                                                      int keep_nonneg) {
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= hi) return;
+    const int e = t.lv_onet[k];
+    const R so = s.slack[t.lv_out[k]];
+    if (!keep_nonneg && !(so < R(0))) {  // no negative path passes through this node
+        s.bcnt[e] = 0;
+        return;
+    }
+    const int pi = s.pred_in[e], pn = s.pred_net[e];
+    const A apred = s.arr[pi];
+    R od[kMaxFanin];
+    int op[kMaxFanin];
+    int no = 0;
+    for (int q = t.lv_in_ptr[k]; q < t.lv_in_ptr[k + 1]; ++q) {
+        const int i = t.lv_in_pin[q];
+        if (i == pi) continue;
+        const R d = AC::diff(apred, s.arr[i]);
+        if (!keep_nonneg && !(so + d < R(0))) continue;
+        // insertion by (delta, side of the worst input, pin)
+        int pos = no;
+        while (pos > 0) {
+            R dp = od[pos - 1];
+            int pp = op[pos - 1];
+            bool before = d < dp || (d == dp && ((i < pi) != (pp < pi) ? (i < pi) : i < pp));
+            if (!before) break;
+            od[pos] = dp;
+            op[pos] = pp;
+            --pos;
+        }
+        od[pos] = d;
+        op[pos] = i;
+        ++no;
+    }
+    const BEnt<R> *pl = s.blist + (size_t)pn * L;
+    const int npl = s.bcnt[pn];
+    BEnt<R> *out = s.blist + (size_t)e * L;
+    int a = 0, b = 0, m = 0;
+    while (m < L) {
+        const bool ha = a < no;
+        const bool hb = b < npl && (keep_nonneg || pl[b].delta + so < R(0));
+        if (!ha && !hb) break;
+        bool take_own;
+        if (!hb) take_own = true;
+        else if (!ha) take_own = false;
+        else {
+            const R db = pl[b].delta;
+            take_own = od[a] < db || (od[a] == db && op[a] < pi);
+        }
+        if (take_own) {
+            out[m].delta = od[a];
+            out[m].pin = op[a];
+            ++a;
+        } else {
+            out[m] = pl[b];
+            ++b;
+        }
+        ++m;
+    }
+    s.bcnt[e] = (uint8_t)m;
+}
+
+// Is candidate a (parent path pa + sidetrack pin sa) ordered before candidate
+// b (pb + sb) when both have the same slack?  Paths are compared by their pin
+// sequences read from the endpoint; two paths first differ at the first
+// sidetrack where they disagree, on a shared worst-input chain.
+template <typename R>
+__device__ bool cand_before(const Topo &t, const State<R> &s, const int *par, const int *side,
+                            int pa, int sa, int pb, int sb) {
+    int A[kMaxK], B[kMaxK];
+    int na = 0, nb = 0;
+    A[na++] = sa;
+    for (int q = pa; q > 0; q = par[q]) A[na++] = side[q];
+    B[nb++] = sb;
+    for (int q = pb; q > 0; q = par[q]) B[nb++] = side[q];
+    // A[na-1] .. A[0] is the sequence from the endpoint
+    for (int k = 0;; ++k) {
+        const bool ea = k >= na, eb = k >= nb;
+        if (ea && eb) return false;
+        if (ea) {
+            const int x = B[nb - 1 - k];
+            return s.pred_in[t.sink_onet[x]] < x;
+        }
+        if (eb) {
+            const int x = A[na - 1 - k];
+            return x < s.pred_in[t.sink_onet[x]];
+        }
+        const int x = A[na - 1 - k], y = B[nb - 1 - k];
+        if (x == y) continue;
+        const int vx = t.sink_onet[x], vy = t.sink_onet[y];
+        if (vx == vy) return x < y;
+        if (t.net_level[vx] > t.net_level[vy]) return x < s.pred_in[vx];
+        return s.pred_in[vy] < y;
+    }
+}
+
+constexpr int kTopkWarps = 4;
+
+template <typename R>
+__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int L,
+                                                          int keep_nonneg, int n_cap) {
+    __shared__ int sh_par[kTopkWarps][kMaxK], sh_side[kTopkWarps][kMaxK];
+    __shared__ int sh_len[kTopkWarps][kMaxK];
+    __shared__ R sh_cost[kTopkWarps][kMaxK];
+    __shared__ int ct_par[kTopkWarps][32], ct_side[kTopkWarps][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const R INF = (R)__longlong_as_double(0x7ff0000000000000ll);
+    const int nv = min(*s.nviol, n_cap);
+    for (int i = blockIdx.x * kTopkWarps + w; i < nv; i += gridDim.x * kTopkWarps) {
+        const int ep = s.viol[i];
+        const R se = s.slack[ep];
+        const int e0 = t.pin_net[ep];
+        if (lane == 0) {
+            sh_par[w][0] = -1;
+            sh_side[w][0] = -1;
+            sh_len[w][0] = 1 + s.plen[e0];
+            sh_cost[w][0] = R(0);
+        }
+        bool cv = false;
+        int cpar = 0, cj = 0, ctail = 0;
+        R ccost = R(0);
+        if (lane == 0 && K > 1 && s.bcnt[e0] > 0) {
+            const R d = s.blist[(size_t)e0 * L].delta;
+            if (keep_nonneg || se + d < R(0)) {
+                cv = true;
+                ctail = e0;
+                ccost = d;
+            }
+        }
+        __syncwarp();
+        int n = 1;
+        for (; n < K; ++n) {
+            R mn = cv ? ccost : INF;
+            for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(FULL, mn, o));
+            if (!(mn < INF)) break;
+            const unsigned tied = __ballot_sync(FULL, cv && ccost == mn);
+            int win = __ffs(tied) - 1;
+            if (__popc(tied) > 1) {  // equal slack: order by pin sequence
+                if (cv) {
+                    ct_par[w][lane] = cpar;
+                    ct_side[w][lane] = s.blist[(size_t)ctail * L + cj].pin;
+                }
+                __syncwarp();
+                int best = win;
+                if (lane == 0) {
+                    for (int l = win + 1; l < 32; ++l) {
+                        if (!((tied >> l) & 1u)) continue;
+                        if (cand_before<R>(t, s, sh_par[w], sh_side[w], ct_par[w][l], ct_side[w][l],
+                                           ct_par[w][best], ct_side[w][best]))
+                            best = l;
+                    }
+                }
+                win = __shfl_sync(FULL, best, 0);
+            }
+            const int wpar = __shfl_sync(FULL, cpar, win);
+            const int wj = __shfl_sync(FULL, cj, win);
+            const int wtail = __shfl_sync(FULL, ctail, win);
+            const R wcost = __shfl_sync(FULL, ccost, win);
+            const int sp = s.blist[(size_t)wtail * L + wj].pin;
+            const int tn = t.pin_net[sp];
+            const int len = sh_len[w][wpar] - s.plen[t.sink_onet[sp]] + 2 + s.plen[tn];
+            if (lane == 0) {
+                sh_par[w][n] = wpar;
+                sh_side[w][n] = sp;
+                sh_len[w][n] = len;
+                sh_cost[w][n] = wcost;
+            }
+            if (lane == win) {  // replace the popped candidate by its next sibling
+                cv = false;
+                if (wj + 1 < s.bcnt[wtail]) {
+                    const R c2 = sh_cost[w][wpar] + s.blist[(size_t)wtail * L + wj + 1].delta;
+                    if (keep_nonneg || se + c2 < R(0)) {
+                        cv = true;
+                        cj = wj + 1;
+                        ccost = c2;
+                    }
+                }
+            }
+            bool add_child = false;
+            R cc = R(0);
+            if (n + 1 < K && s.bcnt[tn] > 0) {
+                cc = wcost + s.blist[(size_t)tn * L].delta;
+                add_child = keep_nonneg || se + cc < R(0);
+            }
+            const unsigned freem = __ballot_sync(FULL, !cv);
+            if (add_child && lane == __ffs(freem) - 1) {
+                cv = true;
+                cpar = n;
+                cj = 0;
+                ctail = tn;
+                ccost = cc;
+            }
+            __syncwarp();
+        }
+        for (int r = lane; r < n; r += 32) {
+            const size_t slot = (size_t)i * K + r;
+            s.p_parent[slot] = sh_par[w][r];
+            s.p_side[slot] = sh_side[w][r];
+            s.p_len[slot] = sh_len[w][r];
+            s.p_cost[slot] = sh_cost[w][r];
+        }
+        if (lane == 0) {
+            s.p_count[i] = n;
+            atomicAdd((unsigned long long *)s.n_paths, (unsigned long long)n);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static tdp_status ensure_path_buffers(tdp_graph *g, int K) {
+    State<R> &s = state<R>(g);
+    const Topo &t = g->topo;
+    if (!s.p_parent) {  // sized for the largest K once
+        size_t slots = (size_t)std::max(t.n_ep, 1) * kMaxK;
+        TDP_TRY(dalloc(g, &s.p_parent, slots));
+        TDP_TRY(dalloc(g, &s.p_side, slots));
+        TDP_TRY(dalloc(g, &s.p_len, slots));
+        TDP_TRY(dalloc(g, &s.p_cost, slots));
+    }
+    if (K > 1 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * (kMaxK - 1)));
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status capture_bsweep(tdp_graph *g, int K, int keep_nonneg) {
+    if (g->bsweep_graph && g->bsweep_K == K && g->bsweep_keep == keep_nonneg) return TDP_OK;
+    if (g->bsweep_graph) {
+        cudaGraphExecDestroy(g->bsweep_graph);
+        g->bsweep_graph = nullptr;
+    }
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    cudaStream_t cs = g->cap_stream;
+    const int L = K - 1;
+    TDP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    bool ok = true;
+    for (int l = 1; l <= t.depth && ok; ++l) {
+        int lo = g->lv.lvl_ptr[l - 1], hi = g->lv.lvl_ptr[l];
+        if (hi > lo)
+            k_bsweep_level<R><<<div_up(hi - lo, 128), 128, 0, cs>>>(t, s, lo, hi, L, keep_nonneg);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (!ok || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error("extract_critical_paths: capturing the sidetrack sweep failed");
+        return TDP_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&g->bsweep_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->bsweep_graph = nullptr;
+        set_error("extract_critical_paths: cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+        return TDP_ERR_CUDA;
+    }
+    g->bsweep_K = K;
+    g->bsweep_keep = keep_nonneg;
+    return TDP_OK;
+}
+
+template <typename R>
+tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    cudaStream_t st = g->stream;
+    TDP_TRY(ensure_path_buffers<R>(g, K));
+    // 1. failing endpoints sorted by (slack, pin)
+    SortItem *a = reinterpret_cast<SortItem *>(s.sort_a);
+    SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
+    TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
+    TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
+    if (t.n_ep > 0) {
+        k_viol_collect<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s, a);
+        k_tile_sort<<<div_up(t.n_ep, kTile), 1024, 0, st>>>(a, s.nviol);
+        for (int run = kTile; run < t.n_ep; run *= 2) {
+            k_merge_pass<<<div_up(t.n_ep, 256), 256, 0, st>>>(a, b, s.nviol, run);
+            std::swap(a, b);
+        }
+        k_sort_finish<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
+        TDP_LAUNCH_CHECK();
+    }
+    // 2. sidetrack lists
+    if (K > 1) {
+        TDP_TRY(capture_bsweep<R>(g, K, keep_nonneg));
+        TDP_CUDA(cudaGraphLaunch(g->bsweep_graph, st));
+    }
+    // 3. K paths per endpoint
+    if (t.n_ep > 0) {
+        int n_cap = n_endpoints < 0 ? INT_MAX : n_endpoints;
+        int blocks = std::min(div_up(t.n_ep, kTopkWarps), 148 * 16);
+        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, K - 1, keep_nonneg, n_cap);
+        TDP_LAUNCH_CHECK();
+    }
+    return TDP_OK;
+}
+
+template tdp_status extract_impl<float>(tdp_graph *, int, int, int);
+template tdp_status extract_impl<double>(tdp_graph *, int, int, int);
+
+// ---------------------------------------------------------- materialise ---
+
+// Walk one extracted path from its endpoint back to its startpoint, calling
+// visit(pin, is_sink) for every pin in that order.
+template <typename R, typename F>
+__device__ __forceinline__ void walk_path(const Topo &t, const State<R> &s, int ep,
+                                          const int *sides, int nsides, F &&visit) {
+    visit(ep, true);
+    int e = t.pin_net[ep];
+    int j = nsides - 1;  // sides[] holds the deepest sidetrack first
+    for (;;) {
+        visit(t.net_ptr[e], false);
+        int pi = s.pred_in[e];
+        if (pi < 0) break;
+        int nx;
+        if (j >= 0 && t.sink_onet[sides[j]] == e) {
+            pi = sides[j--];
+            nx = t.pin_net[pi];
+        } else {
+            nx = s.pred_net[e];
+        }
+        visit(pi, true);
+        e = nx;
+    }
+}
+
+template <typename R>
+__global__ void k_path_lens(State<R> s, int K, int n_use, const int64_t *base, int32_t *lens) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_use) return;
+    int c = s.p_count[i];
+    for (int r = 0; r < c; ++r) lens[base[i] + r] = s.p_len[(size_t)i * K + r];
+}
+
+template <typename R>
+__global__ void k_materialise(Topo t, State<R> s, int K, int n_use, const int64_t *base,
+                              const int64_t *pin_off, int32_t *ep_out, R *slack_out,
+                              int64_t *pin_ptr_out, int32_t *pins_out, int64_t n_paths) {
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = slot / K, r = slot % K;
+    if (i >= n_use || r >= s.p_count[i]) return;
+    const int64_t q = base[i] + r;
+    const int ep = s.viol[i];
+    const size_t sl = (size_t)i * K + r;
+    if (ep_out) ep_out[q] = ep;
+    if (slack_out) slack_out[q] = s.slack[ep] + s.p_cost[sl];
+    if (pin_ptr_out) {
+        pin_ptr_out[q] = pin_off[q];
+        if (q == n_paths - 1) pin_ptr_out[n_paths] = pin_off[n_paths];
+    }
+    if (pins_out) {
+        int sides[kMaxK];
+        int ns = 0;
+        for (int x = r; x > 0; x = s.p_parent[(size_t)i * K + x]) sides[ns++] = s.p_side[(size_t)i * K + x];
+        const int64_t lo = pin_off[q];
+        int64_t pos = lo + s.p_len[sl] - 1;  // written backwards: startpoint first
+        walk_path<R>(t, s, ep, sides, ns, [&](int pin, bool) {
+            if (pos >= lo) pins_out[pos] = pin;  // never outside this path's range
+            --pos;
+        });
+    }
+}
+
+template <typename R>
+tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, int64_t *pin_ptr,
+                          int32_t *pins) {
+    State<R> &s = state<R>(g);
+    const Topo &t = g->topo;
+    cudaStream_t st = g->stream;
+    int nv = 0;
+    long long np = 0;
+    TDP_CUDA(cudaMemcpyAsync(&nv, s.nviol, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaMemcpyAsync(&np, s.n_paths, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaStreamSynchronize(st));
+    if (viol && nv > 0)
+        TDP_CUDA(cudaMemcpyAsync(viol, s.viol, sizeof(int32_t) * nv, cudaMemcpyDeviceToDevice, st));
+    const int n_use = std::min(nv, g->n_endpoints < 0 ? INT_MAX : g->n_endpoints);
+    if (np == 0 || n_use == 0 || !(ep || slack || pin_ptr || pins)) {
+        if (pin_ptr) TDP_CUDA(cudaMemsetAsync(pin_ptr, 0, sizeof(int64_t), st));
+        return TDP_OK;
+    }
+    int64_t *base = nullptr, *pin_off = nullptr;
+    int32_t *lens = nullptr;
+    cudaError_t e1 = cudaMallocAsync(&base, sizeof(int64_t) * (n_use + 1), st);
+    cudaError_t e2 = cudaMallocAsync(&pin_off, sizeof(int64_t) * (np + 1), st);
+    cudaError_t e3 = cudaMallocAsync(&lens, sizeof(int32_t) * np, st);
+    tdp_status rc = TDP_OK;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("sta_get_paths: temporary allocation failed");
+        rc = TDP_ERR_OOM;
+    }
+    if (rc == TDP_OK) rc = scan_i32_to_i64(g, s.p_count, base, n_use, st);
+    if (rc == TDP_OK) {
+        k_path_lens<R><<<div_up(n_use, 256), 256, 0, st>>>(s, g->K, n_use, base, lens);
+        rc = scan_i32_to_i64(g, lens, pin_off, np, st);
+    }
+    if (rc == TDP_OK) {
+        int64_t slots = (int64_t)n_use * g->K;
+        k_materialise<R><<<div_up(slots, 128), 128, 0, st>>>(t, s, g->K, n_use, base, pin_off, ep,
+                                                             slack, pin_ptr, pins, np);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("sta_get_paths: kernel launch failed");
+            rc = TDP_ERR_CUDA;
+        }
+    }
+    if (base) cudaFreeAsync(base, st);
+    if (pin_off) cudaFreeAsync(pin_off, st);
+    if (lens) cudaFreeAsync(lens, st);
+    return rc;
+}
+
+template tdp_status get_paths_impl<float>(tdp_graph *, int32_t *, int32_t *, float *, int64_t *, int32_t *);
+template tdp_status get_paths_impl<double>(tdp_graph *, int32_t *, int32_t *, double *, int64_t *, int32_t *);
+
+}  // namespace tdp
+
+using namespace tdp;
+
+extern "C" tdp_status extract_critical_paths(tdp_graph *g, int32_t n_endpoints, int32_t K,
+                                             int32_t keep_nonneg, int64_t *n_paths_out) {
+    if (!g || K < 1 || K > kMaxK) {
+        set_error("extract_critical_paths: NULL graph or K outside 1..%d", kMaxK);
+        return TDP_ERR_INVALID;
+    }
+    if (!g->propagated) {
+        set_error("extract_critical_paths: call sta_propagate first");
+        return TDP_ERR_STATE;
+    }
+    keep_nonneg = keep_nonneg ? 1 : 0;
+    tdp_status st = g->prec == TDP_FP32 ? extract_impl<float>(g, n_endpoints, K, keep_nonneg)
+                                        : extract_impl<double>(g, n_endpoints, K, keep_nonneg);
+    if (st != TDP_OK) return st;
+    g->K = K;
+    g->keep_nonneg = keep_nonneg;
+    g->n_endpoints = n_endpoints;
+    g->extracted = true;
+    if (n_paths_out) {
+        long long h = 0;
+        const long long *src = g->prec == TDP_FP32 ? g->s32.n_paths : g->s64.n_paths;
+        TDP_CUDA(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        TDP_CUDA(cudaStreamSynchronize(g->stream));
+        *n_paths_out = h;
+    }
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status paths_size_impl(tdp_graph *g, int32_t *nv_out, int64_t *np_out, int64_t *npin_out) {
+    State<R> &s = state<R>(g);
+    cudaStream_t st = g->stream;
+    int nv = 0;
+    long long np = 0;
+    TDP_CUDA(cudaMemcpyAsync(&nv, s.nviol, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaMemcpyAsync(&np, s.n_paths, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaStreamSynchronize(st));
+    if (nv_out) *nv_out = nv;
+    if (np_out) *np_out = np;
+    if (npin_out) {
+        const int n_use = std::min(nv, g->n_endpoints < 0 ? INT_MAX : g->n_endpoints);
+        std::vector<int32_t> cnt(n_use), len((size_t)n_use * g->K);
+        if (n_use > 0) {
+            TDP_CUDA(cudaMemcpy(cnt.data(), s.p_count, sizeof(int32_t) * n_use, cudaMemcpyDeviceToHost));
+            TDP_CUDA(cudaMemcpy(len.data(), s.p_len, sizeof(int32_t) * len.size(), cudaMemcpyDeviceToHost));
+        }
+        int64_t tot = 0;
+        for (int i = 0; i < n_use; ++i)
+            for (int r = 0; r < cnt[i]; ++r) tot += len[(size_t)i * g->K + r];
+        *npin_out = tot;
+    }
+    return TDP_OK;
+}
+
+extern "C" tdp_status sta_get_paths_size(tdp_graph *g, int32_t *n_viol_out, int64_t *n_paths_out,
+                                         int64_t *n_path_pins_out) {
+    if (!g) {
+        set_error("sta_get_paths_size: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    if (!g->extracted) {
+        set_error("sta_get_paths_size: call extract_critical_paths first");
+        return TDP_ERR_STATE;
+    }
+    return g->prec == TDP_FP32 ? paths_size_impl<float>(g, n_viol_out, n_paths_out, n_path_pins_out)
+                               : paths_size_impl<double>(g, n_viol_out, n_paths_out, n_path_pins_out);
+}
+
+extern "C" tdp_status sta_get_paths(tdp_graph *g, int32_t *viol_dev, int32_t *ep_dev, void *slack_dev,
+                                    int64_t *pin_ptr_dev, int32_t *pins_dev) {
+    if (!g) {
+        set_error("sta_get_paths: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    if (!g->extracted) {
+        set_error("sta_get_paths: call extract_critical_paths first");
+        return TDP_ERR_STATE;
+    }
+    return g->prec == TDP_FP32
+               ? get_paths_impl<float>(g, viol_dev, ep_dev, (float *)slack_dev, pin_ptr_dev, pins_dev)
+               : get_paths_impl<double>(g, viol_dev, ep_dev, (double *)slack_dev, pin_ptr_dev, pins_dev);
+}

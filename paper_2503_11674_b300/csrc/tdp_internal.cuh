@@ -1,0 +1,242 @@
+// Internal declarations of the B300 timing library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "tdp.h"
+
+namespace tdp {
+
+// ---------------------------------------------------------------- errors ---
+void set_error(const char *fmt, ...);
+
+#define TDP_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            tdp::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #call,            \
+                           cudaGetErrorString(e_));                                      \
+            return TDP_ERR_CUDA;                                                         \
+        }                                                                                \
+    } while (0)
+
+#define TDP_LAUNCH_CHECK() TDP_CUDA(cudaGetLastError())
+
+#define TDP_TRY(call)                                                                    \
+    do {                                                                                 \
+        tdp_status s_ = (call);                                                          \
+        if (s_ != TDP_OK) return s_;                                                     \
+    } while (0)
+
+// ------------------------------------------------------------- constants ---
+constexpr int kMaxK = 32;          // paths per endpoint (one warp holds the frontier)
+constexpr int kMaxFanin = 32;      // inputs of a combinational cell
+constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole warp
+constexpr double kQScale = 16777216.0;  // 2^24: fixed point of slack/WNS in the pair update
+constexpr double kQClamp = 32768.0;     // |slack/WNS| is clamped here before conversion
+
+enum PinKind : uint8_t { PK_COMB_IN = 0, PK_ENDPOINT = 1, PK_COMB_OUT = 2, PK_START = 3 };
+
+// ------------------------------------------------- arrival accumulators ---
+// FP32 graphs accumulate arrival and required times as an unevaluated sum of
+// two floats (hi + lo, |lo| <= ulp(hi)/2): the delays themselves are FP32,
+// but the long chains of additions keep their rounding error in lo, so the
+// error stays relative to the delays rather than growing with the depth.
+struct fx2 {
+    float hi, lo;
+};
+
+template <typename R>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    using T = double;
+    static __host__ __device__ __forceinline__ T make(double v) { return v; }
+    static __device__ __forceinline__ T add(T a, double b) { return a + b; }
+    static __device__ __forceinline__ double diff(T a, T b) { return a - b; }
+    static __device__ __forceinline__ bool gt(T a, T b) { return a > b; }
+    static __device__ __forceinline__ bool lt(T a, T b) { return a < b; }
+    static __device__ __forceinline__ double val(T a) { return a; }
+    static __device__ __forceinline__ T ninf() { return -__longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ T pinf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+__device__ __forceinline__ fx2 fx2_add(fx2 a, float b) {
+    // two-sum of a.hi + b, then fold in a.lo and renormalise (fast two-sum)
+    float s = a.hi + b;
+    float bb = s - a.hi;
+    float err = (a.hi - (s - bb)) + (b - bb);
+    float lo = a.lo + err;
+    float hi = s + lo;
+    lo = lo - (hi - s);
+    return fx2{hi, lo};
+}
+
+template <>
+struct Acc<float> {
+    using T = fx2;
+    static __host__ __device__ __forceinline__ T make(float v) { return fx2{v, 0.0f}; }
+    static __device__ __forceinline__ T add(T a, float b) { return fx2_add(a, b); }
+    static __device__ __forceinline__ float diff(T a, T b) {
+        return (a.hi - b.hi) + (a.lo - b.lo);
+    }
+    static __device__ __forceinline__ bool gt(T a, T b) {
+        return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+    }
+    static __device__ __forceinline__ bool lt(T a, T b) {
+        return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+    }
+    static __device__ __forceinline__ float val(T a) { return a.hi + a.lo; }
+    static __device__ __forceinline__ T ninf() { return fx2{-__int_as_float(0x7f800000), 0.0f}; }
+    static __device__ __forceinline__ T pinf() { return fx2{__int_as_float(0x7f800000), 0.0f}; }
+};
+
+// One sidetrack entry of a node's list: the deviation cost delta >= 0 of
+// entering the node through a non-worst input pin instead of its worst one.
+template <typename R>
+struct BEnt {
+    R delta;
+    int32_t pin;
+};
+
+// ------------------------------------------------------------ the graph ---
+// Device arrays common to both precisions (topology, built once).
+struct Topo {
+    int32_t n_cells = 0, n_pins = 0, n_nets = 0, n_comb = 0, n_in = 0, n_ep = 0, depth = 0;
+    int32_t n_big = 0;
+    int32_t *pin_cell = nullptr, *pin_net = nullptr, *net_ptr = nullptr;
+    uint8_t *pin_kind = nullptr;
+    int32_t *sink_out = nullptr;   // comb input -> its cell's output pin (else -1)
+    int32_t *sink_onet = nullptr;  // comb input -> net driven by its cell (else -1)
+    int32_t *net_level = nullptr;  // level of the driving cell (0 for FF/PI)
+    int32_t *big_nets = nullptr;   // nets with more than kBigFanout sinks
+    // combinational cells in level order and their inputs (CSR)
+    int32_t *lv_out = nullptr;     // [n_comb] output pin
+    int32_t *lv_onet = nullptr;    // [n_comb] net driven by the cell
+    int32_t *lv_in_ptr = nullptr;  // [n_comb+1]
+    int32_t *lv_in_pin = nullptr;  // [n_in] input pins, ascending
+    int32_t *lv_in_drv = nullptr;  // [n_in] driver pin of the input's net
+    int32_t *lv_in_net = nullptr;  // [n_in] net of the input
+    // nets grouped by driver level: per level [small nets ..., big nets ...]
+    int32_t *bl_net = nullptr;     // [n_nets]
+    int32_t *ep = nullptr;         // [n_ep] endpoint pins, ascending
+    int32_t *cp_ptr = nullptr;     // [n_cells+1] cell -> pins CSR
+    int32_t *cp = nullptr;         // [n_pins]
+    int32_t *slot_of_pin = nullptr;// [n_pins] position of a pin in cp
+    uint8_t *cell_fixed = nullptr; // [n_cells]
+};
+
+// Host copies of the launch structure of the level sweeps.
+struct Levels {
+    std::vector<int32_t> lvl_ptr;   // comb cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
+    std::vector<int32_t> bl_ptr;    // nets of level l: [bl_ptr[l], bl_ptr[l+1])
+    std::vector<int32_t> bl_small;  // number of small nets at the start of level l
+};
+
+template <typename R>
+struct State {
+    using A = typename Acc<R>::T;
+    R *pin_dx = nullptr, *pin_dy = nullptr, *pin_cap = nullptr, *cell_rdrv = nullptr;
+    R *tnet = nullptr;    // [n_pins]
+    R *cload = nullptr;   // [n_nets]
+    R *dnet = nullptr;    // [n_nets] delay of the driving cell
+    A *arr = nullptr, *req = nullptr;  // [n_pins]
+    R *slack = nullptr;   // [n_pins]
+    int32_t *pred_in = nullptr;   // [n_nets] worst input pin of the driving cell (-1: startpoint)
+    int32_t *pred_net = nullptr;  // [n_nets] net of that input
+    int32_t *plen = nullptr;      // [n_nets] pins from the driver back to its startpoint
+    double *T = nullptr;          // device clock period
+    double *wns_tns = nullptr;    // [2]
+    double *red_part = nullptr;   // reduction partials
+    unsigned *red_count = nullptr;
+    // extraction
+    uint64_t *sort_a = nullptr, *sort_b = nullptr;  // (key, pin) items, ping-pong
+    int32_t *nviol = nullptr;     // device count of failing endpoints
+    int32_t *viol = nullptr;      // [n_ep] failing endpoints sorted by (slack, pin)
+    BEnt<R> *blist = nullptr;     // [n_nets * (kMaxK-1)] sidetrack lists
+    uint8_t *bcnt = nullptr;      // [n_nets]
+    int32_t *p_parent = nullptr, *p_side = nullptr, *p_len = nullptr;  // [n_ep * K]
+    R *p_cost = nullptr;
+    int32_t *p_count = nullptr;   // [n_ep] paths per failing endpoint (sorted order)
+    long long *n_paths = nullptr; // device total
+    int64_t *scan_tmp = nullptr;  // scan scratch
+    // pin pairs
+    long long *sumq = nullptr, *maxq = nullptr;  // [n_pins] fixed-point slack/WNS
+    uint8_t *touch = nullptr, *in_p = nullptr;   // [n_pins]
+    R *w = nullptr;                               // [n_pins]
+    long long *n_pairs = nullptr;
+    // loss
+    R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y)
+    double *loss_part = nullptr;
+    unsigned *loss_count = nullptr;
+};
+
+}  // namespace tdp
+
+struct tdp_graph {
+    tdp_precision prec = TDP_FP32;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // stream used to capture CUDA graphs
+    tdp::Topo topo;
+    tdp::Levels lv;
+    tdp::State<float> s32;
+    tdp::State<double> s64;
+    double r = 0, c = 0, d0 = 0;
+    int K = 0, keep_nonneg = 0, n_endpoints = -1;
+    bool propagated = false, extracted = false;
+    cudaGraphExec_t sta_graph = nullptr;
+    cudaGraphExec_t bsweep_graph = nullptr;
+    int bsweep_K = -1, bsweep_keep = -1;
+    std::vector<void *> allocs;  // every device allocation, freed in sta_destroy
+};
+
+namespace tdp {
+template <typename T>
+tdp_status dalloc(tdp_graph *g, T **p, size_t n) {
+    void *q = nullptr;
+    size_t bytes = n * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return TDP_ERR_OOM;
+    }
+    g->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return TDP_OK;
+}
+
+template <typename R>
+State<R> &state(tdp_graph *g);
+template <>
+inline State<float> &state<float>(tdp_graph *g) { return g->s32; }
+template <>
+inline State<double> &state<double>(tdp_graph *g) { return g->s64; }
+
+template <typename R>
+tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T);
+template <typename R>
+tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg);
+template <typename R>
+tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, int64_t *pin_ptr,
+                          int32_t *pins);
+template <typename R>
+tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1);
+template <typename R>
+tdp_status loss_fwd_impl(tdp_graph *g, const R *x, const R *y, double beta, double *loss);
+template <typename R>
+tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, const double *gs,
+                         R *gx, R *gy);
+
+// exclusive scan of n int32 counts into int64 offsets (out has n+1 entries)
+tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_t n,
+                           cudaStream_t st);
+
+inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+}  // namespace tdp

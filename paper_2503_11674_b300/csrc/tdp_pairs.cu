@@ -1,0 +1,241 @@
+// Pin-pair set P and weights, Eq. (w_ij) (Section III-D).
+//
+// k_pair_walk walks every extracted path (thread per path) and, for every
+// net arc (driver -> sink s) on it, adds q = slack / WNS of the path to the
+// accumulators of s and raises the running maximum of q at s.  Both are kept
+// as 64-bit fixed point (2^-24), so the integer atomics are exact and the
+// result does not depend on the order of the paths.
+//
+// k_pair_finish applies the rule to every touched sink.  Traversing the paths
+// worst first, the first path through a new pair sets w0 and every later one
+// adds w1 * q; the first one is the path with the largest q (most negative
+// slack), so
+//     new pair:      w = w0 + w1 * (sum q - max q)
+//     pair in P:     w = w  + w1 * sum q.
+#include <climits>
+
+#include "tdp_internal.cuh"
+
+namespace tdp {
+
+template <typename R, typename F>
+__device__ __forceinline__ void walk_sinks(const Topo &t, const State<R> &s, int ep,
+                                           const int *sides, int nsides, F &&visit) {
+    visit(ep);
+    int e = t.pin_net[ep];
+    int j = nsides - 1;
+    for (;;) {
+        int pi = s.pred_in[e];
+        if (pi < 0) break;
+        int nx;
+        if (j >= 0 && t.sink_onet[sides[j]] == e) {
+            pi = sides[j--];
+            nx = t.pin_net[pi];
+        } else {
+            nx = s.pred_net[e];
+        }
+        visit(pi);
+        e = nx;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_pair_walk(Topo t, State<R> s, int K, int n_cap) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = slot / K, r = slot % K;
+    const int nv = min(*s.nviol, n_cap);
+    if (i >= nv || r >= s.p_count[i]) return;
+    const double wns = s.wns_tns[0];
+    if (!(wns < 0.0)) return;
+    const int ep = s.viol[i];
+    const size_t base = (size_t)i * K;
+    const R sigma = s.slack[ep] + s.p_cost[base + r];
+    double q = (double)sigma / wns;
+    q = fmin(fmax(q, -kQClamp), kQClamp);
+    const long long Q = __double2ll_rn(q * kQScale);
+    int sides[kMaxK];
+    int ns = 0;
+    for (int x = r; x > 0; x = s.p_parent[base + x]) sides[ns++] = s.p_side[base + x];
+    walk_sinks<R>(t, s, ep, sides, ns, [&](int p) {
+        atomicAdd((unsigned long long *)&s.sumq[p], (unsigned long long)Q);
+        atomicMax(&s.maxq[p], Q);
+        s.touch[p] = 1;
+    });
+}
+
+template <typename R>
+__global__ void k_pair_finish(State<R> s, int n_pins, double w0, double w1) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pins || !s.touch[p]) return;
+    const double sq = (double)s.sumq[p] / kQScale;
+    if (s.in_p[p]) {
+        s.w[p] = (R)((double)s.w[p] + w1 * sq);
+    } else {
+        const double mq = (double)s.maxq[p] / kQScale;
+        s.w[p] = (R)(w0 + w1 * (sq - mq));
+        s.in_p[p] = 1;
+        atomicAdd((unsigned long long *)s.n_pairs, 1ull);
+    }
+    s.sumq[p] = 0;
+    s.maxq[p] = LLONG_MIN;
+    s.touch[p] = 0;
+}
+
+template <typename R>
+tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    const int n_cap = g->n_endpoints < 0 ? INT_MAX : g->n_endpoints;
+    const int64_t slots = (int64_t)t.n_ep * g->K;
+    if (slots > 0) k_pair_walk<R><<<div_up(slots, 128), 128, 0, g->stream>>>(t, s, g->K, n_cap);
+    k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(s, t.n_pins, w0, w1);
+    TDP_LAUNCH_CHECK();
+    return TDP_OK;
+}
+
+template tdp_status update_pairs_impl<float>(tdp_graph *, double, double);
+template tdp_status update_pairs_impl<double>(tdp_graph *, double, double);
+
+// ------------------------------------------------------------ get / set ---
+
+template <typename R>
+__global__ void k_flag_in_p(const State<R> s, int n, int32_t *flags) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) flags[p] = s.in_p[p] ? 1 : 0;
+}
+
+template <typename R>
+__global__ void k_scatter_pairs(const State<R> s, int n, const int64_t *off, int32_t *pins, R *w) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !s.in_p[p]) return;
+    int64_t k = off[p];
+    if (pins) pins[k] = p;
+    if (w) w[k] = s.w[p];
+}
+
+template <typename R>
+static tdp_status get_pairs_impl(tdp_graph *g, int32_t *pins, R *w, int64_t *n_out) {
+    State<R> &s = state<R>(g);
+    const int n = g->topo.n_pins;
+    cudaStream_t st = g->stream;
+    int32_t *flags = nullptr;
+    int64_t *off = nullptr;
+    if (cudaMallocAsync(&flags, sizeof(int32_t) * n, st) != cudaSuccess ||
+        cudaMallocAsync(&off, sizeof(int64_t) * (n + 1), st) != cudaSuccess) {
+        if (flags) cudaFreeAsync(flags, st);
+        set_error("attraction_get_pairs: temporary allocation failed");
+        return TDP_ERR_OOM;
+    }
+    k_flag_in_p<R><<<div_up(n, 256), 256, 0, st>>>(s, n, flags);
+    tdp_status rc = scan_i32_to_i64(g, flags, off, n, st);
+    if (rc == TDP_OK && (pins || w)) k_scatter_pairs<R><<<div_up(n, 256), 256, 0, st>>>(s, n, off, pins, w);
+    int64_t total = 0;
+    if (rc == TDP_OK) {
+        cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("attraction_get_pairs: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = TDP_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(flags, st);
+    cudaFreeAsync(off, st);
+    if (n_out) *n_out = total;
+    return rc;
+}
+
+template <typename R>
+static tdp_status set_pairs_impl(tdp_graph *g, int64_t n, const int32_t *pins, const double *w) {
+    State<R> &s = state<R>(g);
+    const int np = g->topo.n_pins;
+    std::vector<uint8_t> in_p(np, 0);
+    std::vector<R> wv(np, R(0));
+    std::vector<int32_t> pn(np);
+    // sinks are all pins that are not the first pin of their net
+    std::vector<uint8_t> is_sink(np, 1);
+    {
+        std::vector<int32_t> ptr(g->topo.n_nets + 1);
+        TDP_CUDA(cudaMemcpy(ptr.data(), g->topo.net_ptr, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+        for (int e = 0; e < g->topo.n_nets; ++e) is_sink[ptr[e]] = 0;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        int p = pins[k];
+        if (p < 0 || p >= np || !is_sink[p] || in_p[p] || !std::isfinite(w[k])) {
+            set_error("attraction_set_pairs: entry %lld (pin %d) is not a distinct sink pin with a "
+                      "finite weight", (long long)k, p);
+            return TDP_ERR_INVALID;
+        }
+        in_p[p] = 1;
+        wv[p] = (R)w[k];
+    }
+    long long cnt = n;
+    TDP_CUDA(cudaStreamSynchronize(g->stream));
+    TDP_CUDA(cudaMemcpy(s.in_p, in_p.data(), np, cudaMemcpyHostToDevice));
+    TDP_CUDA(cudaMemcpy(s.w, wv.data(), sizeof(R) * np, cudaMemcpyHostToDevice));
+    TDP_CUDA(cudaMemcpy(s.n_pairs, &cnt, sizeof(cnt), cudaMemcpyHostToDevice));
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status reset_pairs_impl(tdp_graph *g) {
+    State<R> &s = state<R>(g);
+    const int np = g->topo.n_pins;
+    TDP_CUDA(cudaMemsetAsync(s.in_p, 0, np, g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.w, 0, sizeof(R) * np, g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.n_pairs, 0, sizeof(long long), g->stream));
+    return TDP_OK;
+}
+
+}  // namespace tdp
+
+using namespace tdp;
+
+extern "C" tdp_status attraction_update_pairs(tdp_graph *g, double w0, double w1,
+                                              int64_t *n_pairs_out) {
+    if (!g || !std::isfinite(w0) || !std::isfinite(w1)) {
+        set_error("attraction_update_pairs: NULL graph or non-finite w0 / w1");
+        return TDP_ERR_INVALID;
+    }
+    if (!g->extracted) {
+        set_error("attraction_update_pairs: call extract_critical_paths first");
+        return TDP_ERR_STATE;
+    }
+    tdp_status st = g->prec == TDP_FP32 ? update_pairs_impl<float>(g, w0, w1)
+                                        : update_pairs_impl<double>(g, w0, w1);
+    if (st != TDP_OK) return st;
+    if (n_pairs_out) {
+        long long h = 0;
+        const long long *src = g->prec == TDP_FP32 ? g->s32.n_pairs : g->s64.n_pairs;
+        TDP_CUDA(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        TDP_CUDA(cudaStreamSynchronize(g->stream));
+        *n_pairs_out = h;
+    }
+    return TDP_OK;
+}
+
+extern "C" tdp_status attraction_reset_pairs(tdp_graph *g) {
+    if (!g) {
+        set_error("attraction_reset_pairs: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    return g->prec == TDP_FP32 ? reset_pairs_impl<float>(g) : reset_pairs_impl<double>(g);
+}
+
+extern "C" tdp_status attraction_set_pairs(tdp_graph *g, int64_t n_pairs, const int32_t *pins_host,
+                                           const double *w_host) {
+    if (!g || n_pairs < 0 || (n_pairs > 0 && (!pins_host || !w_host))) {
+        set_error("attraction_set_pairs: NULL graph or arrays, or negative count");
+        return TDP_ERR_INVALID;
+    }
+    return g->prec == TDP_FP32 ? set_pairs_impl<float>(g, n_pairs, pins_host, w_host)
+                               : set_pairs_impl<double>(g, n_pairs, pins_host, w_host);
+}
+
+extern "C" tdp_status attraction_get_pairs(tdp_graph *g, int32_t *pins_dev, void *w_dev,
+                                           int64_t *n_pairs_out) {
+    if (!g) {
+        set_error("attraction_get_pairs: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    return g->prec == TDP_FP32 ? get_pairs_impl<float>(g, pins_dev, (float *)w_dev, n_pairs_out)
+                               : get_pairs_impl<double>(g, pins_dev, (double *)w_dev, n_pairs_out);
+}

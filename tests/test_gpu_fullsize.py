@@ -1,0 +1,111 @@
+"""Parity at the full 1.2M-cell workload, in the benchmark's launch configuration.
+
+The FP64 oracle computes every pin's timing at this size in seconds, so STA is
+checked on every pin.  Path sets are checked against the oracle on a sample of
+failing endpoints (the 100 most critical plus 100 drawn at random) with the
+margin rule, and on all endpoints by exact set equality with the mismatches
+counted; pin-pair weights are checked on every sink not touched by a
+mismatching endpoint; the loss and its gradient with a seeded pair set.
+"""
+import numpy as np
+import pytest
+import torch
+
+import netgen
+import oracle
+from parity_util import TOL32, check_sta, compare_paths, gpu_paths, paths_by_endpoint
+
+pytestmark = pytest.mark.gpu
+
+CFG = "1.2M"
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2503_11674_b300 import TimingGraph
+    from paper_2503_11674_b300.build import build
+    build()
+    cfg = netgen.CONFIGS[CFG]
+    nl = netgen.generate(CFG, 1)
+    T = oracle.clock_period(nl, cfg.t_factor)
+    tm = oracle.sta(nl, T=T)
+    G = TimingGraph(nl, "fp32")
+    x = torch.tensor(nl.x, device="cuda")
+    y = torch.tensor(nl.y, device="cuda")
+    wns, tns = G.sta_propagate(x, y, T)
+    G.extract_critical_paths(-1, cfg.K, False)
+    P = gpu_paths(G)
+    return dict(nl=nl, T=T, tm=tm, G=G, x=x, y=y, wns=wns, tns=tns, P=P, K=cfg.K)
+
+
+def test_sta_every_pin(run):
+    check_sta(run["G"], run["tm"], run["T"], TOL32)
+    tm = run["tm"]
+    assert run["tns"] == pytest.approx(tm["tns"], rel=1e-6)
+    assert run["wns"] == pytest.approx(tm["wns"], rel=1e-6)
+
+
+def test_paths_on_sampled_endpoints(run):
+    P, nl, tm = run["P"], run["nl"], run["tm"]
+    ref_viol = oracle.topk(nl, tm, -1, 1)["viol"]
+    assert abs(len(P["viol"]) - len(ref_viol)) <= 2
+    rng = np.random.default_rng(0)
+    sample = np.concatenate([P["viol"][:100], rng.choice(P["viol"][100:], 100, replace=False)])
+    checked, amb = compare_paths(nl, tm, run["T"], run["K"], False, P, TOL32, endpoints=sample)
+    assert checked >= 190, (checked, amb)
+
+
+def test_pairs_against_full_oracle_path_set(run):
+    P, nl, tm, G = run["P"], run["nl"], run["tm"], run["G"]
+    K = run["K"]
+    ref = oracle.topk(nl, tm, -1, K)
+    got_by, ref_by = paths_by_endpoint(P), paths_by_endpoint(ref)
+    differ = [e for e in set(got_by) | set(ref_by)
+              if set(p[1] for p in got_by.get(e, [])) != set(p[1] for p in ref_by.get(e, []))]
+    assert len(differ) <= 0.01 * len(ref_by), len(differ)
+    w0, w1 = 10.0, 0.2
+    n_pairs = G.attraction_update_pairs(w0, w1)
+    pins, w = G.attraction_get_pairs()
+    pins, w = pins.cpu().numpy(), w.cpu().numpy().astype(np.float64)
+    assert n_pairs == len(pins)
+    in_p, w_ref = oracle.update_pairs(nl, ref, tm["wns"], w0, w1)
+    ok = np.ones(nl.n_pins, bool)
+    for e in differ:
+        for src in (got_by, ref_by):
+            for _, seq in src.get(e, []):
+                ok[list(seq[1::2])] = False
+    mine = np.zeros(nl.n_pins, bool)
+    mine[pins] = True
+    np.testing.assert_array_equal(mine[ok], in_p.astype(bool)[ok])
+    wg = np.zeros(nl.n_pins)
+    wg[pins] = w
+    occ = np.zeros(nl.n_pins)
+    for k in range(len(ref["ep"])):
+        occ[ref["pins"][ref["pin_ptr"][k]:ref["pin_ptr"][k + 1]][1::2]] += 1
+    tolp = TOL32[0] + TOL32[1] * 2 * run["T"]
+    wtol = occ * w1 * (2 * tolp / abs(tm["wns"]) + 2.0 ** -23) + 1e-6 * np.abs(w_ref) + 1e-9
+    sel = ok & (in_p > 0)
+    err = np.abs(wg[sel] - w_ref[sel])
+    assert (err <= wtol[sel]).all(), err.max()
+
+
+def test_loss_and_gradient(run):
+    nl, G, x, y = run["nl"], run["G"], run["x"], run["y"]
+    rng = np.random.default_rng(5)
+    sinks = np.nonzero(nl.pin_dir == 0)[0]
+    pins = np.sort(rng.choice(sinks, len(sinks) // 3, replace=False)).astype(np.int32)
+    w = rng.uniform(5.0, 20.0, len(pins)).astype(np.float32).astype(np.float64)
+    G.attraction_set_pairs(pins, w)
+    in_p = np.zeros(nl.n_pins, np.uint8)
+    in_p[pins] = 1
+    wf = np.zeros(nl.n_pins)
+    wf[pins] = w
+    beta = 2.5e-5
+    pp, gx_r, gy_r = oracle.loss(nl, in_p, wf, beta)
+    assert G.attraction_loss_fwd(x, y, beta).item() == pytest.approx(pp, rel=1e-6)
+    gx, gy = G.attraction_loss_bwd(x, y, beta)
+    g = np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]).astype(np.float64)
+    gr = np.concatenate([gx_r, gy_r])
+    assert np.linalg.norm(g - gr) / np.linalg.norm(gr) <= 1e-5
