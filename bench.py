@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Timing iterations per second of the timing-driven placement hot path.
+
+One step = one timing iteration of the method on one synthetic netlist:
+    sta_propagate -> extract_critical_paths (report_timing_endpoint(all, K))
+    -> attraction_update_pairs (Eq. w_ij) -> attraction_loss_fwd -> _bwd
+at a new placement every step (seeded Gaussian moves, sigma = 2 um).  The
+workload is the 1.2M-cell netlist (1.3M nets, ~4.2M pins, depth 80, 0.5% nets
+of fanout 64-1000, clock at 0.85x the largest arrival, K = 16).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs as independent replicas (one netlist per rank, no collective in
+the data path); launch with torch.distributed.run.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "STA+path-extract+attraction fwd/bwd iters/sec at 1.2M cells; % HBM roofline"
+UNIT = "iter/s"
+W0, W1, BETA, SIGMA = 10.0, 0.2, 2.5e-5, 2.0
+N_POS_SETS = 32            # distinct placements cycled through by the timed loop
+ROOFLINE_KERNEL = "pair_walk"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="1.2M")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--roofline-kernel", default=ROOFLINE_KERNEL)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stages", action="store_true", help="also time each entry point (diagnostic)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers --
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    """Max over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL,
+                start_new_session=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        try:
+            os.killpg(self.proc.pid, signal.SIGTERM)
+        except OSError:
+            pass
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_desc(cfg, nl):
+    st = nl.stats()
+    return {"workload": f"{cfg.name}: {st['cells']:,} cells ({cfg.n_ff:,} FF, {st['pi']:,} PI, {st['po']:,} PO), "
+                        f"{st['nets']:,} nets, {st['pins']:,} pins, depth {cfg.depth}, K={cfg.K}, "
+                        f"clock {cfg.t_factor}x max arrival",
+            "cells": st["cells"], "nets": st["nets"], "pins": st["pins"], "depth": cfg.depth, "K": cfg.K,
+            "max_fanout": st["max_fanout"], "t_factor": cfg.t_factor}
+
+
+# ------------------------------------------------------ algorithmic bytes --
+
+def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
+    """Compulsory DRAM bytes of one launch of `kernel` (FP32 graph, 4-byte indices).
+
+    Each array element a kernel must read or write is counted once; gathers
+    of shared data (cell positions, driver arrival) are counted once per
+    element of the gathered array.
+    """
+    import numpy as np
+    C, P, N = nl.n_cells, nl.n_pins, nl.n_nets
+    S = P - N
+    n_start = int(np.isin(nl.cell_type[nl.pin_cell[nl.net_ptr[:-1]]], (1, 2)).sum())
+    if kernel == "net_rc":
+        return (4 * (N + 1) + 4 * P + 8 * P + 4 * S + 8 * C + 4 * N + N
+                + 4 * S + 4 * N + 4 * N + 8 * n_start)
+    if kernel == "pair_walk":
+        occ = g_info["path_pins"] / 2.0                 # sink pins on paths = net arcs
+        paths = g_info["paths"]
+        # per net arc: pred_in + pred_net of the driver (8), two 8-byte
+        # read-modify-writes (32) and the touch flag (1); per path: its
+        # endpoint, slack, cost, count and parent / sidetrack records (24)
+        return occ * 41.0 + paths * 24.0
+    if kernel == "pp_fwd":
+        nP = g_info["pairs"]
+        return 4 * (N + 1) + S + 16 * nP + 12 * N + 8 * C
+    if kernel == "pp_bwd_net":
+        nP = g_info["pairs"]
+        return 4 * (N + 1) + S + 16 * nP + 12 * N + 8 * C + 12 * P
+    if kernel == "pp_bwd_cell":
+        return 4 * (C + 1) + 8 * P + C + 8 * C
+    if kernel == "topk":
+        return g_info["viol"] * (4 + 4 + 4 + 4 + 1) + g_info["paths"] * (16 + 8 + 16)
+    raise ValueError(kernel)
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import netgen
+    from paper_2503_11674_b300 import TimingGraph
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = netgen.CONFIGS[args.config]
+    seed = args.seed + rank                       # independent replica per rank
+    nl = netgen.generate(cfg, seed)
+    G = TimingGraph(nl, "fp32", device=dev)
+    n = nl.n_cells
+
+    # placements: a seeded random walk of the movable cells, resident on the device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + seed)
+    mv = torch.tensor(nl.cell_fixed == 0, device=dev)
+    xs = torch.empty((N_POS_SETS, n), dtype=torch.float32, device=dev)
+    ys = torch.empty((N_POS_SETS, n), dtype=torch.float32, device=dev)
+    x = torch.tensor(nl.x, device=dev)
+    y = torch.tensor(nl.y, device=dev)
+    for k in range(N_POS_SETS):
+        x = torch.where(mv, (x + SIGMA * torch.randn(n, generator=gen, device=dev)).clamp(0, netgen.DIE_UM), x)
+        y = torch.where(mv, (y + SIGMA * torch.randn(n, generator=gen, device=dev)).clamp(0, netgen.DIE_UM), y)
+        xs[k].copy_(x)
+        ys[k].copy_(y)
+    # clock period from this placement: with T = 0 every endpoint fails and
+    # WNS = -(largest endpoint arrival)
+    wns0, _ = G.sta_propagate(xs[0], ys[0], 0.0)
+    T = cfg.t_factor * (-wns0)
+    K = cfg.K
+    loss_buf = torch.zeros((), dtype=torch.float64, device=dev)
+    gx = torch.empty(n, dtype=torch.float32, device=dev)
+    gy = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def step(k):
+        xk, yk = xs[k % N_POS_SETS], ys[k % N_POS_SETS]
+        G.sta_propagate(xk, yk, T, sync=False)
+        G.extract_critical_paths(-1, K, False, sync=False)
+        G.attraction_update_pairs(W0, W1, sync=False)
+        G.attraction_loss_fwd(xk, yk, BETA, out=loss_buf)
+        G.attraction_loss_bwd(xk, yk, BETA, gx=gx, gy=gy)
+
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+
+    # sizes of the per-step work (for the roofline units), from the last warm-up step
+    n_viol, n_paths, n_path_pins = G.sta_get_paths_size()
+    info = {"viol": n_viol, "paths": n_paths, "path_pins": n_path_pins}
+
+    # ------------------------------------------------ device-timed region --
+    G.tdp_profile_kernel(args.roofline_kernel)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = G.tdp_get_launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    launches = G.tdp_get_launch_count() - launches0
+    clk = clocks.stop()
+    prof_n, prof_ms = G.tdp_profile_read()
+    G.tdp_profile_kernel(None)
+    ms = reduce_max(ms_local, world, dev)
+    value = world * args.steps / (ms / 1000.0)
+    n_pairs = G.attraction_get_pairs()[0].numel()
+    info["pairs"] = n_pairs
+    wns, tns = G.sta_propagate(xs[0], ys[0], T)
+
+    # ------------------------------------- end to end through host buffers --
+    xh = torch.empty((N_POS_SETS, n), dtype=torch.float32, pin_memory=True)
+    yh = torch.empty((N_POS_SETS, n), dtype=torch.float32, pin_memory=True)
+    xh.copy_(xs)
+    yh.copy_(ys)
+    xd = torch.empty(n, dtype=torch.float32, device=dev)
+    yd = torch.empty(n, dtype=torch.float32, device=dev)
+    gxh = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    gyh = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    lossh = torch.empty((), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 100))
+
+    def e2e_step(k):
+        xd.copy_(xh[k % N_POS_SETS], non_blocking=True)
+        yd.copy_(yh[k % N_POS_SETS], non_blocking=True)
+        G.sta_propagate(xd, yd, T)                     # WNS / TNS to the host
+        G.extract_critical_paths(-1, K, False, sync=False)
+        G.attraction_update_pairs(W0, W1, sync=False)
+        G.attraction_loss_fwd(xd, yd, BETA, out=loss_buf)
+        G.attraction_loss_bwd(xd, yd, BETA, gx=gx, gy=gy)
+        gxh.copy_(gx, non_blocking=True)
+        gyh.copy_(gy, non_blocking=True)
+        lossh.copy_(loss_buf, non_blocking=True)
+        stream.synchronize()
+
+    for k in range(2):
+        e2e_step(k)
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        e2e_step(k)
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
+           "d2h_bytes_per_step": 2 * n * 4 + 8 + 16, "steps": e2e_steps,
+           "api": "TimingGraph.sta_propagate/extract_critical_paths/attraction_update_pairs/"
+                  "attraction_loss_fwd/bwd with pinned host positions in, gradient/loss/WNS/TNS out"}
+
+    stages = None
+    if args.stages:
+        stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
+
+    # -------------------------------------------------------------- report --
+    result = None
+    if rank == 0:
+        import json as _json
+        peaks = {}
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pp):
+            with open(pp) as f:
+                peaks = _json.load(f)
+        hbm = peaks.get("hbm_gbs")
+        peak_src = "of measured" if hbm else "of fallback"
+        hbm = hbm or 6400.0
+        roof = None
+        if prof_n > 0:
+            per_launch_ms = prof_ms / prof_n
+            bytes_ = algorithmic_bytes(args.roofline_kernel, nl, info)
+            achieved = bytes_ / (per_launch_ms / 1000.0) / 1e9
+            roof = {"kernel": args.roofline_kernel, "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                    "peak_source": peak_src, "traffic": None,
+                    "algorithmic_bytes_per_launch": int(bytes_),
+                    "launch_ms": round(per_launch_ms, 4), "launches": prof_n}
+        cfgd = workload_desc(cfg, nl)
+        cfgd.update({"seed": args.seed, "placements": f"{N_POS_SETS} seeded Gaussian moves (sigma {SIGMA} um), cycled",
+                     "l2": "no flush: per-step working set (netlist + timing state, ~0.5 GB) exceeds the 126 MB L2",
+                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                     "w0": W0, "w1": W1, "beta": BETA})
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded levelized random netlist standing in for the ICCAD 2015 superblue designs",
+            "config": cfgd, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": round(launches / args.steps, 1), "clocks": clk,
+            "timing": {"wns_ps": wns, "tns_ps": tns, "T_ps": T, "failing_endpoints": n_viol,
+                       "paths_per_step": n_paths, "path_pins_per_step": n_path_pins, "pairs_after": n_pairs},
+        }
+        if stages:
+            result["stages_ms"] = stages
+        if world == 1 and not args.no_cpu_baseline:
+            pos = (xs[0].cpu().numpy(), ys[0].cpu().numpy())
+            result["cpu_baseline"] = cpu_baseline(nl, cfg, T, pos, sample_frac=0.5, offset=0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
+    """Device time of each entry point, bracketed by events (diagnostic)."""
+    import torch
+    names = ["sta_propagate", "extract_critical_paths", "attraction_update_pairs",
+             "attraction_loss_fwd", "attraction_loss_bwd"]
+    tot = {k: 0.0 for k in names}
+    for r in range(reps):
+        x, y = xs[r % len(xs)], ys[r % len(ys)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        G.sta_propagate(x, y, T, sync=False)
+        ev[1].record(stream)
+        G.extract_critical_paths(-1, K, False, sync=False)
+        ev[2].record(stream)
+        G.attraction_update_pairs(W0, W1, sync=False)
+        ev[3].record(stream)
+        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
+        ev[4].record(stream)
+        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        for i, k in enumerate(names):
+            tot[k] += ev[i].elapsed_time(ev[i + 1])
+    return {k: round(v / reps, 4) for k, v in tot.items()}
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_iteration(nl, cfg, T, pos, sample_frac, offset, state=None):
+    """One timing iteration of the FP64 oracle on a bounded sample.
+
+    STA and the loss run on the whole netlist; report_timing_endpoint and the
+    pair update run on every (1/sample_frac)-th failing endpoint (starting at
+    `offset`), and their time is scaled by 1/sample_frac.  Returns the
+    estimated seconds of a full iteration and the measured CPU seconds.
+    """
+    import numpy as np
+    import oracle
+    x, y = pos
+    t0 = time.perf_counter()
+    tm = oracle.sta(nl, x, y, T)
+    t1 = time.perf_counter()
+    viol = oracle.topk(nl, tm, -1, 1)["viol"] if tm["wns"] < 0 else np.zeros(0, np.int32)
+    stride = max(1, int(round(1.0 / sample_frac)))
+    sample = viol[offset % stride::stride]
+    t2 = time.perf_counter()
+    P = oracle.topk(nl, tm, -1, cfg.K, endpoints=sample)
+    in_p, w = oracle.update_pairs(nl, P, tm["wns"], W0, W1,
+                                  None if state is None else state[0], None if state is None else state[1])
+    t3 = time.perf_counter()
+    oracle.loss(nl, in_p, w, BETA, x, y)
+    t4 = time.perf_counter()
+    frac = len(sample) / max(1, len(viol))
+    est = (t1 - t0) + (t3 - t2) / max(frac, 1e-9) + (t4 - t3)
+    return est, t4 - t0, (in_p, w), len(sample), len(viol)
+
+
+def cpu_baseline(nl, cfg, T, pos, sample_frac, offset):
+    est, cpu_s, _, ns, nv = oracle_iteration(nl, cfg, T, pos, sample_frac, offset)
+    return {"value": round(1.0 / est, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one timing iteration of the same workload: FP64 STA and loss on the whole netlist, "
+                      f"top-{cfg.K} extraction and pair update on {ns} of {nv} failing endpoints "
+                      f"(time scaled by {nv / max(ns, 1):.2f}); {cpu_s:.1f} s of single-threaded CPU work",
+            "seconds_per_iteration": round(est, 3)}
+
+
+def run_reference(args):
+    import netgen
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    cfg = netgen.CONFIGS[args.config]
+    nl = netgen.generate(cfg, args.seed)
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(1000 + args.seed)
+    x, y = nl.x.astype(np.float64), nl.y.astype(np.float64)
+    mv = nl.cell_fixed == 0
+    T = oracle.clock_period(nl, cfg.t_factor, x, y)
+    frac = 1.0 / 8.0
+    state = None
+    times, cpu_total = [], 0.0
+    for k in range(args.warmup + args.steps):
+        x = np.where(mv, np.clip(x + rng.normal(0, SIGMA, len(x)), 0, netgen.DIE_UM), x)
+        y = np.where(mv, np.clip(y + rng.normal(0, SIGMA, len(y)), 0, netgen.DIE_UM), y)
+        est, cpu_s, state, ns, nv = oracle_iteration(nl, cfg, T, (x, y), frac, k, state)
+        if k >= args.warmup:
+            times.append(est)
+            cpu_total += cpu_s
+    ms = 1000.0 * sum(times) / len(times)
+    value = 1000.0 / ms
+    cfgd = workload_desc(cfg, nl)
+    cfgd.update({"seed": args.seed, "parallelism": "single CPU thread"})
+    sample = (f"each step: FP64 STA and loss on the whole netlist, top-{cfg.K} extraction and pair update "
+              f"on every 8th failing endpoint (rotating), extraction time scaled by 8")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: seeded levelized random netlist standing in for the ICCAD 2015 superblue designs",
+            "config": cfgd,
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample, "cpu_seconds": round(cpu_total, 1)},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

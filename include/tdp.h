@@ -230,6 +230,22 @@ TDP_API tdp_status attraction_loss_fwd(tdp_graph *g, const void *x_dev, const vo
 TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
                                const double *grad_scale_dev, void *gx_dev, void *gy_dev);
 
+/*
+ * Instrumentation (no counterpart in the paper).
+ * tdp_get_launch_count: number of kernels this graph has queued so far
+ * (graph replays count every kernel node).
+ * tdp_profile_kernel: time every later launch of the named kernel with a pair
+ * of CUDA events on the graph's stream ("net_rc", "viol_sort" (the whole
+ * endpoint sort), "topk", "pair_walk", "pair_finish", "pp_fwd", "pp_bwd_net",
+ * "pp_bwd_cell"; NULL or "" stops).  The level sweeps and the WNS / TNS
+ * reduction run inside CUDA graphs and cannot be selected (TDP_ERR_INVALID).
+ * tdp_profile_read: synchronise the stream, return the number of timed
+ * launches and their summed device time in ms, and reset both.
+ */
+TDP_API tdp_status tdp_get_launch_count(tdp_graph *g, int64_t *n_out);
+TDP_API tdp_status tdp_profile_kernel(tdp_graph *g, const char *kernel_name);
+TDP_API tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, double *total_ms_out);
+
 /* Message for the last non-OK status returned on this host thread. */
 TDP_API const char *tdp_last_error(void);
 

@@ -3,6 +3,7 @@
 // and lay the level-ordered CSR arrays out in device memory.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -63,7 +64,7 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(dalloc(g, &s.nviol, 1));
     TDP_TRY(dalloc(g, &s.viol, std::max(t.n_ep, 1)));
     TDP_TRY(dalloc(g, &s.bcnt, t.n_nets));
-    TDP_CUDA(cudaMemset(s.bcnt, 0, t.n_nets));
+    TDP_CUDA(cudaMemset(s.bcnt, 0, sizeof(int32_t) * t.n_nets));
     TDP_TRY(dalloc(g, &s.p_count, std::max(t.n_ep, 1)));
     TDP_TRY(dalloc(g, &s.n_paths, 1));
     // pin pairs
@@ -80,6 +81,10 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_CUDA(cudaMemset(s.in_p, 0, t.n_pins));
     TDP_CUDA(cudaMemset(s.w, 0, sizeof(R) * t.n_pins));
     TDP_CUDA(cudaMemset(s.n_pairs, 0, sizeof(long long)));
+    // backward sweep: partial minima of split nets and their counters
+    TDP_TRY(dalloc(g, &s.bw_part, std::max(t.n_bw_slots, 1)));
+    TDP_TRY(dalloc(g, &s.bw_cnt, std::max(t.n_bw_split, 1)));
+    TDP_CUDA(cudaMemset(s.bw_cnt, 0, sizeof(unsigned long long) * std::max(t.n_bw_split, 1)));
     // loss
     TDP_TRY(dalloc(g, &s.gslot, 2 * (size_t)t.n_pins));
     TDP_TRY(dalloc(g, &s.loss_part, 1024));
@@ -243,6 +248,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     }
     std::vector<int32_t> lv_out(n_comb), lv_onet(n_comb), lv_in_ptr(n_comb + 1, 0);
     std::vector<int32_t> lv_in_pin, lv_in_drv, lv_in_net;
+    std::vector<uint8_t> lv_in_comb;
     for (int k = 0; k < n_comb; ++k) {
         int c = lv_cell[k];
         lv_out[k] = out_pin[c];
@@ -253,6 +259,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             lv_in_pin.push_back(p);
             lv_in_drv.push_back(d->net_ptr[pin_net[p]]);
             lv_in_net.push_back(pin_net[p]);
+            lv_in_comb.push_back(d->cell_type[d->pin_cell[d->net_ptr[pin_net[p]]]] == TDP_CELL_COMB);
         }
         lv_in_ptr[k + 1] = (int32_t)lv_in_pin.size();
     }
@@ -295,6 +302,47 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             bl_net[small ? fs[l]++ : fb[l]++] = e;
         }
     }
+    // backward tasks, highest level first; tasks of level l: [bw_ptr[l], bw_ptr[l+1])
+    std::vector<BwTask> bw;
+    std::vector<int32_t> bw_nets;
+    int n_slots = 0, n_split = 0;
+    std::vector<int32_t> lvl_first(D + 1, 0), lvl_count(D + 1, 0);
+    for (int l = D; l >= 0; --l) {
+        lvl_first[l] = (int32_t)bw.size();
+        std::vector<int32_t> small;
+        for (int q = bl_ptr[l]; q < bl_ptr[l + 1]; ++q) {
+            int e = bl_net[q];
+            int f = d->net_ptr[e + 1] - d->net_ptr[e] - 1;
+            if (f <= kBwSmallFanout) {
+                small.push_back(e);
+                continue;
+            }
+            int parts = (f + kBwPart - 1) / kBwPart;
+            int cnt = parts > 1 ? n_split++ : -1;
+            for (int j = 0; j < parts; ++j) {
+                int p0 = d->net_ptr[e] + 1 + j * kBwPart;
+                int p1 = std::min(d->net_ptr[e + 1], p0 + kBwPart);
+                bw.push_back(BwTask{1, e, p0, p1, parts > 1 ? n_slots + j : -1, parts, cnt, j});
+            }
+            if (parts > 1) n_slots += parts;
+        }
+        for (size_t q = 0; q < small.size(); q += 32) {
+            int cnt = (int)std::min<size_t>(32, small.size() - q);
+            bw.push_back(BwTask{0, -1, (int)bw_nets.size(), cnt, -1, 1, -1, 0});
+            bw_nets.insert(bw_nets.end(), small.begin() + q, small.begin() + q + cnt);
+        }
+        lvl_count[l] = (int32_t)bw.size() - lvl_first[l];
+    }
+    std::vector<int32_t> bw_lo(D + 1), bw_hi(D + 1);
+    for (int l = 0; l <= D; ++l) {
+        bw_lo[l] = lvl_first[l];
+        bw_hi[l] = lvl_first[l] + lvl_count[l];
+    }
+    t.n_bw_tasks = (int32_t)bw.size();
+    t.n_bw_slots = n_slots;
+    t.n_bw_split = n_split;
+    TDP_TRY(upload(g, &t.bw_task, bw));
+    TDP_TRY(upload(g, &t.bw_nets, bw_nets));
     t.n_cells = nc;
     t.n_pins = np;
     t.n_nets = nn;
@@ -304,8 +352,8 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     t.depth = D;
     t.n_big = (int32_t)big.size();
     g->lv.lvl_ptr = lvl_ptr;
-    g->lv.bl_ptr = bl_ptr;
-    g->lv.bl_small = bl_small;
+    g->lv.bw_lo = bw_lo;
+    g->lv.bw_hi = bw_hi;
     std::vector<int32_t> pc(d->pin_cell, d->pin_cell + np), nptr(d->net_ptr, d->net_ptr + nn + 1);
     std::vector<uint8_t> fixed(d->cell_fixed, d->cell_fixed + nc);
     TDP_TRY(upload(g, &t.pin_cell, pc));
@@ -322,7 +370,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(upload(g, &t.lv_in_pin, lv_in_pin));
     TDP_TRY(upload(g, &t.lv_in_drv, lv_in_drv));
     TDP_TRY(upload(g, &t.lv_in_net, lv_in_net));
-    TDP_TRY(upload(g, &t.bl_net, bl_net));
+    TDP_TRY(upload(g, &t.lv_in_comb, lv_in_comb));
     TDP_TRY(upload(g, &t.ep, ep));
     TDP_TRY(upload(g, &t.cp_ptr, cp_ptr));
     TDP_TRY(upload(g, &t.cp, cp));
@@ -333,14 +381,100 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
 
 }  // namespace tdp
 
+namespace tdp {
+
+const char *const kKernelNames[KID_COUNT] = {"net_rc", "viol_sort", "topk", "pair_walk",
+                                              "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell"};
+
+static cudaEvent_t prof_event(tdp_graph *g) {
+    if (!g->prof_free.empty()) {
+        cudaEvent_t e = g->prof_free.back();
+        g->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+LaunchScope::LaunchScope(tdp_graph *g_, KernelId id, int n_kernels) : g(g_), on(g_->prof_id == id) {
+    g->n_launch += n_kernels;
+    if (on) {
+        a = prof_event(g);
+        if (a) cudaEventRecord(a, g->stream);
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (!on || !a) return;
+    cudaEvent_t b = prof_event(g);
+    if (!b) return;
+    cudaEventRecord(b, g->stream);
+    g->prof_pending.emplace_back(a, b);
+}
+
+}  // namespace tdp
+
 using namespace tdp;
 
 extern "C" const char *tdp_last_error(void) { return g_err; }
 
+extern "C" tdp_status tdp_get_launch_count(tdp_graph *g, int64_t *n_out) {
+    if (!g || !n_out) {
+        set_error("tdp_get_launch_count: NULL argument");
+        return TDP_ERR_INVALID;
+    }
+    *n_out = g->n_launch;
+    return TDP_OK;
+}
+
+extern "C" tdp_status tdp_profile_kernel(tdp_graph *g, const char *name) {
+    if (!g) {
+        set_error("tdp_profile_kernel: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    int id = -1;
+    if (name && name[0]) {
+        for (int k = 0; k < KID_COUNT; ++k)
+            if (!strcmp(name, kKernelNames[k])) id = k;
+        if (id < 0) {
+            set_error("tdp_profile_kernel: unknown kernel name '%s'", name);
+            return TDP_ERR_INVALID;
+        }
+    }
+    g->prof_id = id;
+    return TDP_OK;
+}
+
+extern "C" tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, double *total_ms_out) {
+    if (!g) {
+        set_error("tdp_profile_read: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    TDP_CUDA(cudaStreamSynchronize(g->stream));
+    double total = 0.0;
+    for (auto &pr : g->prof_pending) {
+        float ms = 0.0f;
+        TDP_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        total += ms;
+        g->prof_free.push_back(pr.first);
+        g->prof_free.push_back(pr.second);
+    }
+    if (launches_out) *launches_out = (int64_t)g->prof_pending.size();
+    if (total_ms_out) *total_ms_out = total;
+    g->prof_pending.clear();
+    return TDP_OK;
+}
+
 extern "C" void sta_destroy(tdp_graph *g) {
     if (!g) return;
     if (g->sta_graph) cudaGraphExecDestroy(g->sta_graph);
-    if (g->bsweep_graph) cudaGraphExecDestroy(g->bsweep_graph);
+    if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
+    for (auto &pr : g->prof_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : g->prof_free) cudaEventDestroy(e);
     for (void *p : g->allocs) cudaFree(p);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;

@@ -3,17 +3,16 @@
 // 1. k_viol_collect / k_tile_sort / k_merge_pass / k_sort_finish
 //      failing endpoints sorted by (slack, pin): the pin breaks every tie, so
 //      the (slack, pin) items are unique and the sorted order is unique.
-// 2. k_bsweep_level (one launch per level, captured in a CUDA graph)
-//      For every combinational output v with negative slack, the K-1 cheapest
-//      sidetracks on the worst-input chain from v back to its startpoint.
-//      A sidetrack enters a node u through an input pin i other than u's
-//      worst input; its cost delta = Arr(worst input) - Arr(i) >= 0 is the
-//      slack a path loses by taking it.  list(v) = merge(own sidetracks of v,
-//      list(worst-input driver of v)), so each list is one merge of two sorted
-//      lists.  Equal costs are ordered as the pin sequences of the resulting
-//      paths would be (read from the endpoint): v's own sidetracks through a
-//      lower pin than v's worst input come first, then the inherited entries,
-//      then v's sidetracks through a higher pin.
+// 2. sidetrack lists (built by the forward sweep, tdp_sta.cu)
+//      For every combinational output v, the cheapest sidetracks on the
+//      worst-input chain from v back to its startpoint.  A sidetrack enters a
+//      node u through an input pin i other than u's worst input; its cost
+//      delta = Arr(worst input) - Arr(i) >= 0 is the slack a path loses by
+//      taking it.  list(v) = merge(own sidetracks of v, list(worst-input
+//      driver of v)).  Equal costs are ordered as the pin sequences of the
+//      resulting paths would be (read from the endpoint).  The forward sweep
+//      builds lists as long as the last extraction needed (K - 1); when an
+//      extraction needs longer lists it reruns the forward sweep first.
 // 3. k_topk: one warp per failing endpoint.  The worst path follows worst
 //      inputs from the endpoint; every other path is its parent path plus one
 //      sidetrack taken on the parent's last worst-input chain.  A candidate
@@ -132,72 +131,6 @@ __global__ void k_sort_finish(State<R> s, const SortItem *items) {
     if (i < *s.nviol) s.viol[i] = (int)items[i].pin;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_bsweep_level(Topo t, State<R> s, int lo, int hi, int L,
-                                                      int keep_nonneg) {
-    using AC = Acc<R>;
-    using A = typename AC::T;
-    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= hi) return;
-    const int e = t.lv_onet[k];
-    const R so = s.slack[t.lv_out[k]];
-    if (!keep_nonneg && !(so < R(0))) {  // no negative path passes through this node
-        s.bcnt[e] = 0;
-        return;
-    }
-    const int pi = s.pred_in[e], pn = s.pred_net[e];
-    const A apred = s.arr[pi];
-    R od[kMaxFanin];
-    int op[kMaxFanin];
-    int no = 0;
-    for (int q = t.lv_in_ptr[k]; q < t.lv_in_ptr[k + 1]; ++q) {
-        const int i = t.lv_in_pin[q];
-        if (i == pi) continue;
-        const R d = AC::diff(apred, s.arr[i]);
-        if (!keep_nonneg && !(so + d < R(0))) continue;
-        // insertion by (delta, side of the worst input, pin)
-        int pos = no;
-        while (pos > 0) {
-            R dp = od[pos - 1];
-            int pp = op[pos - 1];
-            bool before = d < dp || (d == dp && ((i < pi) != (pp < pi) ? (i < pi) : i < pp));
-            if (!before) break;
-            od[pos] = dp;
-            op[pos] = pp;
-            --pos;
-        }
-        od[pos] = d;
-        op[pos] = i;
-        ++no;
-    }
-    const BEnt<R> *pl = s.blist + (size_t)pn * L;
-    const int npl = s.bcnt[pn];
-    BEnt<R> *out = s.blist + (size_t)e * L;
-    int a = 0, b = 0, m = 0;
-    while (m < L) {
-        const bool ha = a < no;
-        const bool hb = b < npl && (keep_nonneg || pl[b].delta + so < R(0));
-        if (!ha && !hb) break;
-        bool take_own;
-        if (!hb) take_own = true;
-        else if (!ha) take_own = false;
-        else {
-            const R db = pl[b].delta;
-            take_own = od[a] < db || (od[a] == db && op[a] < pi);
-        }
-        if (take_own) {
-            out[m].delta = od[a];
-            out[m].pin = op[a];
-            ++a;
-        } else {
-            out[m] = pl[b];
-            ++b;
-        }
-        ++m;
-    }
-    s.bcnt[e] = (uint8_t)m;
-}
-
 // Is candidate a (parent path pa + sidetrack pin sa) ordered before candidate
 // b (pb + sb) when both have the same slack?  Paths are compared by their pin
 // sequences read from the endpoint; two paths first differ at the first
@@ -306,7 +239,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             }
             if (lane == win) {  // replace the popped candidate by its next sibling
                 cv = false;
-                if (wj + 1 < s.bcnt[wtail]) {
+                if (wj + 1 < min(s.bcnt[wtail], K - 1)) {  // lists may be longer than K - 1
                     const R c2 = sh_cost[w][wpar] + s.blist[(size_t)wtail * L + wj + 1].delta;
                     if (keep_nonneg || se + c2 < R(0)) {
                         cv = true;
@@ -357,45 +290,6 @@ static tdp_status ensure_path_buffers(tdp_graph *g, int K) {
         TDP_TRY(dalloc(g, &s.p_len, slots));
         TDP_TRY(dalloc(g, &s.p_cost, slots));
     }
-    if (K > 1 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * (kMaxK - 1)));
-    return TDP_OK;
-}
-
-template <typename R>
-static tdp_status capture_bsweep(tdp_graph *g, int K, int keep_nonneg) {
-    if (g->bsweep_graph && g->bsweep_K == K && g->bsweep_keep == keep_nonneg) return TDP_OK;
-    if (g->bsweep_graph) {
-        cudaGraphExecDestroy(g->bsweep_graph);
-        g->bsweep_graph = nullptr;
-    }
-    Topo &t = g->topo;
-    State<R> &s = state<R>(g);
-    cudaStream_t cs = g->cap_stream;
-    const int L = K - 1;
-    TDP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    bool ok = true;
-    for (int l = 1; l <= t.depth && ok; ++l) {
-        int lo = g->lv.lvl_ptr[l - 1], hi = g->lv.lvl_ptr[l];
-        if (hi > lo)
-            k_bsweep_level<R><<<div_up(hi - lo, 128), 128, 0, cs>>>(t, s, lo, hi, L, keep_nonneg);
-        ok = cudaGetLastError() == cudaSuccess;
-    }
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    if (!ok || e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        set_error("extract_critical_paths: capturing the sidetrack sweep failed");
-        return TDP_ERR_CUDA;
-    }
-    e = cudaGraphInstantiate(&g->bsweep_graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-        g->bsweep_graph = nullptr;
-        set_error("extract_critical_paths: cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
-        return TDP_ERR_CUDA;
-    }
-    g->bsweep_K = K;
-    g->bsweep_keep = keep_nonneg;
     return TDP_OK;
 }
 
@@ -411,6 +305,9 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
     TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
     if (t.n_ep > 0) {
+        int passes = 0;
+        for (int run = kTile; run < t.n_ep; run *= 2) ++passes;
+        LaunchScope ls(g, KID_VIOL_SORT, 3 + passes);
         k_viol_collect<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s, a);
         k_tile_sort<<<div_up(t.n_ep, kTile), 1024, 0, st>>>(a, s.nviol);
         for (int run = kTile; run < t.n_ep; run *= 2) {
@@ -418,18 +315,24 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
             std::swap(a, b);
         }
         k_sort_finish<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
-        TDP_LAUNCH_CHECK();
     }
-    // 2. sidetrack lists
-    if (K > 1) {
-        TDP_TRY(capture_bsweep<R>(g, K, keep_nonneg));
-        TDP_CUDA(cudaGraphLaunch(g->bsweep_graph, st));
+    TDP_LAUNCH_CHECK();
+    // 2. sidetrack lists: the next sweeps build K - 1 entries per node; if the
+    //    current lists are shorter, rebuild them now with the forward sweep
+    if (K > 1 && t.n_ep > 0) {
+        g->list_L = K - 1;
+        if (g->lists_valid_L < K - 1) {
+            TDP_TRY(forward_lists<R>(g));
+            g->lists_valid_L = g->list_L;
+        }
     }
     // 3. K paths per endpoint
     if (t.n_ep > 0) {
         int n_cap = n_endpoints < 0 ? INT_MAX : n_endpoints;
         int blocks = std::min(div_up(t.n_ep, kTopkWarps), 148 * 16);
-        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, K - 1, keep_nonneg, n_cap);
+        LaunchScope ls(g, KID_TOPK);
+        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, std::max(g->lists_valid_L, 1), keep_nonneg,
+                                                      n_cap);
         TDP_LAUNCH_CHECK();
     }
     return TDP_OK;
@@ -531,6 +434,7 @@ tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, in
     }
     if (rc == TDP_OK) rc = scan_i32_to_i64(g, s.p_count, base, n_use, st);
     if (rc == TDP_OK) {
+        g->n_launch += 2;
         k_path_lens<R><<<div_up(n_use, 256), 256, 0, st>>>(s, g->K, n_use, base, lens);
         rc = scan_i32_to_i64(g, lens, pin_off, np, st);
     }

@@ -3,8 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "tdp.h"
@@ -35,18 +37,27 @@ void set_error(const char *fmt, ...);
 // ------------------------------------------------------------- constants ---
 constexpr int kMaxK = 32;          // paths per endpoint (one warp holds the frontier)
 constexpr int kMaxFanin = 32;      // inputs of a combinational cell
-constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole warp
+constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole block
+constexpr int kPre = 4;            // inputs / sinks whose loads are issued together
 constexpr double kQScale = 16777216.0;  // 2^24: fixed point of slack/WNS in the pair update
 constexpr double kQClamp = 32768.0;     // |slack/WNS| is clamped here before conversion
 
 enum PinKind : uint8_t { PK_COMB_IN = 0, PK_ENDPOINT = 1, PK_COMB_OUT = 2, PK_START = 3 };
+
+// Kernels that can be timed with tdp_profile_kernel (names in tdp_build.cu);
+// the level sweeps and WNS / TNS are replayed inside CUDA graphs.
+enum KernelId {
+    KID_NET_RC, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK, KID_PAIR_FINISH, KID_PP_FWD,
+    KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_COUNT
+};
+extern const char *const kKernelNames[KID_COUNT];
 
 // ------------------------------------------------- arrival accumulators ---
 // FP32 graphs accumulate arrival and required times as an unevaluated sum of
 // two floats (hi + lo, |lo| <= ulp(hi)/2): the delays themselves are FP32,
 // but the long chains of additions keep their rounding error in lo, so the
 // error stays relative to the delays rather than growing with the depth.
-struct fx2 {
+struct __align__(8) fx2 {
     float hi, lo;
 };
 
@@ -96,13 +107,43 @@ struct Acc<float> {
     static __device__ __forceinline__ T pinf() { return fx2{__int_as_float(0x7f800000), 0.0f}; }
 };
 
+// Read-only loads through the non-coherent path.  Used for arrays a kernel
+// never writes during its lifetime (topology, delays, and timing values of
+// other levels, which earlier launches wrote).
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+__device__ __forceinline__ fx2 ldg(const fx2 *p) {
+    float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return fx2{v.x, v.y};
+}
+
 // One sidetrack entry of a node's list: the deviation cost delta >= 0 of
-// entering the node through a non-worst input pin instead of its worst one.
+// entering a node through a non-worst input pin instead of its worst one.
 template <typename R>
-struct BEnt {
+struct __align__(2 * sizeof(R)) BEnt {
     R delta;
     int32_t pin;
 };
+
+__device__ __forceinline__ BEnt<float> ldg(const BEnt<float> *p) {
+    float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return BEnt<float>{v.x, __float_as_int(v.y)};
+}
+__device__ __forceinline__ BEnt<double> ldg(const BEnt<double> *p) {
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return BEnt<double>{v.x, (int32_t)(__double_as_longlong(v.y) & 0xffffffffll)};
+}
+
+// One task of the backward sweep (one warp).
+//   kind 0: nets bw_nets[p0 .. p0+p1) (at most 32 nets of at most 8 sinks), one per lane;
+//   kind 1: sinks [p0, p1) of net `net`; when the net is split into nparts
+//           tasks, task `part` writes its minimum to `slot` and the last task
+//           to finish (counter `cnt`) combines the slots.
+struct BwTask {
+    int32_t kind, net, p0, p1, slot, nparts, cnt, part;
+};
+constexpr int kBwSmallFanout = 8;    // nets up to this fanout are handled one per lane
+constexpr int kBwPart = 128;         // sinks per warp task of a larger net
 
 // ------------------------------------------------------------ the graph ---
 // Device arrays common to both precisions (topology, built once).
@@ -122,20 +163,22 @@ struct Topo {
     int32_t *lv_in_pin = nullptr;  // [n_in] input pins, ascending
     int32_t *lv_in_drv = nullptr;  // [n_in] driver pin of the input's net
     int32_t *lv_in_net = nullptr;  // [n_in] net of the input
-    // nets grouped by driver level: per level [small nets ..., big nets ...]
-    int32_t *bl_net = nullptr;     // [n_nets]
+    uint8_t *lv_in_comb = nullptr; // [n_in] 1 if that net is driven by a combinational cell
     int32_t *ep = nullptr;         // [n_ep] endpoint pins, ascending
     int32_t *cp_ptr = nullptr;     // [n_cells+1] cell -> pins CSR
     int32_t *cp = nullptr;         // [n_pins]
     int32_t *slot_of_pin = nullptr;// [n_pins] position of a pin in cp
     uint8_t *cell_fixed = nullptr; // [n_cells]
+    // backward sweep tasks, highest level first
+    BwTask *bw_task = nullptr;
+    int32_t *bw_nets = nullptr;    // small nets in task order
+    int32_t n_bw_tasks = 0, n_bw_slots = 0, n_bw_split = 0;
 };
 
 // Host copies of the launch structure of the level sweeps.
 struct Levels {
     std::vector<int32_t> lvl_ptr;   // comb cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
-    std::vector<int32_t> bl_ptr;    // nets of level l: [bl_ptr[l], bl_ptr[l+1])
-    std::vector<int32_t> bl_small;  // number of small nets at the start of level l
+    std::vector<int32_t> bw_lo, bw_hi;  // backward tasks of level l: [bw_lo[l], bw_hi[l])
 };
 
 template <typename R>
@@ -154,17 +197,18 @@ struct State {
     double *wns_tns = nullptr;    // [2]
     double *red_part = nullptr;   // reduction partials
     unsigned *red_count = nullptr;
+    A *bw_part = nullptr;         // [n_bw_slots] partial minima of split nets
+    unsigned long long *bw_cnt = nullptr;  // [n_bw_split] finished parts (monotone)
     // extraction
     uint64_t *sort_a = nullptr, *sort_b = nullptr;  // (key, pin) items, ping-pong
     int32_t *nviol = nullptr;     // device count of failing endpoints
     int32_t *viol = nullptr;      // [n_ep] failing endpoints sorted by (slack, pin)
-    BEnt<R> *blist = nullptr;     // [n_nets * (kMaxK-1)] sidetrack lists
-    uint8_t *bcnt = nullptr;      // [n_nets]
+    BEnt<R> *blist = nullptr;     // [n_nets * list_L] sidetrack lists
+    int32_t *bcnt = nullptr;      // [n_nets] entries in each sidetrack list
     int32_t *p_parent = nullptr, *p_side = nullptr, *p_len = nullptr;  // [n_ep * K]
     R *p_cost = nullptr;
     int32_t *p_count = nullptr;   // [n_ep] paths per failing endpoint (sorted order)
     long long *n_paths = nullptr; // device total
-    int64_t *scan_tmp = nullptr;  // scan scratch
     // pin pairs
     long long *sumq = nullptr, *maxq = nullptr;  // [n_pins] fixed-point slack/WNS
     uint8_t *touch = nullptr, *in_p = nullptr;   // [n_pins]
@@ -189,10 +233,17 @@ struct tdp_graph {
     double r = 0, c = 0, d0 = 0;
     int K = 0, keep_nonneg = 0, n_endpoints = -1;
     bool propagated = false, extracted = false;
-    cudaGraphExec_t sta_graph = nullptr;
-    cudaGraphExec_t bsweep_graph = nullptr;
-    int bsweep_K = -1, bsweep_keep = -1;
+    // sidetrack lists are built by the forward sweep: list_L entries per node
+    // (the K - 1 of the last extraction), lists_valid_L of them are current
+    int list_L = 0, lists_valid_L = 0;
+    cudaGraphExec_t sta_graph = nullptr, fwd_graph = nullptr;
+    int sta_graph_L = -1, fwd_graph_L = -1, sta_graph_kernels = 0, fwd_graph_kernels = 0;
     std::vector<void *> allocs;  // every device allocation, freed in sta_destroy
+    // instrumentation
+    int64_t n_launch = 0;                 // kernels queued by this graph so far
+    int prof_id = -1;                     // kernel timed with CUDA events (-1: none)
+    std::vector<cudaEvent_t> prof_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
 };
 
 namespace tdp {
@@ -222,6 +273,8 @@ inline State<double> &state<double>(tdp_graph *g) { return g->s64; }
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T);
 template <typename R>
+tdp_status forward_lists(tdp_graph *g);
+template <typename R>
 tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg);
 template <typename R>
 tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, int64_t *pin_ptr,
@@ -239,4 +292,14 @@ tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_
                            cudaStream_t st);
 
 inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// Brackets the launches of one kernel with CUDA events on the graph's stream
+// when that kernel is selected by tdp_profile_kernel; counts launches always.
+struct LaunchScope {
+    tdp_graph *g;
+    bool on;
+    cudaEvent_t a = nullptr;
+    LaunchScope(tdp_graph *g_, KernelId id, int n_kernels = 1);
+    ~LaunchScope();
+};
 }  // namespace tdp

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const d
 
 template <typename R>
 tdp_status loss_fwd_impl(tdp_graph *g, const R *x, const R *y, double beta, double *loss) {
+    LaunchScope ls(g, KID_PP_FWD);
     k_pp_fwd<R><<<kLossBlocks, kLossThreads, 0, g->stream>>>(g->topo, state<R>(g), x, y, beta, loss);
     TDP_LAUNCH_CHECK();
     return TDP_OK;
@@ -178,8 +179,14 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
     State<R> &s = state<R>(g);
     const int nsw = div_up(t.n_nets, 32);
     const int64_t threads = (int64_t)(nsw + t.n_big) * 32;
-    k_pp_bwd_net<R><<<div_up(threads, 256), 256, 0, g->stream>>>(t, s, x, y, beta, nsw);
-    k_pp_bwd_cell<R><<<div_up(t.n_cells, 256), 256, 0, g->stream>>>(t, s, gs, gx, gy);
+    {
+        LaunchScope ls(g, KID_PP_BWD_NET);
+        k_pp_bwd_net<R><<<div_up(threads, 256), 256, 0, g->stream>>>(t, s, x, y, beta, nsw);
+    }
+    {
+        LaunchScope ls(g, KID_PP_BWD_CELL);
+        k_pp_bwd_cell<R><<<div_up(t.n_cells, 256), 256, 0, g->stream>>>(t, s, gs, gx, gy);
+    }
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t *in, 
 }
 
 tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_t n, cudaStream_t st) {
-    (void)g;
+    g->n_launch += 3;
     const int nt = div_up(std::max<int64_t>(n, 1), kScanTile);
     long long *tile = nullptr;
     if (cudaMallocAsync(&tile, sizeof(long long) * nt, st) != cudaSuccess) {

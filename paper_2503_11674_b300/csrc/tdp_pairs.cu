@@ -18,49 +18,92 @@
 
 namespace tdp {
 
-template <typename R, typename F>
-__device__ __forceinline__ void walk_sinks(const Topo &t, const State<R> &s, int ep,
-                                           const int *sides, int nsides, F &&visit) {
-    visit(ep);
-    int e = t.pin_net[ep];
-    int j = nsides - 1;
-    for (;;) {
-        int pi = s.pred_in[e];
-        if (pi < 0) break;
-        int nx;
-        if (j >= 0 && t.sink_onet[sides[j]] == e) {
-            pi = sides[j--];
-            nx = t.pin_net[pi];
-        } else {
-            nx = s.pred_net[e];
-        }
-        visit(pi);
-        e = nx;
-    }
-}
+constexpr int kWalkWarps = 4;
 
+// One warp per failing endpoint; lane r walks the endpoint's path of rank r
+// from the endpoint back to its startpoint, one net arc per step.  Paths of
+// one endpoint share their first arcs, and lanes standing on the same sink
+// in the same step are merged (__match_any_sync): the lowest such lane adds
+// the group's summed q and raises the maximum once for all of them.
 template <typename R>
-__global__ void __launch_bounds__(128) k_pair_walk(Topo t, State<R> s, int K, int n_cap) {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = slot / K, r = slot % K;
+__global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> s, int K, int n_cap) {
+    __shared__ long long shQ[kWalkWarps][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nv = min(*s.nviol, n_cap);
-    if (i >= nv || r >= s.p_count[i]) return;
     const double wns = s.wns_tns[0];
     if (!(wns < 0.0)) return;
-    const int ep = s.viol[i];
-    const size_t base = (size_t)i * K;
-    const R sigma = s.slack[ep] + s.p_cost[base + r];
-    double q = (double)sigma / wns;
-    q = fmin(fmax(q, -kQClamp), kQClamp);
-    const long long Q = __double2ll_rn(q * kQScale);
-    int sides[kMaxK];
-    int ns = 0;
-    for (int x = r; x > 0; x = s.p_parent[base + x]) sides[ns++] = s.p_side[base + x];
-    walk_sinks<R>(t, s, ep, sides, ns, [&](int p) {
-        atomicAdd((unsigned long long *)&s.sumq[p], (unsigned long long)Q);
-        atomicMax(&s.maxq[p], Q);
-        s.touch[p] = 1;
-    });
+    for (int i = blockIdx.x * kWalkWarps + w; i < nv; i += gridDim.x * kWalkWarps) {
+        const int ep = s.viol[i];
+        const int cnt = s.p_count[i];
+        const bool on = lane < cnt;
+        const size_t base = (size_t)i * K;
+        long long Q = 0;
+        int sides[kMaxK];
+        int ns = 0;
+        if (on) {
+            const R sigma = s.slack[ep] + s.p_cost[base + lane];
+            double q = (double)sigma / wns;
+            q = fmin(fmax(q, -kQClamp), kQClamp);
+            Q = __double2ll_rn(q * kQScale);
+            for (int x = lane; x > 0; x = s.p_parent[base + x]) sides[ns++] = s.p_side[base + x];
+        }
+        shQ[w][lane] = Q;
+        __syncwarp();
+        // the endpoint's own net arc is on every path
+        if (lane == 0) {
+            long long sum = 0, mx = LLONG_MIN;
+            for (int l = 0; l < cnt; ++l) {
+                sum += shQ[w][l];
+                mx = max(mx, shQ[w][l]);
+            }
+            atomicAdd((unsigned long long *)&s.sumq[ep], (unsigned long long)sum);
+            atomicMax(&s.maxq[ep], mx);
+            s.touch[ep] = 1;
+        }
+        int e = t.pin_net[ep];
+        int j = ns - 1;  // sides[] holds the deepest sidetrack first
+        bool walking = on;
+        unsigned last_mask = 0;
+        long long last_sum = 0, last_max = 0;
+        for (;;) {
+            int pin = -1 - lane;  // distinct per lane when not on a sink
+            if (walking) {
+                int pi = s.pred_in[e];
+                if (pi < 0) {
+                    walking = false;
+                } else {
+                    int nx;
+                    if (j >= 0 && t.sink_onet[sides[j]] == e) {
+                        pi = sides[j--];
+                        nx = t.pin_net[pi];
+                    } else {
+                        nx = s.pred_net[e];
+                    }
+                    pin = pi;
+                    e = nx;
+                }
+            }
+            if (!__any_sync(FULL, walking)) break;
+            const unsigned grp = __match_any_sync(FULL, pin);
+            if (walking && lane == __ffs(grp) - 1) {
+                if (grp != last_mask) {
+                    last_sum = 0;
+                    last_max = LLONG_MIN;
+                    for (unsigned m = grp; m; m &= m - 1) {
+                        const long long v = shQ[w][__ffs(m) - 1];
+                        last_sum += v;
+                        last_max = max(last_max, v);
+                    }
+                    last_mask = grp;
+                }
+                atomicAdd((unsigned long long *)&s.sumq[pin], (unsigned long long)last_sum);
+                atomicMax(&s.maxq[pin], last_max);
+                s.touch[pin] = 1;
+            }
+        }
+        __syncwarp();
+    }
 }
 
 template <typename R>
@@ -86,9 +129,15 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
     const int n_cap = g->n_endpoints < 0 ? INT_MAX : g->n_endpoints;
-    const int64_t slots = (int64_t)t.n_ep * g->K;
-    if (slots > 0) k_pair_walk<R><<<div_up(slots, 128), 128, 0, g->stream>>>(t, s, g->K, n_cap);
-    k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(s, t.n_pins, w0, w1);
+    if (t.n_ep > 0) {
+        LaunchScope ls(g, KID_PAIR_WALK);
+        const int blocks = std::min(div_up(t.n_ep, kWalkWarps), 148 * 16);
+        k_pair_walk<R><<<blocks, kWalkWarps * 32, 0, g->stream>>>(t, s, g->K, n_cap);
+    }
+    {
+        LaunchScope ls(g, KID_PAIR_FINISH);
+        k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(s, t.n_pins, w0, w1);
+    }
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
@@ -126,6 +175,7 @@ static tdp_status get_pairs_impl(tdp_graph *g, int32_t *pins, R *w, int64_t *n_o
         set_error("attraction_get_pairs: temporary allocation failed");
         return TDP_ERR_OOM;
     }
+    g->n_launch += 2;
     k_flag_in_p<R><<<div_up(n, 256), 256, 0, st>>>(s, n, flags);
     tdp_status rc = scan_i32_to_i64(g, flags, off, n, st);
     if (rc == TDP_OK && (pins || w)) k_scatter_pairs<R><<<div_up(n, 256), 256, 0, st>>>(s, n, off, pins, w);

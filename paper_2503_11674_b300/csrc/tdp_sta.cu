@@ -3,14 +3,22 @@
 //
 //   k_net_rc     one pass over the nets: pin positions, Elmore delay of every
 //                sink, net load and driving-cell delay (thread per net up to 32
-//                sinks, warp per net above, FP64 load sum there)
-//   k_fwd_level  arrival times of the combinational cells of one level
-//                (thread per cell; max / argmax over its inputs)
-//   k_bwd_level  required times of the nets driven from one level
-//                (thread per net, warp per high-fanout net; min over sinks)
+//                sinks, block per net above, FP64 load sum there)
+//   k_fwd_level  arrival times of the combinational cells of one level (thread
+//                per cell; max / argmax over its inputs), and, when asked, the
+//                cell's sidetrack list for report_timing_endpoint
+//   k_bwd_level  required times of the nets driven from one level (lane per
+//                net of at most 8 sinks, warp per 128 sinks of larger nets,
+//                split nets combined by the last warp to finish)
 //   k_wns_tns    FP64 WNS / TNS over the endpoints (fixed-order reduction)
 //
 // The per-level launches are captured once into a CUDA graph and replayed.
+// Every array a level kernel reads was written by an earlier launch (a lower
+// level going forward, a higher level going backward), so the reads use the
+// read-only path and all loads of a group of inputs / sinks are issued before
+// the first store.
+#include <type_traits>
+
 #include "tdp_internal.cuh"
 
 namespace tdp {
@@ -25,160 +33,338 @@ __device__ __forceinline__ fx2 acc_from_double<float>(double v) {
     return fx2{hi, (float)(v - (double)hi)};
 }
 
+// ------------------------------------------------------------- net RC ---
+
 template <typename R>
 __device__ __forceinline__ void net_finish(const Topo &t, State<R> &s, int e, int drv, int cd,
                                            double load, R d0) {
     R ld = (R)load;
     s.cload[e] = ld;
-    R dd = d0 + s.cell_rdrv[cd] * ld;
+    R dd = d0 + ldg(&s.cell_rdrv[cd]) * ld;
     s.dnet[e] = dd;
-    if (t.pin_kind[drv] == PK_START) s.arr[drv] = Acc<R>::make(dd);
+    if (ldg(&t.pin_kind[drv]) == PK_START) s.arr[drv] = Acc<R>::make(dd);
 }
 
+// Elmore delay of the sinks first, first+step, ... < b of the net driven by
+// pin a (Eq. (8)); returns the part of the net's load they contribute.
 template <typename R>
-__global__ void __launch_bounds__(256) k_net_rc(Topo t, State<R> s, const R *__restrict__ x,
-                                                const R *__restrict__ y, double T, R r, R c, R d0,
-                                                int n_small_warps) {
-    const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ double sinks_rc(const Topo &t, State<R> &s, const R *x, const R *y,
+                                           int a, int b, int first, int step, R r, R c) {
+    const int cd = ldg(&t.pin_cell[a]);
+    const R xd = ldg(&x[cd]) + ldg(&s.pin_dx[a]), yd = ldg(&y[cd]) + ldg(&s.pin_dy[a]);
+    double load = 0.0;
+#pragma unroll 4
+    for (int p = first; p < b; p += step) {
+        const int cs = ldg(&t.pin_cell[p]);
+        const R L = fabs(ldg(&x[cs]) + ldg(&s.pin_dx[p]) - xd) + fabs(ldg(&y[cs]) + ldg(&s.pin_dy[p]) - yd);
+        const R Rw = r * L, Cw = c * L;
+        const R cap = ldg(&s.pin_cap[p]);
+        s.tnet[p] = Rw * (Cw * R(0.5) + cap);
+        load += (double)(Cw + cap);
+    }
+    return load;
+}
+
+constexpr int kRcThreads = 256;
+
+// Blocks [0, n_small_blocks): one thread per net with at most kBigFanout sinks.
+// Blocks after that: one block per high-fanout net (FP64 load sum, fixed order).
+template <typename R>
+__global__ void __launch_bounds__(kRcThreads) k_net_rc(Topo t, State<R> s, const R *__restrict__ x,
+                                                       const R *__restrict__ y, double T, R r, R c,
+                                                       R d0, int n_small_blocks) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *s.T = T;
-    if (gw < n_small_warps) {
-        int e = gw * 32 + lane;
+    if ((int)blockIdx.x < n_small_blocks) {
+        const int e = blockIdx.x * kRcThreads + threadIdx.x;
         if (e >= t.n_nets) return;
-        int a = t.net_ptr[e], b = t.net_ptr[e + 1];
+        const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
         if (b - a - 1 > kBigFanout) return;
-        int cd = t.pin_cell[a];
-        R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
+        // FP32 sum for nets of at most kBigFanout sinks
+        const int cd = ldg(&t.pin_cell[a]);
+        const R xd = ldg(&x[cd]) + ldg(&s.pin_dx[a]), yd = ldg(&y[cd]) + ldg(&s.pin_dy[a]);
         R load = 0;
+#pragma unroll 4
         for (int p = a + 1; p < b; ++p) {
-            int cs = t.pin_cell[p];
-            R L = fabs(x[cs] + s.pin_dx[p] - xd) + fabs(y[cs] + s.pin_dy[p] - yd);
-            R Rw = r * L, Cw = c * L;
-            R cap = s.pin_cap[p];
+            const int cs = ldg(&t.pin_cell[p]);
+            const R L = fabs(ldg(&x[cs]) + ldg(&s.pin_dx[p]) - xd) + fabs(ldg(&y[cs]) + ldg(&s.pin_dy[p]) - yd);
+            const R Rw = r * L, Cw = c * L;
+            const R cap = ldg(&s.pin_cap[p]);
             s.tnet[p] = Rw * (Cw * R(0.5) + cap);
             load += Cw + cap;
         }
         net_finish(t, s, e, a, cd, (double)load, d0);
-    } else {
-        int k = gw - n_small_warps;
-        if (k >= t.n_big) return;
-        int e = t.big_nets[k];
-        int a = t.net_ptr[e], b = t.net_ptr[e + 1];
-        int cd = t.pin_cell[a];
-        R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
-        double load = 0.0;
-        for (int p = a + 1 + lane; p < b; p += 32) {
-            int cs = t.pin_cell[p];
-            R L = fabs(x[cs] + s.pin_dx[p] - xd) + fabs(y[cs] + s.pin_dy[p] - yd);
-            R Rw = r * L, Cw = c * L;
-            R cap = s.pin_cap[p];
-            s.tnet[p] = Rw * (Cw * R(0.5) + cap);
-            load += (double)(Cw + cap);
-        }
-        for (int o = 16; o > 0; o >>= 1) load += __shfl_xor_sync(0xffffffffu, load, o);
-        if (lane == 0) net_finish(t, s, e, a, cd, load, d0);
+        return;
+    }
+    __shared__ double part[kRcThreads / 32];
+    const int e = ldg(&t.big_nets[blockIdx.x - n_small_blocks]);
+    const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
+    double load = sinks_rc<R>(t, s, x, y, a, b, a + 1 + threadIdx.x, kRcThreads, r, c);
+    for (int o = 16; o > 0; o >>= 1) load += __shfl_xor_sync(0xffffffffu, load, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = load;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < kRcThreads / 32; ++k) tot += part[k];
+        net_finish(t, s, e, a, ldg(&t.pin_cell[a]), tot, d0);
     }
 }
 
+// ------------------------------------------------------------ forward ---
+
+constexpr int kLvThreads = 128;
+
 template <typename R>
-__global__ void __launch_bounds__(128) k_fwd_level(Topo t, State<R> s, int lo, int hi) {
+__device__ __forceinline__ BEnt<R> bent_none() {
+    return BEnt<R>{(R)__longlong_as_double(0x7ff0000000000000ll), -1};
+}
+
+// Sidetrack list of one node (Section III-B extraction): the L cheapest
+// deviations on the worst-input chain from the node back to its startpoint.
+// A deviation enters a node through an input other than its worst one; its
+// cost is Arr(worst input) - Arr(that input).  The list is the merge of the
+// node's own deviations with the list of its worst input's driver.  Equal
+// costs are ordered as the resulting paths' pin sequences (read from the
+// endpoint) would be: own deviations through a pin below the worst input,
+// then the inherited entries, then own deviations through a pin above it.
+// Lists hold exactly L entries; unused ones are +inf sentinels (pin -1).
+template <typename R>
+__device__ __forceinline__ void build_sidetracks(const Topo &t, State<R> &s, int e, int bi,
+                                                 int bn, bool bn_comb,
+                                                 typename Acc<R>::T best, const int *ip,
+                                                 const typename Acc<R>::T *ain, int nin, int L) {
+    using AC = Acc<R>;
+    BEnt<R> pl[kMaxK - 1];
+    if (bn_comb) {  // issue the inherited list's loads before anything else
+        const BEnt<R> *src = s.blist + (size_t)bn * L;
+        for (int j = 0; j < L; ++j) pl[j] = ldg(&src[j]);
+    }
+    R od[kMaxFanin];
+    int op[kMaxFanin];
+    int no = 0;
+    for (int u = 0; u < nin; ++u) {
+        const int i = ip[u];
+        if (i == bi) continue;
+        const R d = AC::diff(best, ain[u]);
+        int pos = no;
+        while (pos > 0) {  // insertion by (delta, side of the worst input, pin)
+            const R dp = od[pos - 1];
+            const int pp = op[pos - 1];
+            const bool before = d < dp || (d == dp && ((i < bi) != (pp < bi) ? (i < bi) : i < pp));
+            if (!before) break;
+            od[pos] = dp;
+            op[pos] = pp;
+            --pos;
+        }
+        od[pos] = d;
+        op[pos] = i;
+        ++no;
+    }
+    BEnt<R> *out = s.blist + (size_t)e * L;
+    int ia = 0, ib = 0, m = 0;
+    for (; m < L; ++m) {
+        const bool ha = ia < no;
+        const bool hb = bn_comb && ib < L && pl[ib].pin >= 0;
+        if (!ha && !hb) break;
+        bool take_own;
+        if (!hb) take_own = true;
+        else if (!ha) take_own = false;
+        else take_own = od[ia] < pl[ib].delta || (od[ia] == pl[ib].delta && op[ia] < bi);
+        if (take_own) {
+            out[m] = BEnt<R>{od[ia], op[ia]};
+            ++ia;
+        } else {
+            out[m] = pl[ib];
+            ++ib;
+        }
+    }
+    s.bcnt[e] = m;
+    for (int j = m; j < L; ++j) out[j] = bent_none<R>();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kLvThreads) k_fwd_level(Topo t, State<R> s, int lo, int hi, int L) {
     using AC = Acc<R>;
     using A = typename AC::T;
     const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= hi) return;
-    const int a = t.lv_in_ptr[k], b = t.lv_in_ptr[k + 1];
+    const int a = ldg(&t.lv_in_ptr[k]), b = ldg(&t.lv_in_ptr[k + 1]);
+    const int e = ldg(&t.lv_onet[k]), o = ldg(&t.lv_out[k]);
+    const R dcell = ldg(&s.dnet[e]);
     // inputs ascending by pin: strict > keeps the lowest pin on ties (and the
     // first input if arrivals are not comparable)
-    int bi = t.lv_in_pin[a], bn = t.lv_in_net[a];
-    A best = AC::add(s.arr[t.lv_in_drv[a]], s.tnet[bi]);
-    s.arr[bi] = best;
-    for (int q = a + 1; q < b; ++q) {
-        const int i = t.lv_in_pin[q];
-        A v = AC::add(s.arr[t.lv_in_drv[q]], s.tnet[i]);
-        s.arr[i] = v;
-        if (AC::gt(v, best)) {
-            best = v;
-            bi = i;
-            bn = t.lv_in_net[q];
+    int bi = -1, bn = -1, bl = 0;
+    bool bc = false;
+    A best = AC::ninf();
+    int ipa[kMaxFanin];
+    A ain[kMaxFanin];
+    for (int q0 = a; q0 < b; q0 += kPre) {
+        int ip[kPre], in[kPre], dv[kPre], pl[kPre];
+        uint8_t cb[kPre];
+        A av[kPre];
+        R tv[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (q0 + u < b) {
+                ip[u] = ldg(&t.lv_in_pin[q0 + u]);
+                in[u] = ldg(&t.lv_in_net[q0 + u]);
+                dv[u] = ldg(&t.lv_in_drv[q0 + u]);
+                cb[u] = ldg(&t.lv_in_comb[q0 + u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (q0 + u < b) {
+                av[u] = ldg(&s.arr[dv[u]]);
+                tv[u] = ldg(&s.tnet[ip[u]]);
+                pl[u] = ldg(&s.plen[in[u]]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (q0 + u < b) {
+                const A v = AC::add(av[u], tv[u]);
+                s.arr[ip[u]] = v;
+                ipa[q0 - a + u] = ip[u];
+                ain[q0 - a + u] = v;
+                if (bi < 0 || AC::gt(v, best)) {
+                    best = v;
+                    bi = ip[u];
+                    bn = in[u];
+                    bl = pl[u];
+                    bc = cb[u];
+                }
+            }
         }
     }
-    const int e = t.lv_onet[k];
-    s.arr[t.lv_out[k]] = AC::add(best, s.dnet[e]);
+    s.arr[o] = AC::add(best, dcell);
     s.pred_in[e] = bi;
     s.pred_net[e] = bn;
-    s.plen[e] = s.plen[bn] + 2;
+    s.plen[e] = bl + 2;
+    if (L > 0) build_sidetracks<R>(t, s, e, bi, bn, bc, best, ipa, ain, b - a, L);
 }
 
-// Required time of one sink and its contribution to the driver's required time.
-template <typename R>
-__device__ __forceinline__ typename Acc<R>::T sink_req(const Topo &t, State<R> &s, int p,
-                                                       typename Acc<R>::T ad,
-                                                       typename Acc<R>::T Tacc) {
-    using AC = Acc<R>;
-    using A = typename AC::T;
-    const R tp = s.tnet[p];
-    A rq, ap;
-    if (t.pin_kind[p] == PK_ENDPOINT) {
-        ap = AC::add(ad, tp);
-        s.arr[p] = ap;
-        rq = Tacc;
-    } else {
-        rq = AC::add(s.req[t.sink_out[p]], -s.dnet[t.sink_onet[p]]);
-        ap = s.arr[p];
-    }
-    s.req[p] = rq;
-    s.slack[p] = AC::diff(rq, ap);
-    return AC::add(rq, -tp);
-}
+// ----------------------------------------------------------- backward ---
 
+// req / slack of the sinks first, first+step, ... < b of a net whose driver
+// has arrival ad; returns min over them of req(s) - t(s).
 template <typename R>
-__global__ void __launch_bounds__(128) k_bwd_level(Topo t, State<R> s, int lo, int nsmall, int hi) {
+__device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State<R> &s, int first,
+                                                            int b, int step,
+                                                            typename Acc<R>::T ad,
+                                                            typename Acc<R>::T Tacc) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    const int nsw = (nsmall + 31) >> 5;
-    const A Tacc = acc_from_double<R>(*s.T);
-    if (gw < nsw) {
-        const int idx = lo + gw * 32 + lane;
-        if (idx >= lo + nsmall) return;
-        const int e = t.bl_net[idx];
-        const int a = t.net_ptr[e], b = t.net_ptr[e + 1];
-        const A ad = s.arr[a];
-        A m = AC::pinf();
-        for (int p = a + 1; p < b; ++p) {
-            A cand = sink_req<R>(t, s, p, ad, Tacc);
-            if (AC::lt(cand, m)) m = cand;
+    A m = AC::pinf();
+    for (int p0 = first; p0 < b; p0 += kPre * step) {
+        uint8_t kd[kPre];
+        R tp[kPre];
+        int so[kPre], sn[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int p = p0 + u * step;
+            if (p < b) {
+                kd[u] = ldg(&t.pin_kind[p]);
+                tp[u] = ldg(&s.tnet[p]);
+                so[u] = ldg(&t.sink_out[p]);
+                sn[u] = ldg(&t.sink_onet[p]);
+            }
         }
+        A rq[kPre], ap[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int p = p0 + u * step;
+            if (p < b) {
+                if (kd[u] == PK_ENDPOINT) {
+                    ap[u] = AC::add(ad, tp[u]);
+                    rq[u] = Tacc;
+                } else {
+                    rq[u] = AC::add(ldg(&s.req[so[u]]), -ldg(&s.dnet[sn[u]]));
+                    ap[u] = ldg(&s.arr[p]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int p = p0 + u * step;
+            if (p < b) {
+                if (kd[u] == PK_ENDPOINT) s.arr[p] = ap[u];
+                s.req[p] = rq[u];
+                s.slack[p] = AC::diff(rq[u], ap[u]);
+                const A cand = AC::add(rq[u], -tp[u]);
+                if (AC::lt(cand, m)) m = cand;
+            }
+        }
+    }
+    return m;
+}
+
+template <typename A>
+__device__ __forceinline__ A shfl_xor_acc(A v, int o) {
+    if constexpr (std::is_same<A, double>::value) {
+        return __shfl_xor_sync(0xffffffffu, v, o);
+    } else {
+        A r;
+        r.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        r.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        return r;
+    }
+}
+
+// L2 loads of values another block of the same launch has just written.
+__device__ __forceinline__ double ldcg_acc(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ fx2 ldcg_acc(const fx2 *p) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return fx2{v.x, v.y};
+}
+
+// One warp per task of this level (tasks [lo, hi) of the backward list).
+template <typename R>
+__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int lo, int hi) {
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    const int w = lo + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= hi) return;
+    const A Tacc = acc_from_double<R>(*s.T);
+    const BwTask task = t.bw_task[w];
+    if (task.kind == 0) {
+        if (lane >= task.p1) return;
+        const int e = ldg(&t.bw_nets[task.p0 + lane]);
+        const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
+        const A ad = ldg(&s.arr[a]);
+        const A m = net_sinks_req<R>(t, s, a + 1, b, 1, ad, Tacc);
         s.req[a] = m;
         s.slack[a] = AC::diff(m, ad);
-    } else {
-        const int idx = lo + nsmall + (gw - nsw);
-        if (idx >= hi) return;
-        const int e = t.bl_net[idx];
-        const int a = t.net_ptr[e], b = t.net_ptr[e + 1];
-        const A ad = s.arr[a];
-        A m = AC::pinf();
-        for (int p = a + 1 + lane; p < b; p += 32) {
-            A cand = sink_req<R>(t, s, p, ad, Tacc);
-            if (AC::lt(cand, m)) m = cand;
-        }
-        for (int o = 16; o > 0; o >>= 1) {  // min is exact: the order does not matter
-            A other;
-            if constexpr (sizeof(A) == 8 && sizeof(R) == 4) {
-                other.hi = __shfl_xor_sync(0xffffffffu, m.hi, o);
-                other.lo = __shfl_xor_sync(0xffffffffu, m.lo, o);
-            } else {
-                other = __shfl_xor_sync(0xffffffffu, m, o);
-            }
-            if (AC::lt(other, m)) m = other;
-        }
-        if (lane == 0) {
-            s.req[a] = m;
-            s.slack[a] = AC::diff(m, ad);
+        return;
+    }
+    const int a = ldg(&t.net_ptr[task.net]);
+    const A ad = ldg(&s.arr[a]);
+    A m = net_sinks_req<R>(t, s, task.p0 + lane, task.p1, 32, ad, Tacc);
+    for (int o = 16; o > 0; o >>= 1) {  // min is exact: any order gives the same value
+        const A other = shfl_xor_acc(m, o);
+        if (AC::lt(other, m)) m = other;
+    }
+    if (lane != 0) return;
+    if (task.nparts > 1) {
+        // several warps share this net: each leaves its minimum in a slot,
+        // and the last one to finish combines them (the counter only grows)
+        s.bw_part[task.slot] = m;
+        __threadfence();
+        const unsigned long long done = atomicAdd(&s.bw_cnt[task.cnt], 1ull) + 1ull;
+        if (done % (unsigned long long)task.nparts != 0ull) return;
+        __threadfence();
+        const int base = task.slot - task.part;
+        m = ldcg_acc(&s.bw_part[base]);
+        for (int j = 1; j < task.nparts; ++j) {
+            const A v = ldcg_acc(&s.bw_part[base + j]);
+            if (AC::lt(v, m)) m = v;
         }
     }
+    s.req[a] = m;
+    s.slack[a] = AC::diff(m, ad);
 }
+
+// ---------------------------------------------------------- WNS / TNS ---
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 148;
@@ -236,57 +422,105 @@ __global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
     }
 }
 
+// ------------------------------------------------------------ launch ---
+
 template <typename R>
-static tdp_status capture_sta_graph(tdp_graph *g) {
+static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, bool fwd, bool bwd,
+                          int L) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
     cudaStream_t cs = g->cap_stream;
     TDP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     bool ok = true;
-    for (int l = 1; l <= t.depth && ok; ++l) {
-        int lo = g->lv.lvl_ptr[l - 1], hi = g->lv.lvl_ptr[l];
-        if (hi > lo) k_fwd_level<R><<<div_up(hi - lo, 128), 128, 0, cs>>>(t, s, lo, hi);
+    int nk = 0;
+    for (int l = 1; fwd && l <= t.depth && ok; ++l) {
+        const int lo = g->lv.lvl_ptr[l - 1], hi = g->lv.lvl_ptr[l];
+        if (hi > lo) {
+            k_fwd_level<R><<<div_up(hi - lo, kLvThreads), kLvThreads, 0, cs>>>(t, s, lo, hi, L);
+            ++nk;
+        }
         ok = cudaGetLastError() == cudaSuccess;
     }
-    for (int l = t.depth; l >= 0 && ok; --l) {
-        int lo = g->lv.bl_ptr[l], hi = g->lv.bl_ptr[l + 1], ns = g->lv.bl_small[l];
-        int warps = div_up(ns, 32) + (hi - lo - ns);
-        if (warps > 0) k_bwd_level<R><<<div_up((int64_t)warps * 32, 128), 128, 0, cs>>>(t, s, lo, ns, hi);
+    for (int l = t.depth; bwd && l >= 0 && ok; --l) {
+        const int lo = g->lv.bw_lo[l], hi = g->lv.bw_hi[l];
+        if (hi > lo) {
+            k_bwd_level<R><<<div_up((int64_t)(hi - lo) * 32, kLvThreads), kLvThreads, 0, cs>>>(t, s, lo, hi);
+            ++nk;
+        }
         ok = cudaGetLastError() == cudaSuccess;
     }
-    if (ok) {
+    if (bwd && ok) {
         k_wns_tns<R><<<kRedBlocks, kRedThreads, 0, cs>>>(t, s);
+        ++nk;
         ok = cudaGetLastError() == cudaSuccess;
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (!ok || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
-        set_error("sta_propagate: capturing the level sweep failed: %s",
+        set_error("capturing the level sweep failed: %s",
                   cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
         return TDP_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&g->sta_graph, graph, 0);
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-        g->sta_graph = nullptr;
-        set_error("sta_propagate: cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+        *exec = nullptr;
+        set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
         return TDP_ERR_CUDA;
     }
+    *n_kernels = nk;
     return TDP_OK;
 }
+
+// Forward and backward sweeps and WNS / TNS, one graph replay.  The forward
+// sweep also builds sidetrack lists of length g->list_L (0: none).
+template <typename R>
+static tdp_status sweep(tdp_graph *g) {
+    if (!g->sta_graph || g->sta_graph_L != g->list_L) {
+        if (g->sta_graph) cudaGraphExecDestroy(g->sta_graph);
+        g->sta_graph = nullptr;
+        TDP_TRY(capture<R>(g, &g->sta_graph, &g->sta_graph_kernels, true, true, g->list_L));
+        g->sta_graph_L = g->list_L;
+    }
+    g->n_launch += g->sta_graph_kernels;
+    TDP_CUDA(cudaGraphLaunch(g->sta_graph, g->stream));
+    return TDP_OK;
+}
+
+// Forward sweep only, rebuilding sidetrack lists of length g->list_L.  The
+// arrival times it writes are identical to the ones already there.
+template <typename R>
+tdp_status forward_lists(tdp_graph *g) {
+    State<R> &s = state<R>(g);
+    if (!s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * (kMaxK - 1)));
+    if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
+        if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
+        g->fwd_graph = nullptr;
+        TDP_TRY(capture<R>(g, &g->fwd_graph, &g->fwd_graph_kernels, true, false, g->list_L));
+        g->fwd_graph_L = g->list_L;
+    }
+    g->n_launch += g->fwd_graph_kernels;
+    TDP_CUDA(cudaGraphLaunch(g->fwd_graph, g->stream));
+    return TDP_OK;
+}
+
+template tdp_status forward_lists<float>(tdp_graph *);
+template tdp_status forward_lists<double>(tdp_graph *);
 
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    int nsw = div_up(t.n_nets, 32);
-    int64_t threads = (int64_t)(nsw + t.n_big) * 32;
-    k_net_rc<R><<<div_up(threads, 256), 256, 0, g->stream>>>(t, s, x, y, T, (R)g->r, (R)g->c,
-                                                             (R)g->d0, nsw);
+    const int nsb = div_up(t.n_nets, kRcThreads);
+    {
+        LaunchScope ls(g, KID_NET_RC);
+        k_net_rc<R><<<nsb + t.n_big, kRcThreads, 0, g->stream>>>(t, s, x, y, T, (R)g->r, (R)g->c,
+                                                                 (R)g->d0, nsb);
+    }
     TDP_LAUNCH_CHECK();
-    if (!g->sta_graph) TDP_TRY(capture_sta_graph<R>(g));
-    TDP_CUDA(cudaGraphLaunch(g->sta_graph, g->stream));
+    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * (kMaxK - 1)));
+    TDP_TRY(sweep<R>(g));
     return TDP_OK;
 }
 
@@ -303,6 +537,7 @@ template <typename R>
 static tdp_status get_timing_impl(tdp_graph *g, R *arr, R *req, R *slack) {
     State<R> &s = state<R>(g);
     int n = g->topo.n_pins;
+    g->n_launch += (arr ? 1 : 0) + (req ? 1 : 0);
     if (arr) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.arr, arr, n);
     if (req) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.req, req, n);
     TDP_LAUNCH_CHECK();
@@ -340,6 +575,7 @@ extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void 
     if (st != TDP_OK) return st;
     g->propagated = true;
     g->extracted = false;
+    g->lists_valid_L = g->list_L;
     if (wns_out || tns_out) {
         double h[2];
         const double *src = g->prec == TDP_FP32 ? g->s32.wns_tns : g->s64.wns_tns;

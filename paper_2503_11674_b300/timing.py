@@ -189,6 +189,22 @@ class TimingGraph:
                                                 _ptr(grad_scale), _ptr(gx), _ptr(gy)))
         return gx, gy
 
+    # ---------------------------------------------------- instrumentation --
+    def tdp_get_launch_count(self) -> int:
+        n = C.c_int64()
+        _abi.check("tdp_get_launch_count", self.lib.tdp_get_launch_count(self.handle, C.byref(n)))
+        return n.value
+
+    def tdp_profile_kernel(self, name: str | None):
+        _abi.check("tdp_profile_kernel",
+                   self.lib.tdp_profile_kernel(self.handle, None if not name else name.encode()))
+
+    def tdp_profile_read(self):
+        """(number of timed launches, their summed device time in ms); resets."""
+        n, ms = C.c_int64(), C.c_double()
+        _abi.check("tdp_profile_read", self.lib.tdp_profile_read(self.handle, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
     # ----------------------------------------------------------- lifetime --
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

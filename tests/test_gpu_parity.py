@@ -390,3 +390,4 @@ def test_out_of_order_calls_return_state_errors():
     with pytest.raises(_abi.TdpError) as ei:
         G.attraction_set_pairs(np.array([0], np.int32), np.array([1.0]))  # pin 0 is a driver
     assert ei.value.status == _abi.TDP_ERR_INVALID
+
