@@ -231,6 +231,38 @@ TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const vo
                                const double *grad_scale_dev, void *gx_dev, void *gy_dev);
 
 /*
+ * attraction_loss_fwd for callers that cannot allocate device memory (no
+ * counterpart in the paper): code working inside a device-memory budget fixed
+ * in advance, code whose allocator owns all device memory, or code that must
+ * not allocate after start-up cannot call sta_build, which allocates.  This
+ * entry point needs no tdp_graph and calls no cudaMalloc, cudaFree or other
+ * allocating routine: every input and the output are caller device arrays,
+ * and its temporary storage (one FP64 partial sum per 256 nets and a block
+ * counter) is a static device array of the library, 128 KiB + 4 bytes held
+ * on every GPU that loads the library until the process exits.
+ *   n_nets        nets; at most 4,194,304 (more: TDP_ERR_INVALID)
+ *   net_ptr_dev   int32[n_nets+1] pins of each net, driver first (as sta_build)
+ *   pin_cell_dev  int32[n_pins], pin_dx_dev / pin_dy_dev float[n_pins] (um)
+ *   w_dev         float[n_pins] weight of the pair (driver, pin) of every sink
+ *                 pin; 0 for pins not in P (and ignored on drivers)
+ *   x_dev, y_dev  float[n_cells] cell positions
+ *   loss_dev      one device double, overwritten with
+ *                 beta * sum over sinks s with w_s != 0 of w_s * Q(driver, s)
+ *   cuda_stream   cudaStream_t the work is queued on (NULL: legacy stream)
+ * FP32 terms, FP64 sums, fixed-order reduction (deterministic).  The first
+ * call on a device looks up the scratch address for that device (with it
+ * current); make that first call before capturing any stream into a CUDA
+ * graph.  All calls on a device share the scratch: calls that overlap on the
+ * GPU (other streams, or graph replays running at once) race and give wrong
+ * results; calls queued on one stream are safe.
+ */
+TDP_API tdp_status attraction_loss_fwd_noalloc(int32_t n_nets, const int32_t *net_ptr_dev,
+                                               const int32_t *pin_cell_dev, const float *pin_dx_dev,
+                                               const float *pin_dy_dev, const float *w_dev,
+                                               const float *x_dev, const float *y_dev, double beta,
+                                               double *loss_dev, void *cuda_stream);
+
+/*
  * Instrumentation (no counterpart in the paper).
  * tdp_get_launch_count: number of kernels this graph has queued so far
  * (graph replays count every kernel node).

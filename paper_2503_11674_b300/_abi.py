@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "TDP_OK", 1: "TDP_ERR_INVALID", 2: "TDP_ERR_CYCLE", 3: "TDP_E
 EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_get_net_delays",
            "extract_critical_paths", "sta_get_paths_size", "sta_get_paths",
            "attraction_update_pairs", "attraction_reset_pairs", "attraction_set_pairs",
-           "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd", "tdp_get_launch_count",
+           "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
+           "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
            "tdp_profile_kernel", "tdp_profile_read", "tdp_last_error"]
 
 
@@ -67,6 +68,7 @@ def load() -> C.CDLL:
         "attraction_get_pairs": [P, P, P, P],
         "attraction_loss_fwd": [P, P, P, D, P],
         "attraction_loss_bwd": [P, P, P, D, P, P, P],
+        "attraction_loss_fwd_noalloc": [I32, P, P, P, P, P, P, P, D, P, P],
         "tdp_get_launch_count": [P, P],
         "tdp_profile_kernel": [P, C.c_char_p],
         "tdp_profile_read": [P, P, P],
