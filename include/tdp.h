@@ -267,10 +267,10 @@ TDP_API tdp_status attraction_loss_fwd_noalloc(int32_t n_nets, const int32_t *ne
  * tdp_get_launch_count: number of kernels this graph has queued so far
  * (graph replays count every kernel node).
  * tdp_profile_kernel: time every later launch of the named kernel with a pair
- * of CUDA events on the graph's stream ("net_rc", "viol_sort" (the whole
- * endpoint sort), "topk", "pair_walk", "pair_finish", "pp_fwd", "pp_bwd_net",
- * "pp_bwd_cell"; NULL or "" stops).  The level sweeps and the WNS / TNS
- * reduction run inside CUDA graphs and cannot be selected (TDP_ERR_INVALID).
+ * of CUDA events on the graph's stream: "net_rc", "fwd_sweep" (one replay of
+ * the forward level kernels), "bwd_sweep" (the backward level kernels and
+ * WNS / TNS), "viol_sort" (the whole endpoint sort), "topk", "pair_walk",
+ * "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell"; NULL or "" stops.
  * tdp_profile_read: synchronise the stream, return the number of timed
  * launches and their summed device time in ms, and reset both.
  */

@@ -99,8 +99,8 @@ static bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
 static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     Topo &t = g->topo;
     const int nc = d->n_cells, np = d->n_pins, nn = d->n_nets;
-    if (nc <= 0 || np <= 0 || nn <= 0) {
-        set_error("sta_build: n_cells, n_pins and n_nets must be positive");
+    if (nc <= 0 || np <= 0 || nn <= 0 || np >= (1 << 29)) {
+        set_error("sta_build: n_cells, n_pins and n_nets must be positive, n_pins below 2^29");
         return TDP_ERR_INVALID;
     }
     if (!d->pin_cell || !d->net_ptr || !d->pin_dir || !d->cell_type || !d->pin_dx ||
@@ -302,47 +302,48 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             bl_net[small ? fs[l]++ : fb[l]++] = e;
         }
     }
-    // backward tasks, highest level first; tasks of level l: [bw_ptr[l], bw_ptr[l+1])
+    // backward tasks per level: groups of 32 nets of at most kBwSmallFanout
+    // sinks (lane l of group q handles the net whose driver is bw_sa[32q + l]
+    // and whose pins end at bw_sb[32q + l]; -1 pads), and pieces of
+    // kBwPart sinks of the larger nets
     std::vector<BwTask> bw;
-    std::vector<int32_t> bw_nets;
+    std::vector<int32_t> bw_sa, bw_sb;
     int n_slots = 0, n_split = 0;
-    std::vector<int32_t> lvl_first(D + 1, 0), lvl_count(D + 1, 0);
+    std::vector<int32_t> s_lo(D + 1), s_n(D + 1), b_lo(D + 1), b_n(D + 1);
     for (int l = D; l >= 0; --l) {
-        lvl_first[l] = (int32_t)bw.size();
-        std::vector<int32_t> small;
+        s_lo[l] = (int32_t)(bw_sa.size() / 32);
+        b_lo[l] = (int32_t)bw.size();
         for (int q = bl_ptr[l]; q < bl_ptr[l + 1]; ++q) {
-            int e = bl_net[q];
-            int f = d->net_ptr[e + 1] - d->net_ptr[e] - 1;
+            const int e = bl_net[q];
+            const int a = d->net_ptr[e], b = d->net_ptr[e + 1];
+            const int f = b - a - 1;
             if (f <= kBwSmallFanout) {
-                small.push_back(e);
+                bw_sa.push_back(a);
+                bw_sb.push_back(b);
                 continue;
             }
-            int parts = (f + kBwPart - 1) / kBwPart;
-            int cnt = parts > 1 ? n_split++ : -1;
+            const int parts = (f + kBwPart - 1) / kBwPart;
+            const int cnt = parts > 1 ? n_split++ : -1;
             for (int j = 0; j < parts; ++j) {
-                int p0 = d->net_ptr[e] + 1 + j * kBwPart;
-                int p1 = std::min(d->net_ptr[e + 1], p0 + kBwPart);
-                bw.push_back(BwTask{1, e, p0, p1, parts > 1 ? n_slots + j : -1, parts, cnt, j});
+                const int p0 = a + 1 + j * kBwPart;
+                const int p1 = std::min(b, p0 + kBwPart);
+                bw.push_back(BwTask{a, p0, p1, parts > 1 ? n_slots + j : -1, parts, cnt, j, 0});
             }
             if (parts > 1) n_slots += parts;
         }
-        for (size_t q = 0; q < small.size(); q += 32) {
-            int cnt = (int)std::min<size_t>(32, small.size() - q);
-            bw.push_back(BwTask{0, -1, (int)bw_nets.size(), cnt, -1, 1, -1, 0});
-            bw_nets.insert(bw_nets.end(), small.begin() + q, small.begin() + q + cnt);
+        while (bw_sa.size() % 32) {
+            bw_sa.push_back(-1);
+            bw_sb.push_back(-1);
         }
-        lvl_count[l] = (int32_t)bw.size() - lvl_first[l];
-    }
-    std::vector<int32_t> bw_lo(D + 1), bw_hi(D + 1);
-    for (int l = 0; l <= D; ++l) {
-        bw_lo[l] = lvl_first[l];
-        bw_hi[l] = lvl_first[l] + lvl_count[l];
+        s_n[l] = (int32_t)(bw_sa.size() / 32) - s_lo[l];
+        b_n[l] = (int32_t)bw.size() - b_lo[l];
     }
     t.n_bw_tasks = (int32_t)bw.size();
     t.n_bw_slots = n_slots;
     t.n_bw_split = n_split;
     TDP_TRY(upload(g, &t.bw_task, bw));
-    TDP_TRY(upload(g, &t.bw_nets, bw_nets));
+    TDP_TRY(upload(g, &t.bw_sa, bw_sa));
+    TDP_TRY(upload(g, &t.bw_sb, bw_sb));
     t.n_cells = nc;
     t.n_pins = np;
     t.n_nets = nn;
@@ -352,8 +353,10 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     t.depth = D;
     t.n_big = (int32_t)big.size();
     g->lv.lvl_ptr = lvl_ptr;
-    g->lv.bw_lo = bw_lo;
-    g->lv.bw_hi = bw_hi;
+    g->lv.bw_s_lo = s_lo;
+    g->lv.bw_s_n = s_n;
+    g->lv.bw_b_lo = b_lo;
+    g->lv.bw_b_n = b_n;
     std::vector<int32_t> pc(d->pin_cell, d->pin_cell + np), nptr(d->net_ptr, d->net_ptr + nn + 1);
     std::vector<uint8_t> fixed(d->cell_fixed, d->cell_fixed + nc);
     TDP_TRY(upload(g, &t.pin_cell, pc));
@@ -383,8 +386,9 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
 
 namespace tdp {
 
-const char *const kKernelNames[KID_COUNT] = {"net_rc", "viol_sort", "topk", "pair_walk",
-                                              "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell"};
+const char *const kKernelNames[KID_COUNT] = {"net_rc",    "fwd_sweep",   "bwd_sweep", "viol_sort",
+                                              "topk",      "pair_walk",   "pair_finish", "pp_fwd",
+                                              "pp_bwd_net", "pp_bwd_cell"};
 
 static cudaEvent_t prof_event(tdp_graph *g) {
     if (!g->prof_free.empty()) {
@@ -468,8 +472,8 @@ extern "C" tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, doub
 
 extern "C" void sta_destroy(tdp_graph *g) {
     if (!g) return;
-    if (g->sta_graph) cudaGraphExecDestroy(g->sta_graph);
     if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
+    if (g->bwd_graph) cudaGraphExecDestroy(g->bwd_graph);
     for (auto &pr : g->prof_pending) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);

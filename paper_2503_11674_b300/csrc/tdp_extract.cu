@@ -320,7 +320,7 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     // 2. sidetrack lists: the next sweeps build K - 1 entries per node; if the
     //    current lists are shorter, rebuild them now with the forward sweep
     if (K > 1 && t.n_ep > 0) {
-        g->list_L = K - 1;
+        g->list_L = list_bucket(K - 1);
         if (g->lists_valid_L < K - 1) {
             TDP_TRY(forward_lists<R>(g));
             g->lists_valid_L = g->list_L;

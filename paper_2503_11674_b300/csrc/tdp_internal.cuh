@@ -44,11 +44,13 @@ constexpr double kQClamp = 32768.0;     // |slack/WNS| is clamped here before co
 
 enum PinKind : uint8_t { PK_COMB_IN = 0, PK_ENDPOINT = 1, PK_COMB_OUT = 2, PK_START = 3 };
 
-// Kernels that can be timed with tdp_profile_kernel (names in tdp_build.cu);
-// the level sweeps and WNS / TNS are replayed inside CUDA graphs.
+// Kernels that can be timed with tdp_profile_kernel (names in tdp_build.cu).
+// The level sweeps are replayed from CUDA graphs: fwd_sweep is one replay of
+// the forward level kernels, bwd_sweep one of the backward level kernels and
+// the WNS / TNS reduction.
 enum KernelId {
-    KID_NET_RC, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK, KID_PAIR_FINISH, KID_PP_FWD,
-    KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_COUNT
+    KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
+    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -117,6 +119,29 @@ __device__ __forceinline__ fx2 ldg(const fx2 *p) {
     return fx2{v.x, v.y};
 }
 
+// Programmatic dependent launch between the kernels of a sweep: a kernel lets
+// its successor launch as soon as it starts, and the successor reads only
+// static topology until pdl_wait() returns, which happens once every earlier
+// kernel of the stream has finished and its writes are visible.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // One sidetrack entry of a node's list: the deviation cost delta >= 0 of
 // entering a node through a non-worst input pin instead of its worst one.
 template <typename R>
@@ -134,13 +159,12 @@ __device__ __forceinline__ BEnt<double> ldg(const BEnt<double> *p) {
     return BEnt<double>{v.x, (int32_t)(__double_as_longlong(v.y) & 0xffffffffll)};
 }
 
-// One task of the backward sweep (one warp).
-//   kind 0: nets bw_nets[p0 .. p0+p1) (at most 32 nets of at most 8 sinks), one per lane;
-//   kind 1: sinks [p0, p1) of net `net`; when the net is split into nparts
-//           tasks, task `part` writes its minimum to `slot` and the last task
-//           to finish (counter `cnt`) combines the slots.
+// One warp's piece of a net with more than kBwSmallFanout sinks in the
+// backward sweep: sinks [p0, p1) of the net driven by pin drv.  When the net
+// is split into nparts pieces, piece `part` writes its minimum to `slot` and
+// the last piece to finish (counter `cnt`) combines the slots.
 struct BwTask {
-    int32_t kind, net, p0, p1, slot, nparts, cnt, part;
+    int32_t drv, p0, p1, slot, nparts, cnt, part, pad;
 };
 constexpr int kBwSmallFanout = 8;    // nets up to this fanout are handled one per lane
 constexpr int kBwPart = 128;         // sinks per warp task of a larger net
@@ -169,16 +193,19 @@ struct Topo {
     int32_t *cp = nullptr;         // [n_pins]
     int32_t *slot_of_pin = nullptr;// [n_pins] position of a pin in cp
     uint8_t *cell_fixed = nullptr; // [n_cells]
-    // backward sweep tasks, highest level first
+    // backward sweep, highest level first: groups of 32 small nets given by
+    // driver pin / end pin per lane (-1 pads), and pieces of larger nets
+    int32_t *bw_sa = nullptr, *bw_sb = nullptr;
     BwTask *bw_task = nullptr;
-    int32_t *bw_nets = nullptr;    // small nets in task order
     int32_t n_bw_tasks = 0, n_bw_slots = 0, n_bw_split = 0;
 };
 
 // Host copies of the launch structure of the level sweeps.
 struct Levels {
     std::vector<int32_t> lvl_ptr;   // comb cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
-    std::vector<int32_t> bw_lo, bw_hi;  // backward tasks of level l: [bw_lo[l], bw_hi[l])
+    // backward sweep of level l: small-net groups [bw_s_lo[l], +bw_s_n[l]),
+    // pieces of larger nets [bw_b_lo[l], +bw_b_n[l])
+    std::vector<int32_t> bw_s_lo, bw_s_n, bw_b_lo, bw_b_n;
 };
 
 template <typename R>
@@ -236,8 +263,8 @@ struct tdp_graph {
     // sidetrack lists are built by the forward sweep: list_L entries per node
     // (the K - 1 of the last extraction), lists_valid_L of them are current
     int list_L = 0, lists_valid_L = 0;
-    cudaGraphExec_t sta_graph = nullptr, fwd_graph = nullptr;
-    int sta_graph_L = -1, fwd_graph_L = -1, sta_graph_kernels = 0, fwd_graph_kernels = 0;
+    cudaGraphExec_t fwd_graph = nullptr, bwd_graph = nullptr;  // captured level sweeps
+    int fwd_graph_L = -1, fwd_graph_kernels = 0, bwd_graph_kernels = 0;
     std::vector<void *> allocs;  // every device allocation, freed in sta_destroy
     // instrumentation
     int64_t n_launch = 0;                 // kernels queued by this graph so far
@@ -292,6 +319,15 @@ tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_
                            cudaStream_t st);
 
 inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// Sidetrack list lengths the forward sweep builds (one kernel each): the
+// smallest that holds `need` entries.
+inline int list_bucket(int need) {
+    const int lens[] = {0, 3, 7, 15, 31};
+    for (int l : lens)
+        if (l >= need) return l;
+    return kMaxK - 1;
+}
 
 // Brackets the launches of one kernel with CUDA events on the graph's stream
 // when that kernel is selected by tdp_profile_kernel; counts launches always.

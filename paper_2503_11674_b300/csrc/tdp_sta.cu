@@ -113,165 +113,201 @@ __global__ void __launch_bounds__(kRcThreads) k_net_rc(Topo t, State<R> s, const
 
 constexpr int kLvThreads = 128;
 
+// A list entry while a list is being built: the deviation cost and a key that
+// orders equal costs.  key = (group << 29) | pin, group 0 for the node's own
+// deviations through a pin below its worst input, 1 for inherited entries, 2
+// for own deviations through a pin above the worst input.  Own entries are
+// only ever compared with entries of other groups or with own entries, so the
+// pins of inherited entries never decide an order.
 template <typename R>
-__device__ __forceinline__ BEnt<R> bent_none() {
-    return BEnt<R>{(R)__longlong_as_double(0x7ff0000000000000ll), -1};
+struct LEnt {
+    R d;
+    uint32_t key;
+};
+constexpr uint32_t kPinMask = (1u << 29) - 1u;
+constexpr uint32_t kNoneKey = 0xffffffffu;
+
+template <typename R>
+__device__ __forceinline__ bool lent_before(const LEnt<R> &a, const LEnt<R> &b) {
+    return a.d < b.d || (a.d == b.d && a.key < b.key);
+}
+
+template <typename R>
+__device__ __forceinline__ R r_inf() {
+    return (R)__longlong_as_double(0x7ff0000000000000ll);
 }
 
 // Sidetrack list of one node (Section III-B extraction): the L cheapest
 // deviations on the worst-input chain from the node back to its startpoint.
 // A deviation enters a node through an input other than its worst one; its
-// cost is Arr(worst input) - Arr(that input).  The list is the merge of the
-// node's own deviations with the list of its worst input's driver.  Equal
-// costs are ordered as the resulting paths' pin sequences (read from the
-// endpoint) would be: own deviations through a pin below the worst input,
-// then the inherited entries, then own deviations through a pin above it.
-// Lists hold exactly L entries; unused ones are +inf sentinels (pin -1).
-template <typename R>
-__device__ __forceinline__ void build_sidetracks(const Topo &t, State<R> &s, int e, int bi,
-                                                 int bn, bool bn_comb,
-                                                 typename Acc<R>::T best, const int *ip,
-                                                 const typename Acc<R>::T *ain, int nin, int L) {
+// cost is Arr(worst input) - Arr(that input).  The list is the node's own
+// deviations merged into the list of its worst input's driver; equal costs
+// are ordered as the resulting paths' pin sequences (read from the endpoint)
+// would be: own deviations through a pin below the worst input, then the
+// inherited entries, then own deviations through a pin above it.  Lists hold
+// exactly L entries; unused ones are +inf sentinels (pin -1).
+template <typename R, int L, int NIN>
+__device__ __forceinline__ void build_list(State<R> &s, int e, int bi, int bn, bool bn_comb,
+                                           typename Acc<R>::T best, const int *ip,
+                                           const typename Acc<R>::T *ain, int nin) {
     using AC = Acc<R>;
-    BEnt<R> pl[kMaxK - 1];
-    if (bn_comb) {  // issue the inherited list's loads before anything else
+    LEnt<R> li[L];
+    if (bn_comb) {  // the inherited list (written by an earlier level's launch)
         const BEnt<R> *src = s.blist + (size_t)bn * L;
-        for (int j = 0; j < L; ++j) pl[j] = ldg(&src[j]);
-    }
-    R od[kMaxFanin];
-    int op[kMaxFanin];
-    int no = 0;
-    for (int u = 0; u < nin; ++u) {
-        const int i = ip[u];
-        if (i == bi) continue;
-        const R d = AC::diff(best, ain[u]);
-        int pos = no;
-        while (pos > 0) {  // insertion by (delta, side of the worst input, pin)
-            const R dp = od[pos - 1];
-            const int pp = op[pos - 1];
-            const bool before = d < dp || (d == dp && ((i < bi) != (pp < bi) ? (i < bi) : i < pp));
-            if (!before) break;
-            od[pos] = dp;
-            op[pos] = pp;
-            --pos;
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const BEnt<R> v = ldg(&src[j]);
+            li[j] = LEnt<R>{v.delta, v.pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)v.pin)};
         }
-        od[pos] = d;
-        op[pos] = i;
-        ++no;
+    } else {
+#pragma unroll
+        for (int j = 0; j < L; ++j) li[j] = LEnt<R>{r_inf<R>(), kNoneKey};
+    }
+#pragma unroll
+    for (int u = 0; u < NIN; ++u) {
+        if (u >= nin || ip[u] == bi) continue;
+        const LEnt<R> x{AC::diff(best, ain[u]), ((ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)ip[u]};
+        // insert x, keeping the first L entries (compare-and-shift from the top)
+#pragma unroll
+        for (int j = L - 1; j >= 0; --j) {
+            const bool shift = j > 0 && lent_before(x, li[j - 1]);
+            const bool here = lent_before(x, li[j]);
+            li[j] = shift ? li[j - 1] : (here ? x : li[j]);
+        }
     }
     BEnt<R> *out = s.blist + (size_t)e * L;
-    int ia = 0, ib = 0, m = 0;
-    for (; m < L; ++m) {
-        const bool ha = ia < no;
-        const bool hb = bn_comb && ib < L && pl[ib].pin >= 0;
-        if (!ha && !hb) break;
-        bool take_own;
-        if (!hb) take_own = true;
-        else if (!ha) take_own = false;
-        else take_own = od[ia] < pl[ib].delta || (od[ia] == pl[ib].delta && op[ia] < bi);
-        if (take_own) {
-            out[m] = BEnt<R>{od[ia], op[ia]};
-            ++ia;
-        } else {
-            out[m] = pl[ib];
-            ++ib;
-        }
+    int m = 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const bool none = li[j].key == kNoneKey;
+        out[j] = BEnt<R>{li[j].d, none ? -1 : (int32_t)(li[j].key & kPinMask)};
+        m += none ? 0 : 1;
     }
     s.bcnt[e] = m;
-    for (int j = m; j < L; ++j) out[j] = bent_none<R>();
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kLvThreads) k_fwd_level(Topo t, State<R> s, int lo, int hi, int L) {
+// Arrival of one combinational cell (k in level order) whose inputs are
+// [a, b) with b - a <= NIN; builds its sidetrack list when L > 0.
+template <typename R, int L, int NIN>
+__device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, int k, int a, int b) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= hi) return;
-    const int a = ldg(&t.lv_in_ptr[k]), b = ldg(&t.lv_in_ptr[k + 1]);
     const int e = ldg(&t.lv_onet[k]), o = ldg(&t.lv_out[k]);
+    int ip[NIN], in[NIN], dv[NIN], pl[NIN];
+    uint8_t cb[NIN];
+    A av[NIN];
+    R tv[NIN];
+    // every load of the cell's inputs first, then the arithmetic, then stores
+#pragma unroll
+    for (int u = 0; u < NIN; ++u) {
+        if (a + u < b) {
+            ip[u] = ldg(&t.lv_in_pin[a + u]);
+            in[u] = ldg(&t.lv_in_net[a + u]);
+            dv[u] = ldg(&t.lv_in_drv[a + u]);
+            cb[u] = ldg(&t.lv_in_comb[a + u]);
+        }
+    }
+    pdl_wait();  // everything below reads values earlier kernels wrote
     const R dcell = ldg(&s.dnet[e]);
+#pragma unroll
+    for (int u = 0; u < NIN; ++u) {
+        if (a + u < b) {
+            av[u] = ldg(&s.arr[dv[u]]);
+            tv[u] = ldg(&s.tnet[ip[u]]);
+            pl[u] = ldg(&s.plen[in[u]]);
+        }
+    }
     // inputs ascending by pin: strict > keeps the lowest pin on ties (and the
     // first input if arrivals are not comparable)
     int bi = -1, bn = -1, bl = 0;
     bool bc = false;
     A best = AC::ninf();
-    int ipa[kMaxFanin];
-    A ain[kMaxFanin];
-    for (int q0 = a; q0 < b; q0 += kPre) {
-        int ip[kPre], in[kPre], dv[kPre], pl[kPre];
-        uint8_t cb[kPre];
-        A av[kPre];
-        R tv[kPre];
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            if (q0 + u < b) {
-                ip[u] = ldg(&t.lv_in_pin[q0 + u]);
-                in[u] = ldg(&t.lv_in_net[q0 + u]);
-                dv[u] = ldg(&t.lv_in_drv[q0 + u]);
-                cb[u] = ldg(&t.lv_in_comb[q0 + u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            if (q0 + u < b) {
-                av[u] = ldg(&s.arr[dv[u]]);
-                tv[u] = ldg(&s.tnet[ip[u]]);
-                pl[u] = ldg(&s.plen[in[u]]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            if (q0 + u < b) {
-                const A v = AC::add(av[u], tv[u]);
-                s.arr[ip[u]] = v;
-                ipa[q0 - a + u] = ip[u];
-                ain[q0 - a + u] = v;
-                if (bi < 0 || AC::gt(v, best)) {
-                    best = v;
-                    bi = ip[u];
-                    bn = in[u];
-                    bl = pl[u];
-                    bc = cb[u];
-                }
+    for (int u = 0; u < NIN; ++u) {
+        if (a + u < b) {
+            av[u] = AC::add(av[u], tv[u]);
+            if (bi < 0 || AC::gt(av[u], best)) {
+                best = av[u];
+                bi = ip[u];
+                bn = in[u];
+                bl = pl[u];
+                bc = cb[u];
             }
         }
     }
+#pragma unroll
+    for (int u = 0; u < NIN; ++u)
+        if (a + u < b) s.arr[ip[u]] = av[u];
     s.arr[o] = AC::add(best, dcell);
     s.pred_in[e] = bi;
     s.pred_net[e] = bn;
     s.plen[e] = bl + 2;
-    if (L > 0) build_sidetracks<R>(t, s, e, bi, bn, bc, best, ipa, ain, b - a, L);
+    if constexpr (L > 0) build_list<R, L, NIN>(s, e, bi, bn, bc, best, ip, av, b - a);
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(kLvThreads) k_fwd_level(Topo t, State<R> s, int lo, int hi) {
+    pdl_trigger();
+    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= hi) return;
+    const int a = ldg(&t.lv_in_ptr[k]), b = ldg(&t.lv_in_ptr[k + 1]);
+    if (b - a <= kPre) fwd_cell<R, L, kPre>(t, s, k, a, b);
+    else fwd_cell<R, L, kMaxFanin>(t, s, k, a, b);
+}
+
+template <typename R>
+static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, cudaStream_t cs) {
+    const int grid = div_up(hi - lo, kLvThreads);
+    switch (L) {
+        case 0: launch_pdl(k_fwd_level<R, 0>, grid, kLvThreads, cs, t, s, lo, hi); break;
+        case 3: launch_pdl(k_fwd_level<R, 3>, grid, kLvThreads, cs, t, s, lo, hi); break;
+        case 7: launch_pdl(k_fwd_level<R, 7>, grid, kLvThreads, cs, t, s, lo, hi); break;
+        case 15: launch_pdl(k_fwd_level<R, 15>, grid, kLvThreads, cs, t, s, lo, hi); break;
+        default: launch_pdl(k_fwd_level<R, 31>, grid, kLvThreads, cs, t, s, lo, hi); break;
+    }
 }
 
 // ----------------------------------------------------------- backward ---
 
-// req / slack of the sinks first, first+step, ... < b of a net whose driver
-// has arrival ad; returns min over them of req(s) - t(s).
-template <typename R>
+// req / slack of the sinks first, first+step, ... < b of the net driven by
+// pin a, NP sinks per round of loads; returns min over them of req(s) - t(s)
+// and the driver's arrival in ad.  The first round's topology loads are
+// issued before pdl_wait().
+template <typename R, int NP>
 __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State<R> &s, int first,
-                                                            int b, int step,
-                                                            typename Acc<R>::T ad,
-                                                            typename Acc<R>::T Tacc) {
+                                                            int b, int step, int a,
+                                                            typename Acc<R>::T &ad) {
     using AC = Acc<R>;
     using A = typename AC::T;
     A m = AC::pinf();
-    for (int p0 = first; p0 < b; p0 += kPre * step) {
-        uint8_t kd[kPre];
-        R tp[kPre];
-        int so[kPre], sn[kPre];
+    uint8_t kd[NP];
+    int so[NP], sn[NP];
+    auto topo_loads = [&](int p0) {
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
+        for (int u = 0; u < NP; ++u) {
             const int p = p0 + u * step;
             if (p < b) {
                 kd[u] = ldg(&t.pin_kind[p]);
-                tp[u] = ldg(&s.tnet[p]);
                 so[u] = ldg(&t.sink_out[p]);
                 sn[u] = ldg(&t.sink_onet[p]);
             }
         }
-        A rq[kPre], ap[kPre];
+    };
+    topo_loads(first);
+    pdl_wait();  // everything below reads values earlier kernels wrote
+    ad = ldg(&s.arr[a]);
+    const A Tacc = acc_from_double<R>(*s.T);
+    for (int p0 = first; p0 < b; p0 += NP * step) {
+        if (p0 != first) topo_loads(p0);
+        R tp[NP];
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
+        for (int u = 0; u < NP; ++u) {
+            const int p = p0 + u * step;
+            if (p < b) tp[u] = ldg(&s.tnet[p]);
+        }
+        A rq[NP], ap[NP];
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
             const int p = p0 + u * step;
             if (p < b) {
                 if (kd[u] == PK_ENDPOINT) {
@@ -284,7 +320,7 @@ __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State
             }
         }
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
+        for (int u = 0; u < NP; ++u) {
             const int p = p0 + u * step;
             if (p < b) {
                 if (kd[u] == PK_ENDPOINT) s.arr[p] = ap[u];
@@ -317,29 +353,32 @@ __device__ __forceinline__ fx2 ldcg_acc(const fx2 *p) {
     return fx2{v.x, v.y};
 }
 
-// One warp per task of this level (tasks [lo, hi) of the backward list).
+// One warp per task of this level: warps [0, ns) take groups s_lo.. of 32
+// small nets (a lane per net, all its sinks in one round of loads), warps
+// [ns, ns + nb) take pieces b_lo.. of larger nets (lanes stride the sinks).
 template <typename R>
-__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int lo, int hi) {
+__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int s_lo, int ns,
+                                                          int b_lo, int nb) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    const int w = lo + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    pdl_trigger();
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (w >= hi) return;
-    const A Tacc = acc_from_double<R>(*s.T);
-    const BwTask task = t.bw_task[w];
-    if (task.kind == 0) {
-        if (lane >= task.p1) return;
-        const int e = ldg(&t.bw_nets[task.p0 + lane]);
-        const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
-        const A ad = ldg(&s.arr[a]);
-        const A m = net_sinks_req<R>(t, s, a + 1, b, 1, ad, Tacc);
+    if (w < ns) {
+        const int i = (s_lo + w) * 32 + lane;
+        const int a = ldg(&t.bw_sa[i]), b = ldg(&t.bw_sb[i]);
+        if (a < 0) return;
+        A ad;
+        const A m = net_sinks_req<R, kBwSmallFanout>(t, s, a + 1, b, 1, a, ad);
         s.req[a] = m;
         s.slack[a] = AC::diff(m, ad);
         return;
     }
-    const int a = ldg(&t.net_ptr[task.net]);
-    const A ad = ldg(&s.arr[a]);
-    A m = net_sinks_req<R>(t, s, task.p0 + lane, task.p1, 32, ad, Tacc);
+    if (w >= ns + nb) return;
+    const BwTask task = t.bw_task[b_lo + (w - ns)];
+    const int a = task.drv;
+    A ad;
+    A m = net_sinks_req<R, kPre>(t, s, task.p0 + lane, task.p1, 32, a, ad);
     for (int o = 16; o > 0; o >>= 1) {  // min is exact: any order gives the same value
         const A other = shfl_xor_acc(m, o);
         if (AC::lt(other, m)) m = other;
@@ -377,6 +416,7 @@ template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
     __shared__ double smin[kRedThreads / 32], ssum[kRedThreads / 32];
     __shared__ bool last;
+    pdl_wait();
     double mn = 0.0, sm = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < t.n_ep; i += gridDim.x * blockDim.x) {
         double v = (double)s.slack[t.ep[i]];
@@ -436,21 +476,22 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     for (int l = 1; fwd && l <= t.depth && ok; ++l) {
         const int lo = g->lv.lvl_ptr[l - 1], hi = g->lv.lvl_ptr[l];
         if (hi > lo) {
-            k_fwd_level<R><<<div_up(hi - lo, kLvThreads), kLvThreads, 0, cs>>>(t, s, lo, hi, L);
+            launch_fwd<R>(t, s, lo, hi, L, cs);
             ++nk;
         }
         ok = cudaGetLastError() == cudaSuccess;
     }
     for (int l = t.depth; bwd && l >= 0 && ok; --l) {
-        const int lo = g->lv.bw_lo[l], hi = g->lv.bw_hi[l];
-        if (hi > lo) {
-            k_bwd_level<R><<<div_up((int64_t)(hi - lo) * 32, kLvThreads), kLvThreads, 0, cs>>>(t, s, lo, hi);
+        const int ns = g->lv.bw_s_n[l], nb = g->lv.bw_b_n[l];
+        if (ns + nb > 0) {
+            launch_pdl(k_bwd_level<R>, div_up((int64_t)(ns + nb) * 32, kLvThreads), kLvThreads, cs, t, s,
+                       g->lv.bw_s_lo[l], ns, g->lv.bw_b_lo[l], nb);
             ++nk;
         }
         ok = cudaGetLastError() == cudaSuccess;
     }
     if (bwd && ok) {
-        k_wns_tns<R><<<kRedBlocks, kRedThreads, 0, cs>>>(t, s);
+        launch_pdl(k_wns_tns<R>, kRedBlocks, kRedThreads, cs, t, s);
         ++nk;
         ok = cudaGetLastError() == cudaSuccess;
     }
@@ -473,36 +514,36 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     return TDP_OK;
 }
 
-// Forward and backward sweeps and WNS / TNS, one graph replay.  The forward
-// sweep also builds sidetrack lists of length g->list_L (0: none).
-template <typename R>
-static tdp_status sweep(tdp_graph *g) {
-    if (!g->sta_graph || g->sta_graph_L != g->list_L) {
-        if (g->sta_graph) cudaGraphExecDestroy(g->sta_graph);
-        g->sta_graph = nullptr;
-        TDP_TRY(capture<R>(g, &g->sta_graph, &g->sta_graph_kernels, true, true, g->list_L));
-        g->sta_graph_L = g->list_L;
-    }
-    g->n_launch += g->sta_graph_kernels;
-    TDP_CUDA(cudaGraphLaunch(g->sta_graph, g->stream));
-    return TDP_OK;
-}
-
-// Forward sweep only, rebuilding sidetrack lists of length g->list_L.  The
-// arrival times it writes are identical to the ones already there.
+// Forward sweep (one graph replay), building sidetrack lists of length
+// g->list_L (0: none).  Run again, it writes the same arrival times.
 template <typename R>
 tdp_status forward_lists(tdp_graph *g) {
     State<R> &s = state<R>(g);
-    if (!s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * (kMaxK - 1)));
+    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * (kMaxK - 1)));
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
         if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
         g->fwd_graph = nullptr;
         TDP_TRY(capture<R>(g, &g->fwd_graph, &g->fwd_graph_kernels, true, false, g->list_L));
         g->fwd_graph_L = g->list_L;
     }
-    g->n_launch += g->fwd_graph_kernels;
+    LaunchScope ls(g, KID_FWD_SWEEP, g->fwd_graph_kernels);
     TDP_CUDA(cudaGraphLaunch(g->fwd_graph, g->stream));
     return TDP_OK;
+}
+
+// Backward sweep and WNS / TNS (one graph replay).
+template <typename R>
+static tdp_status backward(tdp_graph *g) {
+    if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
+    LaunchScope ls(g, KID_BWD_SWEEP, g->bwd_graph_kernels);
+    TDP_CUDA(cudaGraphLaunch(g->bwd_graph, g->stream));
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status sweep(tdp_graph *g) {
+    TDP_TRY(forward_lists<R>(g));
+    return backward<R>(g);
 }
 
 template tdp_status forward_lists<float>(tdp_graph *);
