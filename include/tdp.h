@@ -50,7 +50,9 @@ typedef enum {
     TDP_ERR_CYCLE = 2,    /* combinational loop in the netlist                  */
     TDP_ERR_OOM = 3,      /* device or host allocation failed                   */
     TDP_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed        */
-    TDP_ERR_STATE = 5     /* call out of order (e.g. extract before propagate)  */
+    TDP_ERR_STATE = 5,    /* call out of order (e.g. extract before propagate)  */
+    TDP_ERR_TIMEOUT = 6   /* a level sweep's grid-wide wait gave up (bounded);
+                             the results of that call are not valid           */
 } tdp_status;
 
 typedef enum { TDP_FP32 = 0, TDP_FP64 = 1 } tdp_precision;

@@ -11,10 +11,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libtdp_b300.so")
 
-TDP_OK, TDP_ERR_INVALID, TDP_ERR_CYCLE, TDP_ERR_OOM, TDP_ERR_CUDA, TDP_ERR_STATE = range(6)
+TDP_OK, TDP_ERR_INVALID, TDP_ERR_CYCLE, TDP_ERR_OOM, TDP_ERR_CUDA, TDP_ERR_STATE, TDP_ERR_TIMEOUT = range(7)
 TDP_FP32, TDP_FP64 = 0, 1
 STATUS_NAMES = {0: "TDP_OK", 1: "TDP_ERR_INVALID", 2: "TDP_ERR_CYCLE", 3: "TDP_ERR_OOM",
-                4: "TDP_ERR_CUDA", 5: "TDP_ERR_STATE"}
+                4: "TDP_ERR_CUDA", 5: "TDP_ERR_STATE", 6: "TDP_ERR_TIMEOUT"}
 
 # every entry point declared in include/tdp.h
 EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_get_net_delays",

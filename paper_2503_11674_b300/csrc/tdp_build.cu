@@ -49,9 +49,11 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(dalloc(g, &s.slack, t.n_pins));
     TDP_TRY(dalloc(g, &s.T, 1));
     TDP_TRY(dalloc(g, &s.wns_tns, 2));
-    TDP_TRY(dalloc(g, &s.red_part, 1024));
+    TDP_TRY(dalloc(g, &s.red_part, 2 * ((size_t)t.n_ep / kRedChunk + 1)));
     TDP_TRY(dalloc(g, &s.red_count, 1));
     TDP_CUDA(cudaMemset(s.red_count, 0, sizeof(unsigned)));
+    TDP_TRY(dalloc(g, &s.gsync, 2));
+    TDP_CUDA(cudaMemset(s.gsync, 0, 2 * sizeof(unsigned)));
     TDP_CUDA(cudaMemset(s.tnet, 0, sizeof(R) * t.n_pins));
     // static per-net path data of startpoints: no worst input, chain length 1
     std::vector<int32_t> pred(t.n_nets, -1), plen(t.n_nets, 1);
@@ -248,7 +250,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     }
     std::vector<int32_t> lv_out(n_comb), lv_onet(n_comb), lv_in_ptr(n_comb + 1, 0);
     std::vector<int32_t> lv_in_pin, lv_in_drv, lv_in_net;
-    std::vector<uint8_t> lv_in_comb;
+    std::vector<uint8_t> lv_in_flags;
     for (int k = 0; k < n_comb; ++k) {
         int c = lv_cell[k];
         lv_out[k] = out_pin[c];
@@ -259,7 +261,9 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             lv_in_pin.push_back(p);
             lv_in_drv.push_back(d->net_ptr[pin_net[p]]);
             lv_in_net.push_back(pin_net[p]);
-            lv_in_comb.push_back(d->cell_type[d->pin_cell[d->net_ptr[pin_net[p]]]] == TDP_CELL_COMB);
+            const int dc = d->pin_cell[d->net_ptr[pin_net[p]]];
+            lv_in_flags.push_back((d->cell_type[dc] == TDP_CELL_COMB ? kInComb : 0) |
+                                  (level[dc] == level[c] - 1 ? kInPrev : 0));
         }
         lv_in_ptr[k + 1] = (int32_t)lv_in_pin.size();
     }
@@ -357,6 +361,12 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     g->lv.bw_s_n = s_n;
     g->lv.bw_b_lo = b_lo;
     g->lv.bw_b_n = b_n;
+    {
+        std::vector<int4> bw_lv(D + 1);
+        for (int l = 0; l <= D; ++l) bw_lv[l] = make_int4(s_lo[l], s_n[l], b_lo[l], b_n[l]);
+        TDP_TRY(upload(g, &t.bw_lv, bw_lv));
+        TDP_TRY(upload(g, &t.lvl_ptr, lvl_ptr));
+    }
     std::vector<int32_t> pc(d->pin_cell, d->pin_cell + np), nptr(d->net_ptr, d->net_ptr + nn + 1);
     std::vector<uint8_t> fixed(d->cell_fixed, d->cell_fixed + nc);
     TDP_TRY(upload(g, &t.pin_cell, pc));
@@ -373,7 +383,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(upload(g, &t.lv_in_pin, lv_in_pin));
     TDP_TRY(upload(g, &t.lv_in_drv, lv_in_drv));
     TDP_TRY(upload(g, &t.lv_in_net, lv_in_net));
-    TDP_TRY(upload(g, &t.lv_in_comb, lv_in_comb));
+    TDP_TRY(upload(g, &t.lv_in_flags, lv_in_flags));
     TDP_TRY(upload(g, &t.ep, ep));
     TDP_TRY(upload(g, &t.cp_ptr, cp_ptr));
     TDP_TRY(upload(g, &t.cp, cp));
@@ -415,6 +425,24 @@ LaunchScope::~LaunchScope() {
     if (!b) return;
     cudaEventRecord(b, g->stream);
     g->prof_pending.emplace_back(a, b);
+}
+
+}  // namespace tdp
+
+namespace tdp {
+
+tdp_status check_sync_status(tdp_graph *g) {
+    unsigned *w = g->prec == TDP_FP32 ? g->s32.gsync : g->s64.gsync;
+    unsigned h = 0;
+    TDP_CUDA(cudaMemcpyAsync(&h, w + 1, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    TDP_CUDA(cudaStreamSynchronize(g->stream));
+    if (h == 0) return TDP_OK;
+    TDP_CUDA(cudaMemsetAsync(w + 1, 0, sizeof(unsigned), g->stream));
+    g->propagated = false;
+    g->extracted = false;
+    set_error("a level sweep's grid-wide wait gave up after %.1f s; timing results are not valid",
+              kSyncTimeoutNs * 1e-9);
+    return TDP_ERR_TIMEOUT;
 }
 
 }  // namespace tdp
@@ -519,6 +547,20 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
     }
     if (st == TDP_OK)
         st = precision == TDP_FP32 ? build_state<float>(g, netlist) : build_state<double>(g, netlist);
+    if (st == TDP_OK) {
+        // single-launch level sweeps need cooperative launches; the
+        // environment variable TDP_LEVEL_GRAPHS=1 selects the per-level graphs
+        int dev = 0, coop = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (e != cudaSuccess) {
+            set_error("sta_build: %s", cudaGetErrorString(e));
+            st = TDP_ERR_CUDA;
+        }
+        const char *env = getenv("TDP_LEVEL_GRAPHS");
+        g->single_launch = coop != 0 && !(env && env[0] == '1');
+    }
     if (st == TDP_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {

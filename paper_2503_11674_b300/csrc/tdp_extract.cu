@@ -168,7 +168,7 @@ __device__ bool cand_before(const Topo &t, const State<R> &s, const int *par, co
 constexpr int kTopkWarps = 4;
 
 template <typename R>
-__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int L,
+__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int G,
                                                           int keep_nonneg, int n_cap) {
     __shared__ int sh_par[kTopkWarps][kMaxK], sh_side[kTopkWarps][kMaxK];
     __shared__ int sh_len[kTopkWarps][kMaxK];
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
         int cpar = 0, cj = 0, ctail = 0;
         R ccost = R(0);
         if (lane == 0 && K > 1 && s.bcnt[e0] > 0) {
-            const R d = s.blist[(size_t)e0 * L].delta;
+            const R d = s.blist[(size_t)e0 * G].delta;
             if (keep_nonneg || se + d < R(0)) {
                 cv = true;
                 ctail = e0;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             if (__popc(tied) > 1) {  // equal slack: order by pin sequence
                 if (cv) {
                     ct_par[w][lane] = cpar;
-                    ct_side[w][lane] = s.blist[(size_t)ctail * L + cj].pin;
+                    ct_side[w][lane] = s.blist[(size_t)ctail * G + cj].pin;
                 }
                 __syncwarp();
                 int best = win;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             const int wj = __shfl_sync(FULL, cj, win);
             const int wtail = __shfl_sync(FULL, ctail, win);
             const R wcost = __shfl_sync(FULL, ccost, win);
-            const int sp = s.blist[(size_t)wtail * L + wj].pin;
+            const int sp = s.blist[(size_t)wtail * G + wj].pin;
             const int tn = t.pin_net[sp];
             const int len = sh_len[w][wpar] - s.plen[t.sink_onet[sp]] + 2 + s.plen[tn];
             if (lane == 0) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             if (lane == win) {  // replace the popped candidate by its next sibling
                 cv = false;
                 if (wj + 1 < min(s.bcnt[wtail], K - 1)) {  // lists may be longer than K - 1
-                    const R c2 = sh_cost[w][wpar] + s.blist[(size_t)wtail * L + wj + 1].delta;
+                    const R c2 = sh_cost[w][wpar] + s.blist[(size_t)wtail * G + wj + 1].delta;
                     if (keep_nonneg || se + c2 < R(0)) {
                         cv = true;
                         cj = wj + 1;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             bool add_child = false;
             R cc = R(0);
             if (n + 1 < K && s.bcnt[tn] > 0) {
-                cc = wcost + s.blist[(size_t)tn * L].delta;
+                cc = wcost + s.blist[(size_t)tn * G].delta;
                 add_child = keep_nonneg || se + cc < R(0);
             }
             const unsigned freem = __ballot_sync(FULL, !cv);
@@ -331,7 +331,7 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
         int n_cap = n_endpoints < 0 ? INT_MAX : n_endpoints;
         int blocks = std::min(div_up(t.n_ep, kTopkWarps), 148 * 16);
         LaunchScope ls(g, KID_TOPK);
-        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, std::max(g->lists_valid_L, 1), keep_nonneg,
+        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, list_group(g->lists_valid_L), keep_nonneg,
                                                       n_cap);
         TDP_LAUNCH_CHECK();
     }
@@ -482,7 +482,7 @@ extern "C" tdp_status extract_critical_paths(tdp_graph *g, int32_t n_endpoints, 
         long long h = 0;
         const long long *src = g->prec == TDP_FP32 ? g->s32.n_paths : g->s64.n_paths;
         TDP_CUDA(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
-        TDP_CUDA(cudaStreamSynchronize(g->stream));
+        TDP_TRY(check_sync_status(g));  // synchronises the stream
         *n_paths_out = h;
     }
     return TDP_OK;

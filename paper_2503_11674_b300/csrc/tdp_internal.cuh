@@ -39,10 +39,16 @@ constexpr int kMaxK = 32;          // paths per endpoint (one warp holds the fro
 constexpr int kMaxFanin = 32;      // inputs of a combinational cell
 constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole block
 constexpr int kPre = 4;            // inputs / sinks whose loads are issued together
+constexpr int kRedChunk = 1024;     // endpoints per partial of the WNS / TNS reduction
 constexpr double kQScale = 16777216.0;  // 2^24: fixed point of slack/WNS in the pair update
 constexpr double kQClamp = 32768.0;     // |slack/WNS| is clamped here before conversion
 
 enum PinKind : uint8_t { PK_COMB_IN = 0, PK_ENDPOINT = 1, PK_COMB_OUT = 2, PK_START = 3 };
+
+// flags of a combinational cell's input: its net is driven by a
+// combinational cell; that driver is one level below the cell (level 0:
+// flip-flops and primary inputs)
+constexpr uint8_t kInComb = 1, kInPrev = 2;
 
 // Kernels that can be timed with tdp_profile_kernel (names in tdp_build.cu).
 // The level sweeps are replayed from CUDA graphs: fwd_sweep is one replay of
@@ -159,6 +165,102 @@ __device__ __forceinline__ BEnt<double> ldg(const BEnt<double> *p) {
     return BEnt<double>{v.x, (int32_t)(__double_as_longlong(v.y) & 0xffffffffll)};
 }
 
+// Loads from L2, bypassing the (non-coherent) L1: for values another block of
+// the same launch wrote before a grid-wide barrier.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+__device__ __forceinline__ fx2 ldcg(const fx2 *p) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return fx2{v.x, v.y};
+}
+__device__ __forceinline__ BEnt<float> ldcg(const BEnt<float> *p) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return BEnt<float>{v.x, __float_as_int(v.y)};
+}
+__device__ __forceinline__ BEnt<double> ldcg(const BEnt<double> *p) {
+    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return BEnt<double>{v.x, (int32_t)(__double_as_longlong(v.y) & 0xffffffffll)};
+}
+
+// Load of a value written during the sweep: by an earlier launch (COH false,
+// read-only path) or by another block of this launch (COH true, L2).
+template <bool COH, typename T>
+__device__ __forceinline__ T ldd(const T *p) {
+    if constexpr (COH) return ldcg(p);
+    else return ldg(p);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident).  count
+// starts at zero for the launch and only grows; barrier n of the launch
+// waits until it reaches n * gridDim.x.  A wait gives up after timeout_ns
+// (or 2^26 polls), records status = 1 and every block leaves the kernel at
+// its next barrier; the host reads status and reports TDP_ERR_TIMEOUT.
+struct GridSync {
+    unsigned *count = nullptr;
+    unsigned *status = nullptr;
+    unsigned long long timeout_ns = 0;
+};
+constexpr unsigned long long kSyncTimeoutNs = 200000000ull;  // 0.2 s per wait
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false (in every thread of the block) when the wait gave up.
+__device__ __forceinline__ bool grid_sync(const GridSync &gs, unsigned target) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's writes before its arrival
+        atomicAdd(gs.count, 1u);
+        int good = 1;
+        unsigned long long t0 = 0;
+        for (unsigned it = 1; ld_acquire(gs.count) < target; ++it) {
+            if ((it & 255u) == 0u) {
+                if (ld_acquire(gs.status) != 0u || it >= (1u << 26)) {
+                    good = 0;
+                    break;
+                }
+                const unsigned long long now = global_ns();
+                if (t0 == 0ull) t0 = now;
+                else if (now - t0 > gs.timeout_ns) {
+                    atomicExch(gs.status, 1u);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        if (!good) atomicExch(gs.status, 1u);
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
+                               Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // One warp's piece of a net with more than kBwSmallFanout sinks in the
 // backward sweep: sinks [p0, p1) of the net driven by pin drv.  When the net
 // is split into nparts pieces, piece `part` writes its minimum to `slot` and
@@ -187,7 +289,7 @@ struct Topo {
     int32_t *lv_in_pin = nullptr;  // [n_in] input pins, ascending
     int32_t *lv_in_drv = nullptr;  // [n_in] driver pin of the input's net
     int32_t *lv_in_net = nullptr;  // [n_in] net of the input
-    uint8_t *lv_in_comb = nullptr; // [n_in] 1 if that net is driven by a combinational cell
+    uint8_t *lv_in_flags = nullptr; // [n_in] kInComb | kInPrev
     int32_t *ep = nullptr;         // [n_ep] endpoint pins, ascending
     int32_t *cp_ptr = nullptr;     // [n_cells+1] cell -> pins CSR
     int32_t *cp = nullptr;         // [n_pins]
@@ -198,6 +300,11 @@ struct Topo {
     int32_t *bw_sa = nullptr, *bw_sb = nullptr;
     BwTask *bw_task = nullptr;
     int32_t n_bw_tasks = 0, n_bw_slots = 0, n_bw_split = 0;
+    // device copies of the level structure for the single-launch sweeps:
+    // lvl_ptr [depth+1] as in Levels, bw_lv [depth+1] = (small-group first,
+    // count, piece first, count) of each level
+    int32_t *lvl_ptr = nullptr;
+    int4 *bw_lv = nullptr;
 };
 
 // Host copies of the launch structure of the level sweeps.
@@ -221,8 +328,9 @@ struct State {
     int32_t *pred_net = nullptr;  // [n_nets] net of that input
     int32_t *plen = nullptr;      // [n_nets] pins from the driver back to its startpoint
     double *T = nullptr;          // device clock period
+    unsigned *gsync = nullptr;    // [2] grid barrier counter, sticky timeout status
     double *wns_tns = nullptr;    // [2]
-    double *red_part = nullptr;   // reduction partials
+    double *red_part = nullptr;   // [2 * chunks] WNS / TNS partials per kRedChunk endpoints
     unsigned *red_count = nullptr;
     A *bw_part = nullptr;         // [n_bw_slots] partial minima of split nets
     unsigned long long *bw_cnt = nullptr;  // [n_bw_split] finished parts (monotone)
@@ -230,7 +338,7 @@ struct State {
     uint64_t *sort_a = nullptr, *sort_b = nullptr;  // (key, pin) items, ping-pong
     int32_t *nviol = nullptr;     // device count of failing endpoints
     int32_t *viol = nullptr;      // [n_ep] failing endpoints sorted by (slack, pin)
-    BEnt<R> *blist = nullptr;     // [n_nets * list_L] sidetrack lists
+    BEnt<R> *blist = nullptr;     // [n_nets * kMaxK] sidetrack lists, list_group(list_L) apart
     int32_t *bcnt = nullptr;      // [n_nets] entries in each sidetrack list
     int32_t *p_parent = nullptr, *p_side = nullptr, *p_len = nullptr;  // [n_ep * K]
     R *p_cost = nullptr;
@@ -263,6 +371,11 @@ struct tdp_graph {
     // sidetrack lists are built by the forward sweep: list_L entries per node
     // (the K - 1 of the last extraction), lists_valid_L of them are current
     int list_L = 0, lists_valid_L = 0;
+    // level sweeps: one cooperative launch each (single_launch), else CUDA
+    // graphs of one kernel per level
+    bool single_launch = true;
+    int n_sm = 0;
+    std::vector<std::pair<const void *, int>> coop_grid;  // kernel -> resident grid
     cudaGraphExec_t fwd_graph = nullptr, bwd_graph = nullptr;  // captured level sweeps
     int fwd_graph_L = -1, fwd_graph_kernels = 0, bwd_graph_kernels = 0;
     std::vector<void *> allocs;  // every device allocation, freed in sta_destroy
@@ -314,11 +427,21 @@ template <typename R>
 tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, const double *gs,
                          R *gx, R *gy);
 
+// reads and clears the sticky status of the grid barriers (synchronises the
+// stream); TDP_ERR_TIMEOUT if a wait gave up since the last check
+tdp_status check_sync_status(tdp_graph *g);
+
 // exclusive scan of n int32 counts into int64 offsets (out has n+1 entries)
 tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_t n,
                            cudaStream_t st);
 
 inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// Lanes per cell in the forward sweep for sidetrack lists of L entries,
+// which is also the stride (in entries) between two nets' lists.
+__host__ __device__ constexpr int list_group(int L) { return L == 0 ? 4 : L + 1; }
+
+__device__ __forceinline__ int div_up_dev(int a, int b) { return (a + b - 1) / b; }
 
 // Sidetrack list lengths the forward sweep builds (one kernel each): the
 // smallest that holds `need` entries.

@@ -4,19 +4,24 @@
 //   k_net_rc     one pass over the nets: pin positions, Elmore delay of every
 //                sink, net load and driving-cell delay (thread per net up to 32
 //                sinks, block per net above, FP64 load sum there)
-//   k_fwd_level  arrival times of the combinational cells of one level (thread
-//                per cell; max / argmax over its inputs), and, when asked, the
-//                cell's sidetrack list for report_timing_endpoint
-//   k_bwd_level  required times of the nets driven from one level (lane per
+//   k_fwd_sweep  the forward sweep in one cooperative launch: arrival times
+//                level by level (thread per combinational cell: max / argmax
+//                over its inputs), and, when asked, each cell's sidetrack list
+//                for report_timing_endpoint; grid-wide barrier between levels
+//   k_bwd_sweep  the backward sweep in one cooperative launch: required times
+//                of the nets driven from each level, deepest first (lane per
 //                net of at most 8 sinks, warp per 128 sinks of larger nets,
-//                split nets combined by the last warp to finish)
-//   k_wns_tns    FP64 WNS / TNS over the endpoints (fixed-order reduction)
+//                split nets combined by the last warp to finish), then WNS /
+//                TNS over the endpoints (FP64, fixed-order reduction)
 //
-// The per-level launches are captured once into a CUDA graph and replayed.
-// Every array a level kernel reads was written by an earlier launch (a lower
-// level going forward, a higher level going backward), so the reads use the
-// read-only path and all loads of a group of inputs / sinks are issued before
-// the first store.
+// Where a cooperative launch cannot be made resident (or TDP_LEVEL_GRAPHS=1),
+// the same per-cell and per-task code runs as one launch per level
+// (k_fwd_level, k_bwd_level, k_wns_tns) captured in CUDA graphs; there every
+// array a level reads was written by an earlier launch, so the reads use the
+// read-only path.  Inside one cooperative launch, values written before a
+// barrier are read from L2.  Either way all loads of a group of inputs /
+// sinks are issued before the first store.
+#include <algorithm>
 #include <type_traits>
 
 #include "tdp_internal.cuh"
@@ -127,9 +132,22 @@ struct LEnt {
 constexpr uint32_t kPinMask = (1u << 29) - 1u;
 constexpr uint32_t kNoneKey = 0xffffffffu;
 
+// Entries compare by cost, then key: a strict total order (costs as
+// order-preserving integer bits), so the merge below ranks every entry of a
+// list uniquely.
+__device__ __forceinline__ uint32_t ord_bits(float d) {
+    const uint32_t u = __float_as_uint(d);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ uint64_t ord_bits(double d) {
+    const uint64_t u = (uint64_t)__double_as_longlong(d);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
 template <typename R>
 __device__ __forceinline__ bool lent_before(const LEnt<R> &a, const LEnt<R> &b) {
-    return a.d < b.d || (a.d == b.d && a.key < b.key);
+    const auto ua = ord_bits(a.d), ub = ord_bits(b.d);
+    return ua < ub || (ua == ub && a.key < b.key);
 }
 
 template <typename R>
@@ -145,119 +163,325 @@ __device__ __forceinline__ R r_inf() {
 // are ordered as the resulting paths' pin sequences (read from the endpoint)
 // would be: own deviations through a pin below the worst input, then the
 // inherited entries, then own deviations through a pin above it.  Lists hold
-// exactly L entries; unused ones are +inf sentinels (pin -1).
-template <typename R, int L, int NIN>
-__device__ __forceinline__ void build_list(State<R> &s, int e, int bi, int bn, bool bn_comb,
-                                           typename Acc<R>::T best, const int *ip,
-                                           const typename Acc<R>::T *ain, int nin) {
-    using AC = Acc<R>;
-    LEnt<R> li[L];
-    if (bn_comb) {  // the inherited list (written by an earlier level's launch)
-        const BEnt<R> *src = s.blist + (size_t)bn * L;
-#pragma unroll
-        for (int j = 0; j < L; ++j) {
-            const BEnt<R> v = ldg(&src[j]);
-            li[j] = LEnt<R>{v.delta, v.pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)v.pin)};
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < L; ++j) li[j] = LEnt<R>{r_inf<R>(), kNoneKey};
-    }
-#pragma unroll
-    for (int u = 0; u < NIN; ++u) {
-        if (u >= nin || ip[u] == bi) continue;
-        const LEnt<R> x{AC::diff(best, ain[u]), ((ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)ip[u]};
-        // insert x, keeping the first L entries (compare-and-shift from the top)
-#pragma unroll
-        for (int j = L - 1; j >= 0; --j) {
-            const bool shift = j > 0 && lent_before(x, li[j - 1]);
-            const bool here = lent_before(x, li[j]);
-            li[j] = shift ? li[j - 1] : (here ? x : li[j]);
-        }
-    }
-    BEnt<R> *out = s.blist + (size_t)e * L;
-    int m = 0;
-#pragma unroll
-    for (int j = 0; j < L; ++j) {
-        const bool none = li[j].key == kNoneKey;
-        out[j] = BEnt<R>{li[j].d, none ? -1 : (int32_t)(li[j].key & kPinMask)};
-        m += none ? 0 : 1;
-    }
-    s.bcnt[e] = m;
+// exactly L entries; unused ones are +inf sentinels (pin -1).  A net's list
+// starts at entry net * G, G = list_group(L) (one aligned block of G entries).
+
+__device__ __forceinline__ LEnt<float> lent_of(const BEnt<float> &v) {
+    return LEnt<float>{v.delta, v.pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)v.pin)};
+}
+__device__ __forceinline__ LEnt<double> lent_of(const BEnt<double> &v) {
+    return LEnt<double>{v.delta, v.pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)v.pin)};
+}
+template <typename R>
+__device__ __forceinline__ BEnt<R> bent_of(const LEnt<R> &x) {
+    return BEnt<R>{x.d, x.key == kNoneKey ? -1 : (int32_t)(x.key & kPinMask)};
 }
 
-// Arrival of one combinational cell (k in level order) whose inputs are
-// [a, b) with b - a <= NIN; builds its sidetrack list when L > 0.
-template <typename R, int L, int NIN>
-__device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, int k, int a, int b) {
+// ---- one cell per thread (cells with more inputs than a group has lanes)
+
+// A cell with more inputs than a group has lanes (rare): one thread visits
+// its inputs kPre at a time (arrival / argmax), then builds the list in
+// place in its output block, inserting the own deviations one by one.
+// While it is built, an entry's pin field holds its ordering key.
+template <typename R, int L, bool COH>
+__device__ __noinline__ void fwd_cell_wide(const Topo &t, State<R> &s, int k, int a, int b) {
     using AC = Acc<R>;
     using A = typename AC::T;
+    constexpr int G = list_group(L);
     const int e = ldg(&t.lv_onet[k]), o = ldg(&t.lv_out[k]);
-    int ip[NIN], in[NIN], dv[NIN], pl[NIN];
-    uint8_t cb[NIN];
-    A av[NIN];
-    R tv[NIN];
-    // every load of the cell's inputs first, then the arithmetic, then stores
-#pragma unroll
-    for (int u = 0; u < NIN; ++u) {
-        if (a + u < b) {
-            ip[u] = ldg(&t.lv_in_pin[a + u]);
-            in[u] = ldg(&t.lv_in_net[a + u]);
-            dv[u] = ldg(&t.lv_in_drv[a + u]);
-            cb[u] = ldg(&t.lv_in_comb[a + u]);
-        }
-    }
-    pdl_wait();  // everything below reads values earlier kernels wrote
-    const R dcell = ldg(&s.dnet[e]);
-#pragma unroll
-    for (int u = 0; u < NIN; ++u) {
-        if (a + u < b) {
-            av[u] = ldg(&s.arr[dv[u]]);
-            tv[u] = ldg(&s.tnet[ip[u]]);
-            pl[u] = ldg(&s.plen[in[u]]);
-        }
-    }
-    // inputs ascending by pin: strict > keeps the lowest pin on ties (and the
-    // first input if arrivals are not comparable)
-    int bi = -1, bn = -1, bl = 0;
-    bool bc = false;
+    int bi = -1, bp = a;
     A best = AC::ninf();
+    for (int p0 = a; p0 < b; p0 += kPre) {
+        int ip[kPre], dv[kPre];
+        A av[kPre];
+        R tv[kPre];
 #pragma unroll
-    for (int u = 0; u < NIN; ++u) {
-        if (a + u < b) {
-            av[u] = AC::add(av[u], tv[u]);
-            if (bi < 0 || AC::gt(av[u], best)) {
-                best = av[u];
-                bi = ip[u];
-                bn = in[u];
-                bl = pl[u];
-                bc = cb[u];
+        for (int u = 0; u < kPre; ++u) {
+            if (p0 + u < b) {
+                ip[u] = ldg(&t.lv_in_pin[p0 + u]);
+                dv[u] = ldg(&t.lv_in_drv[p0 + u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (p0 + u < b) {
+                av[u] = ldd<COH>(&s.arr[dv[u]]);
+                tv[u] = ldg(&s.tnet[ip[u]]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (p0 + u < b) {
+                av[u] = AC::add(av[u], tv[u]);
+                s.arr[ip[u]] = av[u];
+                // largest arrival, lowest pin on ties (the group order below)
+                if (bi < 0 || AC::gt(av[u], best) || (!AC::gt(best, av[u]) && ip[u] < bi)) {
+                    best = av[u];
+                    bi = ip[u];
+                    bp = p0 + u;
+                }
             }
         }
     }
-#pragma unroll
-    for (int u = 0; u < NIN; ++u)
-        if (a + u < b) s.arr[ip[u]] = av[u];
-    s.arr[o] = AC::add(best, dcell);
+    const int bn = ldg(&t.lv_in_net[bp]);
+    const bool bc = (ldg(&t.lv_in_flags[bp]) & kInComb) != 0;
+    s.arr[o] = AC::add(best, ldg(&s.dnet[e]));
     s.pred_in[e] = bi;
     s.pred_net[e] = bn;
-    s.plen[e] = bl + 2;
-    if constexpr (L > 0) build_list<R, L, NIN>(s, e, bi, bn, bc, best, ip, av, b - a);
+    s.plen[e] = ldd<COH>(&s.plen[bn]) + 2;
+    if constexpr (L > 0) {
+        BEnt<R> *out = s.blist + (size_t)e * G;
+        const BEnt<R> *src = s.blist + (size_t)bn * G;
+        for (int j = 0; j < L; ++j) {
+            const LEnt<R> x = bc ? lent_of(ldd<COH>(&src[j])) : LEnt<R>{r_inf<R>(), kNoneKey};
+            out[j] = BEnt<R>{x.d, (int32_t)x.key};
+        }
+        for (int p = a; p < b; ++p) {
+            const int ip = ldg(&t.lv_in_pin[p]);
+            if (ip == bi) continue;
+            const A av = ldcg(&s.arr[ip]);  // stored above by this thread
+            const LEnt<R> x{AC::diff(best, av), ((ip < bi ? 0u : 2u) << 29) | (uint32_t)ip};
+            int j = 0;
+            for (; j < L; ++j) {
+                const BEnt<R> y = ldcg(&out[j]);
+                if (lent_before(x, LEnt<R>{y.delta, (uint32_t)y.pin})) break;
+            }
+            if (j == L) continue;
+            for (int q = L - 1; q > j; --q) out[q] = ldcg(&out[q - 1]);
+            out[j] = BEnt<R>{x.d, (int32_t)x.key};
+        }
+        int m = 0;
+        for (int j = 0; j < L; ++j) {
+            BEnt<R> y = ldcg(&out[j]);
+            const uint32_t key = (uint32_t)y.pin;
+            y.pin = key == kNoneKey ? -1 : (int32_t)(key & kPinMask);
+            m += key == kNoneKey ? 0 : 1;
+            out[j] = y;
+        }
+        s.bcnt[e] = m;
+    }
 }
 
+// ---- one cell per group of G lanes (the common case)
+
+template <typename T>
+__device__ __forceinline__ T shfl_idx(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ fx2 shfl_idx(fx2 v, int src) {
+    return fx2{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ fx2 shfl_x(fx2 v, int o) {
+    return fx2{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// What one lane of a group knows about its group's cell k (k < 0: none) and
+// about the input with index gl (the lane's index in the group), if any:
+// its pin, net, driver pin and flags, and, once loaded, its Elmore delay
+// (has_tv) and its driver's arrival and chain length (has_old).
+template <typename R>
+struct LaneTopo {
+    using A = typename Acc<R>::T;
+    int k, a, b, e, o;
+    int ip, in, dv, fl;
+    bool has_tv, has_old;
+    R tv;
+    A ad;
+    int pl;
+};
+
+// Topology of cell k for lane gl.  With old_vals (single launch, before the
+// barrier that opens the cell's level), also the values that are already
+// final: the input's Elmore delay, and its driver's arrival and chain length
+// unless the driver is on the level just below (still being computed).
+template <typename R, int G>
+__device__ __forceinline__ void lane_topo(const Topo &t, const State<R> &s, int k, int gl,
+                                          LaneTopo<R> &c, bool old_vals) {
+    c.k = k;
+    c.a = c.b = 0;
+    c.has_tv = c.has_old = false;
+    if (k < 0) return;
+    c.a = ldg(&t.lv_in_ptr[k]);
+    c.b = ldg(&t.lv_in_ptr[k + 1]);
+    c.e = ldg(&t.lv_onet[k]);
+    c.o = ldg(&t.lv_out[k]);
+    if (c.b - c.a <= G && gl < c.b - c.a) {
+        c.ip = ldg(&t.lv_in_pin[c.a + gl]);
+        c.in = ldg(&t.lv_in_net[c.a + gl]);
+        c.dv = ldg(&t.lv_in_drv[c.a + gl]);
+        c.fl = ldg(&t.lv_in_flags[c.a + gl]);
+        if (old_vals) {
+            c.tv = ldg(&s.tnet[c.ip]);
+            c.has_tv = true;
+            if (!(c.fl & kInPrev)) {
+                c.ad = ldcg(&s.arr[c.dv]);
+                c.pl = ldcg(&s.plen[c.in]);
+                c.has_old = true;
+            }
+        }
+    }
+}
+
+// Arrival of the group's cell (Section II-B: max over its inputs of the
+// driver's arrival plus the Elmore delay, plus the cell delay) and, when
+// L > 0, its sidetrack list: lane j holds input j and entry j of the
+// inherited list; the own deviations are merged in by rank (an entry's rank
+// is the number of entries of both lists before it), and the first L of the
+// merged list are written, one aligned block per list.  Every lane of the
+// warp calls this (shuffles and ballots span the warp); COH: the drivers'
+// values were written by other blocks of the same launch.  Warps whose cells
+// all have at most kPre inputs take an unrolled path.
+template <typename R, int L, bool COH>
+__device__ __forceinline__ void fwd_group(const Topo &t, State<R> &s, const LaneTopo<R> &c, int lane) {
+    constexpr int G = list_group(L);
+    constexpr unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    const unsigned FULL = 0xffffffffu;
+    const int gl = lane & (G - 1), gbase = lane & ~(G - 1);
+    const int nin = c.k >= 0 ? c.b - c.a : 0;
+    const bool wide = nin > G;
+    const bool act = c.k >= 0 && !wide;
+    const bool mine = act && gl < nin;
+    const bool narrow = __all_sync(FULL, nin <= kPre);
+    A av = AC::ninf();
+    int pl = 0;
+    R dcell = R(0);
+    if (mine) {
+        const R tv = c.has_tv ? c.tv : ldg(&s.tnet[c.ip]);
+        A ad;
+        if (c.has_old) {
+            ad = c.ad;
+            pl = c.pl;
+        } else {
+            ad = ldd<COH>(&s.arr[c.dv]);
+            pl = ldd<COH>(&s.plen[c.in]);
+        }
+        av = AC::add(ad, tv);
+    }
+    if (act && gl == 0) dcell = ldg(&s.dnet[c.e]);
+    // worst input: largest arrival, lowest pin on ties
+    A best = av;
+    int bi = mine ? c.ip : -1;
+    bool bv = mine;
+    int wl = 0;  // lane (in the group) of the worst input
+    int bn = -1, bl = 0, bc = 0;
+    if (narrow) {
+#pragma unroll
+        for (int o = 1; o < kPre; o <<= 1) {
+            const A oa = shfl_x(best, o);
+            const int oi = shfl_x(bi, o);
+            const bool ov = shfl_x((int)bv, o) != 0;
+            if (ov && (!bv || AC::gt(oa, best) || (!AC::gt(best, oa) && oi < bi))) {
+                best = oa;
+                bi = oi;
+                bv = true;
+            }
+        }
+        best = shfl_idx(best, gbase);
+        bi = shfl_idx(bi, gbase);
+        bv = shfl_idx((int)bv, gbase) != 0;
+        const unsigned wm = (__ballot_sync(FULL, mine && c.ip == bi) >> gbase) & gmask;
+        wl = wm ? __ffs(wm) - 1 : 0;
+        bn = shfl_idx(c.in, gbase + wl);
+        bl = shfl_idx(pl, gbase + wl);
+        bc = shfl_idx(c.fl, gbase + wl) & kInComb;
+    } else {
+        bn = mine ? c.in : -1;
+        bl = pl;
+        bc = mine ? (c.fl & kInComb) : 0;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const A oa = shfl_x(best, o);
+            const int oi = shfl_x(bi, o), on = shfl_x(bn, o), ol = shfl_x(bl, o), oc = shfl_x(bc, o);
+            const bool ov = shfl_x((int)bv, o) != 0;
+            if (ov && (!bv || AC::gt(oa, best) || (!AC::gt(best, oa) && oi < bi))) {
+                best = oa;
+                bi = oi;
+                bn = on;
+                bl = ol;
+                bc = oc;
+                bv = true;
+            }
+        }
+    }
+    if (!bv) {
+        bi = bn = -1;
+        bl = bc = 0;
+    }
+    if (mine) s.arr[c.ip] = av;
+    if (act && gl == 0) {
+        s.arr[c.o] = AC::add(best, dcell);
+        s.pred_in[c.e] = bi;
+        s.pred_net[c.e] = bn;
+        s.plen[c.e] = bl + 2;
+    }
+    if constexpr (L > 0) {
+        LEnt<R> inh{r_inf<R>(), kNoneKey};
+        if (act && gl < L && bc) inh = lent_of(ldd<COH>(&s.blist[(size_t)bn * G + gl]));
+        const bool has_own = mine && c.ip != bi;
+        const LEnt<R> own{AC::diff(best, av), ((c.ip < bi ? 0u : 2u) << 29) | (uint32_t)c.ip};
+        int inh_rank = gl, own_rank = 0;
+        if (narrow) {  // the group's inputs are its lanes 0..nin-1
+            unsigned mb = 0u;
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                const LEnt<R> x{shfl_idx(own.d, gbase + u), shfl_idx(own.key, gbase + u)};
+                const bool xv = bv && u < nin && u != wl;
+                if (xv && gl < L && lent_before(x, inh)) ++inh_rank;
+                if (xv && has_own && u != gl && lent_before(x, own)) ++own_rank;
+                const unsigned bb = __ballot_sync(FULL, xv && gl < L && lent_before(inh, x));
+                if (gl == u) mb = bb;
+            }
+            own_rank += __popc((mb >> gbase) & gmask);
+        } else {
+            bool done = !has_own;
+            for (;;) {  // broadcast the group's own deviations one at a time
+                const unsigned rem = __ballot_sync(FULL, !done);
+                if (rem == 0u) break;
+                const unsigned gm = (rem >> gbase) & gmask;
+                const bool live = gm != 0u;
+                const int src = live ? __ffs(gm) - 1 : 0;
+                const LEnt<R> x{shfl_idx(own.d, gbase + src), shfl_idx(own.key, gbase + src)};
+                if (live && gl < L && lent_before(x, inh)) ++inh_rank;
+                if (live && has_own && gl != src && lent_before(x, own)) ++own_rank;
+                const unsigned bb = __ballot_sync(FULL, live && gl < L && lent_before(inh, x));
+                if (live && gl == src) {
+                    own_rank += __popc((bb >> gbase) & gmask);
+                    done = true;
+                }
+            }
+        }
+        BEnt<R> *out = s.blist + (size_t)(act ? c.e : 0) * G;
+        if (act && gl < L && inh_rank < L) out[inh_rank] = bent_of(inh);
+        if (has_own && own_rank < L) out[own_rank] = BEnt<R>{own.d, c.ip};
+        const unsigned vi = __ballot_sync(FULL, act && gl < L && inh.key != kNoneKey);
+        const unsigned vo = __ballot_sync(FULL, has_own);
+        if (act && gl == 0)
+            s.bcnt[c.e] = min(L, __popc((vi >> gbase) & gmask) + __popc((vo >> gbase) & gmask));
+    }
+    if (wide && gl == 0) fwd_cell_wide<R, L, COH>(t, s, c.k, c.a, c.b);
+}
+
+// One launch per level (captured in a CUDA graph): a group of lanes per cell.
 template <typename R, int L>
 __global__ void __launch_bounds__(kLvThreads) k_fwd_level(Topo t, State<R> s, int lo, int hi) {
+    constexpr int G = list_group(L), CPW = 32 / G;
     pdl_trigger();
-    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= hi) return;
-    const int a = ldg(&t.lv_in_ptr[k]), b = ldg(&t.lv_in_ptr[k + 1]);
-    if (b - a <= kPre) fwd_cell<R, L, kPre>(t, s, k, a, b);
-    else fwd_cell<R, L, kMaxFanin>(t, s, k, a, b);
+    const int lane = threadIdx.x & 31;
+    const int chunk = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (lo + chunk * CPW >= hi) return;  // whole warps only
+    const int k = lo + chunk * CPW + lane / G;
+    LaneTopo<R> c;
+    lane_topo<R, G>(t, s, k < hi ? k : -1, lane & (G - 1), c, false);
+    pdl_wait();  // the timing loads read what earlier launches wrote
+    fwd_group<R, L, false>(t, s, c, lane);
 }
 
 template <typename R>
 static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, cudaStream_t cs) {
-    const int grid = div_up(hi - lo, kLvThreads);
+    const int CPW = 32 / list_group(L);
+    const int grid = div_up((int64_t)div_up(hi - lo, CPW) * 32, kLvThreads);
     switch (L) {
         case 0: launch_pdl(k_fwd_level<R, 0>, grid, kLvThreads, cs, t, s, lo, hi); break;
         case 3: launch_pdl(k_fwd_level<R, 3>, grid, kLvThreads, cs, t, s, lo, hi); break;
@@ -267,13 +491,55 @@ static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, 
     }
 }
 
+// Single-launch sweeps: one block of kPsThreads per SM (64 registers a
+// thread), as many warps in flight as registers allow, since a level is a few
+// latency-bound steps per warp; one block per SM keeps the barrier short.
+constexpr int kPsThreads = 1024;
+constexpr int kFwdBlocksPerSM = 1;
+constexpr int kBwdBlocksPerSM = 1;
+
+// The whole forward sweep in one cooperative launch: levels in order, a
+// level's cells in chunks of 32 / G (one per warp), chunk j on block
+// j mod gridDim (spreading a level over every SM), a grid-wide barrier
+// between levels.  Before each barrier a warp loads its first chunk of the
+// next level: topology, Elmore delays and the values of drivers two or more
+// levels down, so only the values the level below wrote are left after it.
+template <typename R, int L>
+__global__ void __launch_bounds__(kPsThreads, kFwdBlocksPerSM) k_fwd_sweep(Topo t, State<R> s, GridSync gs) {
+    constexpr int G = list_group(L), CPW = 32 / G;
+    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane & (G - 1);
+    const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // first chunk of this warp
+    const int wstride = (blockDim.x >> 5) * gridDim.x;
+    auto topo_of = [&](int l, int chunk, LaneTopo<R> &c, bool old_vals) {
+        const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * CPW + grp;
+        lane_topo<R, G>(t, s, k < ldg(&t.lvl_ptr[l]) ? k : -1, gl, c, old_vals);
+    };
+    LaneTopo<R> pre;
+    if (t.depth > 0) topo_of(1, w0, pre, false);
+    for (int l = 1; l <= t.depth; ++l) {
+        const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), CPW);
+        if (w0 < nch) {
+            fwd_group<R, L, true>(t, s, pre, lane);
+            for (int ch = w0 + wstride; ch < nch; ch += wstride) {
+                LaneTopo<R> c;
+                topo_of(l, ch, c, false);
+                fwd_group<R, L, true>(t, s, c, lane);
+            }
+        }
+        if (l == t.depth) break;
+        topo_of(l + 1, w0, pre, true);
+        if (!grid_sync(gs, (unsigned)l * gridDim.x)) return;
+    }
+}
+
 // ----------------------------------------------------------- backward ---
 
 // req / slack of the sinks first, first+step, ... < b of the net driven by
 // pin a, NP sinks per round of loads; returns min over them of req(s) - t(s)
 // and the driver's arrival in ad.  The first round's topology loads are
-// issued before pdl_wait().
-template <typename R, int NP>
+// issued before pdl_wait() (level launches); COH: required times of sink
+// cells were written by other blocks of the same launch.
+template <typename R, int NP, bool COH>
 __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State<R> &s, int first,
                                                             int b, int step, int a,
                                                             typename Acc<R>::T &ad) {
@@ -294,7 +560,7 @@ __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State
         }
     };
     topo_loads(first);
-    pdl_wait();  // everything below reads values earlier kernels wrote
+    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
     ad = ldg(&s.arr[a]);
     const A Tacc = acc_from_double<R>(*s.T);
     for (int p0 = first; p0 < b; p0 += NP * step) {
@@ -314,7 +580,7 @@ __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State
                     ap[u] = AC::add(ad, tp[u]);
                     rq[u] = Tacc;
                 } else {
-                    rq[u] = AC::add(ldg(&s.req[so[u]]), -ldg(&s.dnet[sn[u]]));
+                    rq[u] = AC::add(ldd<COH>(&s.req[so[u]]), -ldg(&s.dnet[sn[u]]));
                     ap[u] = ldg(&s.arr[p]);
                 }
             }
@@ -334,53 +600,73 @@ __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State
     return m;
 }
 
-template <typename A>
-__device__ __forceinline__ A shfl_xor_acc(A v, int o) {
-    if constexpr (std::is_same<A, double>::value) {
-        return __shfl_xor_sync(0xffffffffu, v, o);
-    } else {
-        A r;
-        r.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-        r.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-        return r;
-    }
-}
-
-// L2 loads of values another block of the same launch has just written.
-__device__ __forceinline__ double ldcg_acc(const double *p) { return __ldcg(p); }
-__device__ __forceinline__ fx2 ldcg_acc(const fx2 *p) {
-    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
-    return fx2{v.x, v.y};
-}
-
-// One warp per task of this level: warps [0, ns) take groups s_lo.. of 32
-// small nets (a lane per net, all its sinks in one round of loads), warps
-// [ns, ns + nb) take pieces b_lo.. of larger nets (lanes stride the sinks).
-template <typename R>
-__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int s_lo, int ns,
-                                                          int b_lo, int nb) {
+// A net of at most kBwSmallFanout sinks in slot i of the small-net table,
+// on a group of kBwSmallFanout lanes (a sink per lane; slots of -1 pad a
+// level's table).  Every lane of the warp calls this.
+template <typename R, bool COH>
+__device__ __forceinline__ void bwd_small(const Topo &t, State<R> &s, int i, int lane) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    pdl_trigger();
-    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w < ns) {
-        const int i = (s_lo + w) * 32 + lane;
-        const int a = ldg(&t.bw_sa[i]), b = ldg(&t.bw_sb[i]);
-        if (a < 0) return;
-        A ad;
-        const A m = net_sinks_req<R, kBwSmallFanout>(t, s, a + 1, b, 1, a, ad);
+    const int gl = lane & (kBwSmallFanout - 1);
+    const int a = ldg(&t.bw_sa[i]), b = ldg(&t.bw_sb[i]);
+    const int p = a + 1 + gl;
+    const bool mine = a >= 0 && p < b;
+    int kd = 0, so = 0, sn = 0;
+    if (mine) {
+        kd = ldg(&t.pin_kind[p]);
+        so = ldg(&t.sink_out[p]);
+        sn = ldg(&t.sink_onet[p]);
+    }
+    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
+    A m = AC::pinf(), ad = AC::pinf();
+    if (a >= 0) ad = ldg(&s.arr[a]);
+    if (mine) {
+        const R tp = ldg(&s.tnet[p]);
+        A rq, ap;
+        if (kd == PK_ENDPOINT) {
+            ap = AC::add(ad, tp);
+            rq = acc_from_double<R>(*s.T);
+            s.arr[p] = ap;
+        } else {
+            rq = AC::add(ldd<COH>(&s.req[so]), -ldg(&s.dnet[sn]));
+            ap = ldg(&s.arr[p]);
+        }
+        s.req[p] = rq;
+        s.slack[p] = AC::diff(rq, ap);
+        m = AC::add(rq, -tp);
+    }
+#pragma unroll
+    for (int o = kBwSmallFanout / 2; o > 0; o >>= 1) {  // min is exact: any order gives the same value
+        const A other = shfl_x(m, o);
+        if (AC::lt(other, m)) m = other;
+    }
+    if (a >= 0 && gl == 0) {
         s.req[a] = m;
         s.slack[a] = AC::diff(m, ad);
+    }
+}
+
+constexpr int kBwNetsPerWarp = 32 / kBwSmallFanout;
+
+// One warp-wide task w of a backward level: w < 8 ns is a chunk of
+// kBwNetsPerWarp small nets of the level's ns groups of 32 (from group s_lo);
+// after that, piece b_lo + (w - 8 ns) of a larger net (lanes stride its sinks).
+template <typename R, bool COH>
+__device__ __forceinline__ void bwd_task(const Topo &t, State<R> &s, int w, int s_lo, int ns, int b_lo,
+                                         int lane) {
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    const int n_small = ns * (32 / kBwNetsPerWarp);
+    if (w < n_small) {
+        bwd_small<R, COH>(t, s, s_lo * 32 + w * kBwNetsPerWarp + lane / kBwSmallFanout, lane);
         return;
     }
-    if (w >= ns + nb) return;
-    const BwTask task = t.bw_task[b_lo + (w - ns)];
+    const BwTask task = t.bw_task[b_lo + (w - n_small)];
     const int a = task.drv;
     A ad;
-    A m = net_sinks_req<R, kPre>(t, s, task.p0 + lane, task.p1, 32, a, ad);
-    for (int o = 16; o > 0; o >>= 1) {  // min is exact: any order gives the same value
-        const A other = shfl_xor_acc(m, o);
+    A m = net_sinks_req<R, kPre, COH>(t, s, task.p0 + lane, task.p1, 32, a, ad);
+    for (int o = 16; o > 0; o >>= 1) {
+        const A other = shfl_x(m, o);
         if (AC::lt(other, m)) m = other;
     }
     if (lane != 0) return;
@@ -393,9 +679,9 @@ __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, in
         if (done % (unsigned long long)task.nparts != 0ull) return;
         __threadfence();
         const int base = task.slot - task.part;
-        m = ldcg_acc(&s.bw_part[base]);
+        m = ldcg(&s.bw_part[base]);
         for (int j = 1; j < task.nparts; ++j) {
-            const A v = ldcg_acc(&s.bw_part[base + j]);
+            const A v = ldcg(&s.bw_part[base + j]);
             if (AC::lt(v, m)) m = v;
         }
     }
@@ -403,63 +689,98 @@ __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, in
     s.slack[a] = AC::diff(m, ad);
 }
 
+// warp tasks of a backward level
+__host__ __device__ __forceinline__ int bwd_tasks(int ns, int nb) {
+    return ns * (32 / kBwNetsPerWarp) + nb;
+}
+
+// One launch per level (captured in a CUDA graph): a warp per task.
+template <typename R>
+__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int s_lo, int ns,
+                                                          int b_lo, int nb) {
+    pdl_trigger();
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (w >= bwd_tasks(ns, nb)) return;
+    bwd_task<R, false>(t, s, w, s_lo, ns, b_lo, threadIdx.x & 31);
+}
+
 // ---------------------------------------------------------- WNS / TNS ---
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 148;
+constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
 
-// WNS = min over endpoints with negative slack, TNS = their sum (FP64).
-// Each block reduces a fixed stride of endpoints; the last block to finish
-// combines the per-block partials in block order, so the result does not
-// depend on scheduling.
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
-    __shared__ double smin[kRedThreads / 32], ssum[kRedThreads / 32];
+// WNS = min over endpoints with negative slack, TNS = their sum (FP64;
+// Eqs. (3)-(4)).  The endpoints are cut into chunks of kRedChunk, a warp
+// reduces one chunk in a fixed order, and the last block to finish adds the
+// chunk partials in chunk order: the result does not depend on the grid, the
+// block size or scheduling.
+template <typename R, bool COH>
+__device__ __forceinline__ void wns_tns_blocks(const Topo &t, State<R> &s) {
     __shared__ bool last;
-    pdl_wait();
-    double mn = 0.0, sm = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < t.n_ep; i += gridDim.x * blockDim.x) {
-        double v = (double)s.slack[t.ep[i]];
-        if (v < 0.0) {
-            mn = fmin(mn, v);
-            sm += v;
+    const int lane = threadIdx.x & 31;
+    const int n_chunks = div_up_dev(t.n_ep, kRedChunk);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < n_chunks; ch += nw) {
+        double mn = 0.0, sm = 0.0;
+        const int end = min((ch + 1) * kRedChunk, t.n_ep);
+        for (int i = ch * kRedChunk + lane; i < end; i += 32) {
+            const double v = (double)ldd<COH>(&s.slack[ldg(&t.ep[i])]);
+            if (v < 0.0) {
+                mn = fmin(mn, v);
+                sm += v;
+            }
         }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        smin[w] = mn;
-        ssum[w] = sm;
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        }
+        if (lane == 0) {
+            s.red_part[2 * ch] = mn;
+            s.red_part[2 * ch + 1] = sm;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double bm = smin[0], bs = ssum[0];
-        for (int k = 1; k < kRedThreads / 32; ++k) {
-            bm = fmin(bm, smin[k]);
-            bs += ssum[k];
-        }
-        s.red_part[2 * blockIdx.x] = bm;
-        s.red_part[2 * blockIdx.x + 1] = bs;
         __threadfence();
-        unsigned ticket = atomicAdd(s.red_count, 1u);
-        last = (ticket == gridDim.x - 1);
+        last = atomicAdd(s.red_count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        const volatile double *part = s.red_part;
         double bm = 0.0, bs = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) {
-            bm = fmin(bm, part[2 * k]);
-            bs += part[2 * k + 1];
+        for (int k = 0; k < n_chunks; ++k) {
+            bm = fmin(bm, ldcg(&s.red_part[2 * k]));
+            bs += ldcg(&s.red_part[2 * k + 1]);
         }
         s.wns_tns[0] = bm;
         s.wns_tns[1] = bs;
         *s.red_count = 0u;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
+    pdl_wait();
+    wns_tns_blocks<R, false>(t, s);
+}
+
+// The whole backward sweep and WNS / TNS in one cooperative launch: levels
+// from the deepest down to the startpoints' nets, tasks of a level spread
+// over all warps, a grid-wide barrier after each level.
+template <typename R>
+__global__ void __launch_bounds__(kPsThreads, kBwdBlocksPerSM) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
+    const int lane = threadIdx.x & 31;
+    const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // task j on block j mod gridDim
+    const int wstride = (blockDim.x >> 5) * gridDim.x;
+    unsigned n = 0;
+    for (int l = t.depth; l >= 0; --l) {
+        const int4 q = ldg(&t.bw_lv[l]);  // small groups (first, count), pieces (first, count)
+        const int nt = bwd_tasks(q.y, q.w);
+        for (int w = w0; w < nt; w += wstride) bwd_task<R, true>(t, s, w, q.x, q.y, q.z, lane);
+        if (!grid_sync(gs, (++n) * gridDim.x)) return;
+    }
+    wns_tns_blocks<R, true>(t, s);
 }
 
 // ------------------------------------------------------------ launch ---
@@ -484,7 +805,7 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     for (int l = t.depth; bwd && l >= 0 && ok; --l) {
         const int ns = g->lv.bw_s_n[l], nb = g->lv.bw_b_n[l];
         if (ns + nb > 0) {
-            launch_pdl(k_bwd_level<R>, div_up((int64_t)(ns + nb) * 32, kLvThreads), kLvThreads, cs, t, s,
+            launch_pdl(k_bwd_level<R>, div_up((int64_t)bwd_tasks(ns, nb) * 32, kLvThreads), kLvThreads, cs, t, s,
                        g->lv.bw_s_lo[l], ns, g->lv.bw_b_lo[l], nb);
             ++nk;
         }
@@ -514,12 +835,58 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     return TDP_OK;
 }
 
-// Forward sweep (one graph replay), building sidetrack lists of length
-// g->list_L (0: none).  Run again, it writes the same arrival times.
+// Blocks of a cooperative launch of `kernel` that are resident at once (at
+// most kCoopMaxBlocks), cached per kernel; 0 if none.
+template <typename K>
+static int coop_grid(tdp_graph *g, K kernel) {
+    const void *key = reinterpret_cast<const void *>(kernel);
+    for (auto &pr : g->coop_grid)
+        if (pr.first == key) return pr.second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kPsThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 0;
+    }
+    const int grid = std::min(nb * g->n_sm, kCoopMaxBlocks);
+    g->coop_grid.emplace_back(key, grid);
+    return grid;
+}
+
+template <typename R>
+static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, GridSync), int grid,
+                               KernelId id) {
+    State<R> &s = state<R>(g);
+    GridSync gs;
+    gs.count = s.gsync;
+    gs.status = s.gsync + 1;
+    gs.timeout_ns = kSyncTimeoutNs;
+    LaunchScope ls(g, id);
+    TDP_CUDA(cudaMemsetAsync(s.gsync, 0, sizeof(unsigned), g->stream));
+    TDP_CUDA(launch_coop(kernel, grid, kPsThreads, g->stream, g->topo, s, gs));
+    return TDP_OK;
+}
+
+// Forward sweep, building sidetrack lists of length g->list_L (0: none): one
+// cooperative launch, or one graph replay of the level launches.  Run again,
+// it writes the same arrival times.
 template <typename R>
 tdp_status forward_lists(tdp_graph *g) {
     State<R> &s = state<R>(g);
-    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * (kMaxK - 1)));
+    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * kMaxK));
+    if (g->single_launch) {
+        if (g->topo.depth == 0) return TDP_OK;
+        void (*kernel)(Topo, State<R>, GridSync);
+        switch (g->list_L) {
+            case 0: kernel = k_fwd_sweep<R, 0>; break;
+            case 3: kernel = k_fwd_sweep<R, 3>; break;
+            case 7: kernel = k_fwd_sweep<R, 7>; break;
+            case 15: kernel = k_fwd_sweep<R, 15>; break;
+            default: kernel = k_fwd_sweep<R, 31>; break;
+        }
+        const int grid = coop_grid(g, kernel);
+        if (grid > 0) return launch_sweep<R>(g, kernel, grid, KID_FWD_SWEEP);
+        g->single_launch = false;  // no resident grid: per-level launches from now on
+    }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
         if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
         g->fwd_graph = nullptr;
@@ -531,9 +898,14 @@ tdp_status forward_lists(tdp_graph *g) {
     return TDP_OK;
 }
 
-// Backward sweep and WNS / TNS (one graph replay).
+// Backward sweep and WNS / TNS: one cooperative launch, or one graph replay.
 template <typename R>
 static tdp_status backward(tdp_graph *g) {
+    if (g->single_launch) {
+        const int grid = coop_grid(g, k_bwd_sweep<R>);
+        if (grid > 0) return launch_sweep<R>(g, k_bwd_sweep<R>, grid, KID_BWD_SWEEP);
+        g->single_launch = false;
+    }
     if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
     LaunchScope ls(g, KID_BWD_SWEEP, g->bwd_graph_kernels);
     TDP_CUDA(cudaGraphLaunch(g->bwd_graph, g->stream));
@@ -560,7 +932,7 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
                                                                  (R)g->d0, nsb);
     }
     TDP_LAUNCH_CHECK();
-    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * (kMaxK - 1)));
+    if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * kMaxK));
     TDP_TRY(sweep<R>(g));
     return TDP_OK;
 }
@@ -621,7 +993,7 @@ extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void 
         double h[2];
         const double *src = g->prec == TDP_FP32 ? g->s32.wns_tns : g->s64.wns_tns;
         TDP_CUDA(cudaMemcpyAsync(h, src, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
-        TDP_CUDA(cudaStreamSynchronize(g->stream));
+        TDP_TRY(check_sync_status(g));  // synchronises the stream
         if (wns_out) *wns_out = h[0];
         if (tns_out) *tns_out = h[1];
     }

@@ -308,30 +308,48 @@ def test_autograd_finite_differences(prec):
                 assert abs(fd - gref[c]) <= bound, (c, fd, gref[c], bound)
 
 
-def test_full_pipeline_is_deterministic():
-    nl = netgen.generate("mid", 2)
-    T = oracle.clock_period(nl, 0.85)
-    outs = []
-    for _ in range(2):
-        G = _graph(nl, "fp32")
-        x, y = _pos(nl, G.dtype)
-        r = [G.sta_propagate(x, y, T)]
-        G.extract_critical_paths(-1, 16, False)
-        P = gpu_paths(G)
-        G.attraction_update_pairs(10.0, 0.2)
-        pins, w = G.attraction_get_pairs()
-        loss = G.attraction_loss_fwd(x, y, 2.5e-5)
-        gx, gy = G.attraction_loss_bwd(x, y, 2.5e-5)
-        outs.append((r, P, pins.cpu().numpy(), w.cpu().numpy(), loss.item(), gx.cpu().numpy(),
-                     gy.cpu().numpy(), [t.cpu().numpy() for t in G.sta_get_timing()]))
-    a, b = outs
+def _pipeline(nl, T, prec):
+    G = _graph(nl, prec)
+    x, y = _pos(nl, G.dtype)
+    r = [G.sta_propagate(x, y, T)]
+    G.extract_critical_paths(-1, 16, False)
+    P = gpu_paths(G)
+    G.attraction_update_pairs(10.0, 0.2)
+    pins, w = G.attraction_get_pairs()
+    loss = G.attraction_loss_fwd(x, y, 2.5e-5)
+    gx, gy = G.attraction_loss_bwd(x, y, 2.5e-5)
+    return (r, P, pins.cpu().numpy(), w.cpu().numpy(), loss.item(), gx.cpu().numpy(),
+            gy.cpu().numpy(), [t.cpu().numpy() for t in G.sta_get_timing()])
+
+
+def _assert_same(a, b):
     assert a[0] == b[0] and a[4] == b[4]
-    for k in P:
+    assert a[1].keys() == b[1].keys()
+    for k in a[1]:
         np.testing.assert_array_equal(a[1][k], b[1][k])
     for i in (2, 3, 5, 6):
         np.testing.assert_array_equal(a[i], b[i])
     for u, v in zip(a[7], b[7]):
         np.testing.assert_array_equal(u, v)
+
+
+def test_full_pipeline_is_deterministic():
+    nl = netgen.generate("mid", 2)
+    T = oracle.clock_period(nl, 0.85)
+    _assert_same(_pipeline(nl, T, "fp32"), _pipeline(nl, T, "fp32"))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_level_launches_match_single_launch_sweeps(prec, monkeypatch):
+    """The per-level CUDA-graph sweeps (used where a cooperative launch cannot
+    be resident) do the same arithmetic in the same order as the single-launch
+    sweeps: every output is bit-identical."""
+    nl = netgen.generate("mid", 5)
+    T = oracle.clock_period(nl, 0.85)
+    one = _pipeline(nl, T, prec)
+    monkeypatch.setenv("TDP_LEVEL_GRAPHS", "1")
+    lv = _pipeline(nl, T, prec)
+    _assert_same(one, lv)
 
 
 # --------------------------------------------------------- edge cases ------
