@@ -312,6 +312,19 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     // kBwPart sinks of the larger nets
     std::vector<BwTask> bw;
     std::vector<int32_t> bw_sa, bw_sb;
+    std::vector<int4> bw_slot;  // kBwSmallFanout per small-net slot
+    auto push_slots = [&](int a, int b) {
+        for (int gl = 0; gl < kBwSmallFanout; ++gl) {
+            const int p = a < 0 ? -1 : a + 1 + gl;
+            if (p < 0 || p >= b) {
+                bw_slot.push_back(make_int4(-1, 0, 0, 0));
+                continue;
+            }
+            int fl = kind[p];
+            if (kind[p] == PK_COMB_IN && level[d->pin_cell[p]] == net_level[pin_net[p]] + 1) fl |= kKindPrev;
+            bw_slot.push_back(make_int4(p, fl, sink_out[p], sink_onet[p]));
+        }
+    };
     int n_slots = 0, n_split = 0;
     std::vector<int32_t> s_lo(D + 1), s_n(D + 1), b_lo(D + 1), b_n(D + 1);
     for (int l = D; l >= 0; --l) {
@@ -324,6 +337,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             if (f <= kBwSmallFanout) {
                 bw_sa.push_back(a);
                 bw_sb.push_back(b);
+                push_slots(a, b);
                 continue;
             }
             const int parts = (f + kBwPart - 1) / kBwPart;
@@ -338,6 +352,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
         while (bw_sa.size() % 32) {
             bw_sa.push_back(-1);
             bw_sb.push_back(-1);
+            push_slots(-1, -1);
         }
         s_n[l] = (int32_t)(bw_sa.size() / 32) - s_lo[l];
         b_n[l] = (int32_t)bw.size() - b_lo[l];
@@ -348,6 +363,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(upload(g, &t.bw_task, bw));
     TDP_TRY(upload(g, &t.bw_sa, bw_sa));
     TDP_TRY(upload(g, &t.bw_sb, bw_sb));
+    TDP_TRY(upload(g, &t.bw_slot, bw_slot));
     t.n_cells = nc;
     t.n_pins = np;
     t.n_nets = nn;
@@ -384,6 +400,18 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(upload(g, &t.lv_in_drv, lv_in_drv));
     TDP_TRY(upload(g, &t.lv_in_net, lv_in_net));
     TDP_TRY(upload(g, &t.lv_in_flags, lv_in_flags));
+    {
+        std::vector<int4> rec(n_comb), slot((size_t)n_comb * kPre, make_int4(-1, -1, -1, 0));
+        for (int k = 0; k < n_comb; ++k) {
+            const int a = lv_in_ptr[k], nin = lv_in_ptr[k + 1] - a;
+            rec[k] = make_int4(lv_onet[k], lv_out[k], nin, a);
+            for (int u = 0; u < nin && nin <= kPre; ++u)
+                slot[(size_t)k * kPre + u] = make_int4(lv_in_pin[a + u], lv_in_net[a + u], lv_in_drv[a + u],
+                                                       lv_in_flags[a + u]);
+        }
+        TDP_TRY(upload(g, &t.lv_rec, rec));
+        TDP_TRY(upload(g, &t.lv_slot, slot));
+    }
     TDP_TRY(upload(g, &t.ep, ep));
     TDP_TRY(upload(g, &t.cp_ptr, cp_ptr));
     TDP_TRY(upload(g, &t.cp, cp));

@@ -49,6 +49,9 @@ enum PinKind : uint8_t { PK_COMB_IN = 0, PK_ENDPOINT = 1, PK_COMB_OUT = 2, PK_ST
 // combinational cell; that driver is one level below the cell (level 0:
 // flip-flops and primary inputs)
 constexpr uint8_t kInComb = 1, kInPrev = 2;
+// flag on a combinational input in the backward sweep's sink slots: its cell
+// is one level above the net's driver
+constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 
 // Kernels that can be timed with tdp_profile_kernel (names in tdp_build.cu).
 // The level sweeps are replayed from CUDA graphs: fwd_sweep is one replay of
@@ -213,13 +216,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Returns false (in every thread of the block) when the wait gave up.
-__device__ __forceinline__ bool grid_sync(const GridSync &gs, unsigned target) {
-    __shared__ int ok;
+// grid_wait returns false (in every thread of the block) when the wait gave up.
+// The barrier in two halves: grid_arrive (every thread; this block's writes
+// become visible before its arrival is counted) and grid_wait (every
+// thread); work that needs no other block's results of this step can run in
+// between.
+__device__ __forceinline__ void grid_arrive(const GridSync &gs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();  // this block's writes before its arrival
         atomicAdd(gs.count, 1u);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(const GridSync &gs, unsigned target) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
         int good = 1;
         unsigned long long t0 = 0;
         for (unsigned it = 1; ld_acquire(gs.count) < target; ++it) {
@@ -243,6 +255,11 @@ __device__ __forceinline__ bool grid_sync(const GridSync &gs, unsigned target) {
     }
     __syncthreads();
     return ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(const GridSync &gs, unsigned target) {
+    grid_arrive(gs);
+    return grid_wait(gs, target);
 }
 
 template <typename... KArgs, typename... Args>
@@ -290,6 +307,11 @@ struct Topo {
     int32_t *lv_in_drv = nullptr;  // [n_in] driver pin of the input's net
     int32_t *lv_in_net = nullptr;  // [n_in] net of the input
     uint8_t *lv_in_flags = nullptr; // [n_in] kInComb | kInPrev
+    // the same, padded for loads in one round: per cell (net driven, output
+    // pin, inputs, first input), and kPre input slots per cell
+    // (pin, net, driver pin, flags) for cells of at most kPre inputs
+    int4 *lv_rec = nullptr;        // [n_comb]
+    int4 *lv_slot = nullptr;       // [n_comb * kPre]
     int32_t *ep = nullptr;         // [n_ep] endpoint pins, ascending
     int32_t *cp_ptr = nullptr;     // [n_cells+1] cell -> pins CSR
     int32_t *cp = nullptr;         // [n_pins]
@@ -298,6 +320,9 @@ struct Topo {
     // backward sweep, highest level first: groups of 32 small nets given by
     // driver pin / end pin per lane (-1 pads), and pieces of larger nets
     int32_t *bw_sa = nullptr, *bw_sb = nullptr;
+    // per small-net slot, kBwSmallFanout sink slots (pin, kind | kKindPrev,
+    // its cell's output pin, net driven by its cell; pin -1: none)
+    int4 *bw_slot = nullptr;
     BwTask *bw_task = nullptr;
     int32_t n_bw_tasks = 0, n_bw_slots = 0, n_bw_split = 0;
     // device copies of the level structure for the single-launch sweeps:

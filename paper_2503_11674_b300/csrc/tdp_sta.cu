@@ -262,226 +262,267 @@ __device__ __noinline__ void fwd_cell_wide(const Topo &t, State<R> &s, int k, in
     }
 }
 
-// ---- one cell per group of G lanes (the common case)
+// ---- one cell per thread (at most kPre inputs: the common case)
 
-template <typename T>
-__device__ __forceinline__ T shfl_idx(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ fx2 shfl_idx(fx2 v, int src) {
-    return fx2{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
-}
-template <typename T>
-__device__ __forceinline__ T shfl_x(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ fx2 shfl_x(fx2 v, int o) {
-    return fx2{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+// A list entry in registers.  FP32: one 64-bit sort key, the order-
+// preserving bits of the cost above the 32-bit ordering key, so that an
+// entry compares in one integer comparison; FP64: the pair (cost, key).
+__device__ __forceinline__ float from_ord(uint32_t o) {
+    return (o & 0x80000000u) ? __uint_as_float(o & 0x7fffffffu) : __uint_as_float(~o);
 }
 
-// What one lane of a group knows about its group's cell k (k < 0: none) and
-// about the input with index gl (the lane's index in the group), if any:
-// its pin, net, driver pin and flags, and, once loaded, its Elmore delay
-// (has_tv) and its driver's arrival and chain length (has_old).
 template <typename R>
-struct LaneTopo {
-    using A = typename Acc<R>::T;
-    int k, a, b, e, o;
-    int ip, in, dv, fl;
-    bool has_tv, has_old;
-    R tv;
-    A ad;
-    int pl;
+struct LReg;
+template <>
+struct LReg<float> {
+    using E = uint64_t;
+    static __device__ __forceinline__ E make(float d, uint32_t key) {
+        return ((uint64_t)ord_bits(d) << 32) | key;
+    }
+    static __device__ __forceinline__ E none() { return make(r_inf<float>(), kNoneKey); }
+    static __device__ __forceinline__ bool before(E a, E b) { return a < b; }
+    static __device__ __forceinline__ uint32_t key(E a) { return (uint32_t)a; }
+    static __device__ __forceinline__ float cost(E a) { return from_ord((uint32_t)(a >> 32)); }
+};
+template <>
+struct LReg<double> {
+    using E = LEnt<double>;
+    static __device__ __forceinline__ E make(double d, uint32_t key) { return E{d, key}; }
+    static __device__ __forceinline__ E none() { return E{r_inf<double>(), kNoneKey}; }
+    static __device__ __forceinline__ bool before(const E &a, const E &b) { return lent_before(a, b); }
+    static __device__ __forceinline__ uint32_t key(const E &a) { return a.key; }
+    static __device__ __forceinline__ double cost(const E &a) { return a.d; }
 };
 
-// Topology of cell k for lane gl.  With old_vals (single launch, before the
-// barrier that opens the cell's level), also the values that are already
-// final: the input's Elmore delay, and its driver's arrival and chain length
-// unless the driver is on the level just below (still being computed).
-template <typename R, int G>
-__device__ __forceinline__ void lane_topo(const Topo &t, const State<R> &s, int k, int gl,
-                                          LaneTopo<R> &c, bool old_vals) {
+template <typename R>
+__device__ __forceinline__ typename LReg<R>::E lreg_of(float d, int32_t pin) {
+    return LReg<R>::make(d, pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)pin));
+}
+template <typename R>
+__device__ __forceinline__ typename LReg<R>::E lreg_of(double d, int32_t pin) {
+    return LReg<R>::make(d, pin < 0 ? kNoneKey : ((1u << 29) | (uint32_t)pin));
+}
+template <typename R>
+__device__ __forceinline__ int32_t lreg_pin(const typename LReg<R>::E &x) {
+    const uint32_t k = LReg<R>::key(x);
+    return k == kNoneKey ? -1 : (int32_t)(k & kPinMask);
+}
+
+// insert x into a sorted list held in registers, keeping its first L entries
+// (compare-and-shift from the top); inserting LReg::none() changes nothing
+template <typename R, int L>
+__device__ __forceinline__ void list_insert(typename LReg<R>::E (&li)[L], const typename LReg<R>::E &x) {
+#pragma unroll
+    for (int j = L - 1; j >= 0; --j) {
+        const bool shift = j > 0 && LReg<R>::before(x, li[j - 1]);
+        const bool here = LReg<R>::before(x, li[j]);
+        li[j] = shift ? li[j - 1] : (here ? x : li[j]);
+    }
+}
+
+// list I/O in aligned vectors: a list block is G = L + 1 entries; the entry
+// after the L-th is padding (written as a sentinel)
+template <int L, bool COH>
+__device__ __forceinline__ void list_load(const BEnt<float> *src, uint64_t (&li)[L]) {
+    const float4 *v4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int q = 0; q < list_group(L) / 2; ++q) {
+        const float4 v = ldd<COH>(&v4[q]);
+        if (2 * q < L) li[2 * q] = lreg_of<float>(v.x, __float_as_int(v.y));
+        if (2 * q + 1 < L) li[2 * q + 1] = lreg_of<float>(v.z, __float_as_int(v.w));
+    }
+}
+template <int L, bool COH>
+__device__ __forceinline__ void list_load(const BEnt<double> *src, LEnt<double> (&li)[L]) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const BEnt<double> v = ldd<COH>(&src[j]);
+        li[j] = lreg_of<double>(v.delta, v.pin);
+    }
+}
+template <int L>
+__device__ __forceinline__ void list_put(BEnt<float> *dst, const uint64_t (&li)[L]) {
+    float4 *v4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < list_group(L) / 2; ++q) {
+        const uint64_t x = 2 * q < L ? li[2 * q] : LReg<float>::none();
+        const uint64_t y = 2 * q + 1 < L ? li[2 * q + 1] : LReg<float>::none();
+        v4[q] = make_float4(LReg<float>::cost(x), __int_as_float(lreg_pin<float>(x)), LReg<float>::cost(y),
+                            __int_as_float(lreg_pin<float>(y)));
+    }
+}
+template <int L>
+__device__ __forceinline__ void list_put(BEnt<double> *dst, const LEnt<double> (&li)[L]) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) dst[j] = BEnt<double>{li[j].d, lreg_pin<double>(li[j])};
+}
+
+// One cell for one thread: cell k (k < 0: none), its inputs when it has at
+// most kPre, and, once loaded (vals), the values that stay fixed during the
+// sweep (the cell delay, the inputs' Elmore delays) and the arrival and chain
+// length of drivers two or more levels down (bit u of old).
+template <typename R>
+struct CellPre {
+    using A = typename Acc<R>::T;
+    int k, a, b, e, o;
+    int ip[kPre], in[kPre], dv[kPre];
+    unsigned fl, old;
+    bool vals;
+    R dcell;
+    R tv[kPre];
+    A ad[kPre];
+    int pl[kPre];
+};
+
+// topology of cell k: the cell record and its input slots, one round of loads
+template <typename R>
+__device__ __forceinline__ void cell_topo(const Topo &t, int k, CellPre<R> &c) {
     c.k = k;
     c.a = c.b = 0;
-    c.has_tv = c.has_old = false;
+    c.fl = c.old = 0u;
+    c.vals = false;
     if (k < 0) return;
-    c.a = ldg(&t.lv_in_ptr[k]);
-    c.b = ldg(&t.lv_in_ptr[k + 1]);
-    c.e = ldg(&t.lv_onet[k]);
-    c.o = ldg(&t.lv_out[k]);
-    if (c.b - c.a <= G && gl < c.b - c.a) {
-        c.ip = ldg(&t.lv_in_pin[c.a + gl]);
-        c.in = ldg(&t.lv_in_net[c.a + gl]);
-        c.dv = ldg(&t.lv_in_drv[c.a + gl]);
-        c.fl = ldg(&t.lv_in_flags[c.a + gl]);
-        if (old_vals) {
-            c.tv = ldg(&s.tnet[c.ip]);
-            c.has_tv = true;
-            if (!(c.fl & kInPrev)) {
-                c.ad = ldcg(&s.arr[c.dv]);
-                c.pl = ldcg(&s.plen[c.in]);
-                c.has_old = true;
-            }
+    const int4 r = ldg(&t.lv_rec[k]);
+    int4 sl[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) sl[u] = ldg(&t.lv_slot[(size_t)k * kPre + u]);
+    c.e = r.x;
+    c.o = r.y;
+    c.a = r.w;
+    c.b = r.w + r.z;
+    const int nin = r.z;
+    if (nin > kPre) return;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        if (u < nin) {
+            c.ip[u] = sl[u].x;
+            c.in[u] = sl[u].y;
+            c.dv[u] = sl[u].z;
+            c.fl |= (unsigned)sl[u].w << (8 * u);
         }
     }
 }
 
-// Arrival of the group's cell (Section II-B: max over its inputs of the
-// driver's arrival plus the Elmore delay, plus the cell delay) and, when
-// L > 0, its sidetrack list: lane j holds input j and entry j of the
-// inherited list; the own deviations are merged in by rank (an entry's rank
-// is the number of entries of both lists before it), and the first L of the
-// merged list are written, one aligned block per list.  Every lane of the
-// warp calls this (shuffles and ballots span the warp); COH: the drivers'
-// values were written by other blocks of the same launch.  Warps whose cells
-// all have at most kPre inputs take an unrolled path.
+// the values of cell c that are already final before the barrier that opens
+// its level (single launch): one round of loads
+template <typename R>
+__device__ __forceinline__ void cell_vals(const State<R> &s, CellPre<R> &c) {
+    if (c.k < 0) return;
+    const int nin = c.b - c.a;
+    if (nin > kPre) return;
+    c.dcell = ldg(&s.dnet[c.e]);
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        if (u < nin) {
+            c.tv[u] = ldg(&s.tnet[c.ip[u]]);
+            if (!((c.fl >> (8 * u)) & kInPrev)) {
+                c.ad[u] = ldcg(&s.arr[c.dv[u]]);
+                c.pl[u] = ldcg(&s.plen[c.in[u]]);
+                c.old |= 1u << u;
+            }
+        }
+    }
+    c.vals = true;
+}
+
+// Arrival of one cell (Section II-B: max over its inputs of the driver's
+// arrival plus the Elmore delay, plus the cell delay) and, when L > 0, its
+// sidetrack list.  COH: the drivers' values were written by other blocks of
+// the same launch.
+
 template <typename R, int L, bool COH>
-__device__ __forceinline__ void fwd_group(const Topo &t, State<R> &s, const LaneTopo<R> &c, int lane) {
-    constexpr int G = list_group(L);
-    constexpr unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+__device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, const CellPre<R> &c) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    const unsigned FULL = 0xffffffffu;
-    const int gl = lane & (G - 1), gbase = lane & ~(G - 1);
-    const int nin = c.k >= 0 ? c.b - c.a : 0;
-    const bool wide = nin > G;
-    const bool act = c.k >= 0 && !wide;
-    const bool mine = act && gl < nin;
-    const bool narrow = __all_sync(FULL, nin <= kPre);
-    A av = AC::ninf();
-    int pl = 0;
-    R dcell = R(0);
-    if (mine) {
-        const R tv = c.has_tv ? c.tv : ldg(&s.tnet[c.ip]);
-        A ad;
-        if (c.has_old) {
-            ad = c.ad;
-            pl = c.pl;
-        } else {
-            ad = ldd<COH>(&s.arr[c.dv]);
-            pl = ldd<COH>(&s.plen[c.in]);
-        }
-        av = AC::add(ad, tv);
+    using LR = LReg<R>;
+    if (c.k < 0) return;
+    const int nin = c.b - c.a;
+    if (nin > kPre) {
+        fwd_cell_wide<R, L, COH>(t, s, c.k, c.a, c.b);
+        return;
     }
-    if (act && gl == 0) dcell = ldg(&s.dnet[c.e]);
-    // worst input: largest arrival, lowest pin on ties
-    A best = av;
-    int bi = mine ? c.ip : -1;
-    bool bv = mine;
-    int wl = 0;  // lane (in the group) of the worst input
-    int bn = -1, bl = 0, bc = 0;
-    if (narrow) {
+    // every load first, then the arithmetic, then the stores
+    const R dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
+    A av[kPre];
+    R tv[kPre];
+    int pl[kPre];
 #pragma unroll
-        for (int o = 1; o < kPre; o <<= 1) {
-            const A oa = shfl_x(best, o);
-            const int oi = shfl_x(bi, o);
-            const bool ov = shfl_x((int)bv, o) != 0;
-            if (ov && (!bv || AC::gt(oa, best) || (!AC::gt(best, oa) && oi < bi))) {
-                best = oa;
-                bi = oi;
-                bv = true;
-            }
-        }
-        best = shfl_idx(best, gbase);
-        bi = shfl_idx(bi, gbase);
-        bv = shfl_idx((int)bv, gbase) != 0;
-        const unsigned wm = (__ballot_sync(FULL, mine && c.ip == bi) >> gbase) & gmask;
-        wl = wm ? __ffs(wm) - 1 : 0;
-        bn = shfl_idx(c.in, gbase + wl);
-        bl = shfl_idx(pl, gbase + wl);
-        bc = shfl_idx(c.fl, gbase + wl) & kInComb;
-    } else {
-        bn = mine ? c.in : -1;
-        bl = pl;
-        bc = mine ? (c.fl & kInComb) : 0;
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            const A oa = shfl_x(best, o);
-            const int oi = shfl_x(bi, o), on = shfl_x(bn, o), ol = shfl_x(bl, o), oc = shfl_x(bc, o);
-            const bool ov = shfl_x((int)bv, o) != 0;
-            if (ov && (!bv || AC::gt(oa, best) || (!AC::gt(best, oa) && oi < bi))) {
-                best = oa;
-                bi = oi;
-                bn = on;
-                bl = ol;
-                bc = oc;
-                bv = true;
+    for (int u = 0; u < kPre; ++u) {
+        if (u < nin) {
+            tv[u] = c.vals ? c.tv[u] : ldg(&s.tnet[c.ip[u]]);
+            if ((c.old >> u) & 1u) {
+                av[u] = c.ad[u];
+                pl[u] = c.pl[u];
+            } else {
+                av[u] = ldd<COH>(&s.arr[c.dv[u]]);
+                pl[u] = ldd<COH>(&s.plen[c.in[u]]);
             }
         }
     }
-    if (!bv) {
-        bi = bn = -1;
-        bl = bc = 0;
+    // inputs ascending by pin: strict > keeps the lowest pin on ties (and the
+    // first input if arrivals are not comparable)
+    int bi = -1, bn = -1, bl = 0, bu = 0;
+    A best = AC::ninf();
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        if (u < nin) {
+            av[u] = AC::add(av[u], tv[u]);
+            if (bi < 0 || AC::gt(av[u], best)) {
+                best = av[u];
+                bi = c.ip[u];
+                bn = c.in[u];
+                bl = pl[u];
+                bu = u;
+            }
+        }
     }
-    if (mine) s.arr[c.ip] = av;
-    if (act && gl == 0) {
-        s.arr[c.o] = AC::add(best, dcell);
-        s.pred_in[c.e] = bi;
-        s.pred_net[c.e] = bn;
-        s.plen[c.e] = bl + 2;
-    }
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (u < nin) s.arr[c.ip[u]] = av[u];
+    s.arr[c.o] = AC::add(best, dcell);
+    s.pred_in[c.e] = bi;
+    s.pred_net[c.e] = bn;
+    s.plen[c.e] = bl + 2;
     if constexpr (L > 0) {
-        LEnt<R> inh{r_inf<R>(), kNoneKey};
-        if (act && gl < L && bc) inh = lent_of(ldd<COH>(&s.blist[(size_t)bn * G + gl]));
-        const bool has_own = mine && c.ip != bi;
-        const LEnt<R> own{AC::diff(best, av), ((c.ip < bi ? 0u : 2u) << 29) | (uint32_t)c.ip};
-        int inh_rank = gl, own_rank = 0;
-        if (narrow) {  // the group's inputs are its lanes 0..nin-1
-            unsigned mb = 0u;
-#pragma unroll
-            for (int u = 0; u < kPre; ++u) {
-                const LEnt<R> x{shfl_idx(own.d, gbase + u), shfl_idx(own.key, gbase + u)};
-                const bool xv = bv && u < nin && u != wl;
-                if (xv && gl < L && lent_before(x, inh)) ++inh_rank;
-                if (xv && has_own && u != gl && lent_before(x, own)) ++own_rank;
-                const unsigned bb = __ballot_sync(FULL, xv && gl < L && lent_before(inh, x));
-                if (gl == u) mb = bb;
-            }
-            own_rank += __popc((mb >> gbase) & gmask);
+        constexpr int G = list_group(L);
+        typename LR::E li[L];
+        if (nin > 0 && ((c.fl >> (8 * bu)) & kInComb)) {
+            list_load<L, COH>(s.blist + (size_t)bn * G, li);
         } else {
-            bool done = !has_own;
-            for (;;) {  // broadcast the group's own deviations one at a time
-                const unsigned rem = __ballot_sync(FULL, !done);
-                if (rem == 0u) break;
-                const unsigned gm = (rem >> gbase) & gmask;
-                const bool live = gm != 0u;
-                const int src = live ? __ffs(gm) - 1 : 0;
-                const LEnt<R> x{shfl_idx(own.d, gbase + src), shfl_idx(own.key, gbase + src)};
-                if (live && gl < L && lent_before(x, inh)) ++inh_rank;
-                if (live && has_own && gl != src && lent_before(x, own)) ++own_rank;
-                const unsigned bb = __ballot_sync(FULL, live && gl < L && lent_before(inh, x));
-                if (live && gl == src) {
-                    own_rank += __popc((bb >> gbase) & gmask);
-                    done = true;
-                }
-            }
+#pragma unroll
+            for (int j = 0; j < L; ++j) li[j] = LR::none();
         }
-        BEnt<R> *out = s.blist + (size_t)(act ? c.e : 0) * G;
-        if (act && gl < L && inh_rank < L) out[inh_rank] = bent_of(inh);
-        if (has_own && own_rank < L) out[own_rank] = BEnt<R>{own.d, c.ip};
-        const unsigned vi = __ballot_sync(FULL, act && gl < L && inh.key != kNoneKey);
-        const unsigned vo = __ballot_sync(FULL, has_own);
-        if (act && gl == 0)
-            s.bcnt[c.e] = min(L, __popc((vi >> gbase) & gmask) + __popc((vo >> gbase) & gmask));
+        // every thread inserts kPre entries (absent ones as no-op sentinels),
+        // so that the threads of a warp do not diverge
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool own = u < nin && u != bu;
+            const uint32_t key = ((c.ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)c.ip[u];
+            list_insert<R, L>(li, own ? LR::make(AC::diff(best, av[u]), key) : LR::none());
+        }
+        list_put<L>(s.blist + (size_t)c.e * G, li);
+        int m = 0;
+#pragma unroll
+        for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
+        s.bcnt[c.e] = m;
     }
-    if (wide && gl == 0) fwd_cell_wide<R, L, COH>(t, s, c.k, c.a, c.b);
 }
 
-// One launch per level (captured in a CUDA graph): a group of lanes per cell.
+// One launch per level (captured in a CUDA graph): a thread per cell.
 template <typename R, int L>
 __global__ void __launch_bounds__(kLvThreads) k_fwd_level(Topo t, State<R> s, int lo, int hi) {
-    constexpr int G = list_group(L), CPW = 32 / G;
     pdl_trigger();
-    const int lane = threadIdx.x & 31;
-    const int chunk = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (lo + chunk * CPW >= hi) return;  // whole warps only
-    const int k = lo + chunk * CPW + lane / G;
-    LaneTopo<R> c;
-    lane_topo<R, G>(t, s, k < hi ? k : -1, lane & (G - 1), c, false);
+    const int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= hi) return;
+    CellPre<R> c;
+    cell_topo(t, k, c);
     pdl_wait();  // the timing loads read what earlier launches wrote
-    fwd_group<R, L, false>(t, s, c, lane);
+    fwd_cell<R, L, false>(t, s, c);
 }
 
 template <typename R>
 static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, cudaStream_t cs) {
-    const int CPW = 32 / list_group(L);
-    const int grid = div_up((int64_t)div_up(hi - lo, CPW) * 32, kLvThreads);
+    const int grid = div_up(hi - lo, kLvThreads);
     switch (L) {
         case 0: launch_pdl(k_fwd_level<R, 0>, grid, kLvThreads, cs, t, s, lo, hi); break;
         case 3: launch_pdl(k_fwd_level<R, 3>, grid, kLvThreads, cs, t, s, lo, hi); break;
@@ -491,48 +532,58 @@ static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, 
     }
 }
 
-// Single-launch sweeps: one block of kPsThreads per SM (64 registers a
-// thread), as many warps in flight as registers allow, since a level is a few
-// latency-bound steps per warp; one block per SM keeps the barrier short.
-constexpr int kPsThreads = 1024;
-constexpr int kFwdBlocksPerSM = 1;
-constexpr int kBwdBlocksPerSM = 1;
+// Single-launch sweeps: one block per SM (kFwdThreads / kBwdThreads threads),
+// a level's work cut into warp-sized chunks, chunk j on block j mod gridDim
+// so that a level is spread over every SM.
+constexpr int kFwdThreads = 256;
+constexpr int kBwdThreads = 512;
 
 // The whole forward sweep in one cooperative launch: levels in order, a
-// level's cells in chunks of 32 / G (one per warp), chunk j on block
-// j mod gridDim (spreading a level over every SM), a grid-wide barrier
-// between levels.  Before each barrier a warp loads its first chunk of the
-// next level: topology, Elmore delays and the values of drivers two or more
-// levels down, so only the values the level below wrote are left after it.
+// thread per cell, a grid-wide barrier between levels.  A thread carries its
+// first cell of the next two levels: between its arrival at the barrier that
+// closes level l and the wait, it loads, in one round, the final values of
+// its level l + 1 cell (cell delay, Elmore delays, drivers two or more
+// levels down) and the topology of its level l + 2 cell, so that after the
+// barrier only the values level l wrote are left to load.
 template <typename R, int L>
-__global__ void __launch_bounds__(kPsThreads, kFwdBlocksPerSM) k_fwd_sweep(Topo t, State<R> s, GridSync gs) {
-    constexpr int G = list_group(L), CPW = 32 / G;
-    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane & (G - 1);
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s, GridSync gs) {
+    const int lane = threadIdx.x & 31;
     const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // first chunk of this warp
     const int wstride = (blockDim.x >> 5) * gridDim.x;
-    auto topo_of = [&](int l, int chunk, LaneTopo<R> &c, bool old_vals) {
-        const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * CPW + grp;
-        lane_topo<R, G>(t, s, k < ldg(&t.lvl_ptr[l]) ? k : -1, gl, c, old_vals);
+    auto cell_of = [&](int l, int chunk) {
+        if (l > t.depth) return -1;
+        const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * 32 + lane;
+        return k < ldg(&t.lvl_ptr[l]) ? k : -1;
     };
-    LaneTopo<R> pre;
-    if (t.depth > 0) topo_of(1, w0, pre, false);
+    CellPre<R> cur, nxt;
+    cell_topo(t, cell_of(1, w0), cur);
+    cell_topo(t, cell_of(2, w0), nxt);
     for (int l = 1; l <= t.depth; ++l) {
-        const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), CPW);
+        const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), 32);
         if (w0 < nch) {
-            fwd_group<R, L, true>(t, s, pre, lane);
+            fwd_cell<R, L, true>(t, s, cur);
             for (int ch = w0 + wstride; ch < nch; ch += wstride) {
-                LaneTopo<R> c;
-                topo_of(l, ch, c, false);
-                fwd_group<R, L, true>(t, s, c, lane);
+                CellPre<R> c;
+                cell_topo(t, cell_of(l, ch), c);
+                fwd_cell<R, L, true>(t, s, c);
             }
         }
         if (l == t.depth) break;
-        topo_of(l + 1, w0, pre, true);
-        if (!grid_sync(gs, (unsigned)l * gridDim.x)) return;
+        grid_arrive(gs);
+        cur = nxt;
+        cell_vals(s, cur);                // drivers below level l are final
+        cell_topo(t, cell_of(l + 2, w0), nxt);
+        if (!grid_wait(gs, (unsigned)l * gridDim.x)) return;
     }
 }
 
 // ----------------------------------------------------------- backward ---
+
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ fx2 shfl_x(fx2 v, int o) {
+    return fx2{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
 
 // req / slack of the sinks first, first+step, ... < b of the net driven by
 // pin a, NP sinks per round of loads; returns min over them of req(s) - t(s)
@@ -600,53 +651,128 @@ __device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State
     return m;
 }
 
-// A net of at most kBwSmallFanout sinks in slot i of the small-net table,
-// on a group of kBwSmallFanout lanes (a sink per lane; slots of -1 pad a
-// level's table).  Every lane of the warp calls this.
-template <typename R, bool COH>
-__device__ __forceinline__ void bwd_small(const Topo &t, State<R> &s, int i, int lane) {
-    using AC = Acc<R>;
-    using A = typename AC::T;
-    const int gl = lane & (kBwSmallFanout - 1);
-    const int a = ldg(&t.bw_sa[i]), b = ldg(&t.bw_sb[i]);
-    const int p = a + 1 + gl;
-    const bool mine = a >= 0 && p < b;
-    int kd = 0, so = 0, sn = 0;
-    if (mine) {
-        kd = ldg(&t.pin_kind[p]);
-        so = ldg(&t.sink_out[p]);
-        sn = ldg(&t.sink_onet[p]);
-    }
-    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
-    A m = AC::pinf(), ad = AC::pinf();
-    if (a >= 0) ad = ldg(&s.arr[a]);
-    if (mine) {
-        const R tp = ldg(&s.tnet[p]);
-        A rq, ap;
-        if (kd == PK_ENDPOINT) {
-            ap = AC::add(ad, tp);
-            rq = acc_from_double<R>(*s.T);
-            s.arr[p] = ap;
-        } else {
-            rq = AC::add(ldd<COH>(&s.req[so]), -ldg(&s.dnet[sn]));
-            ap = ldg(&s.arr[p]);
-        }
-        s.req[p] = rq;
-        s.slack[p] = AC::diff(rq, ap);
-        m = AC::add(rq, -tp);
-    }
+// Small nets (at most kBwSmallFanout sinks) go kBwLanes lanes to a net,
+// kBwPerLane sinks to a lane: sinks j = gl, gl + kBwLanes, ... of the net.
+constexpr int kBwLanes = 4;
+constexpr int kBwPerLane = kBwSmallFanout / kBwLanes;
+
+// One lane's share of the net in slot i of the small-net table (i < 0 or
+// a < 0: none): the driver pin a, the lane's sinks (pin -1: none) with their
+// kind and their cell's output pin and net, and, once loaded (vals), the
+// values that stay fixed during the sweep and, for sinks whose cell is two or
+// more levels up (bit j of old), their required time.
+template <typename R>
+struct SinkPre {
+    using A = typename Acc<R>::T;
+    int a;
+    int p[kBwPerLane], kd[kBwPerLane], so[kBwPerLane], sn[kBwPerLane];
+    unsigned old;
+    bool vals;
+    R tp[kBwPerLane], dn[kBwPerLane];
+    A ad, ap[kBwPerLane], rq[kBwPerLane];
+};
+
+// topology: one round of loads
+template <typename R>
+__device__ __forceinline__ void sink_topo(const Topo &t, int i, int gl, SinkPre<R> &c) {
+    c.vals = false;
+    c.old = 0u;
+    c.a = -1;
 #pragma unroll
-    for (int o = kBwSmallFanout / 2; o > 0; o >>= 1) {  // min is exact: any order gives the same value
-        const A other = shfl_x(m, o);
-        if (AC::lt(other, m)) m = other;
-    }
-    if (a >= 0 && gl == 0) {
-        s.req[a] = m;
-        s.slack[a] = AC::diff(m, ad);
+    for (int j = 0; j < kBwPerLane; ++j) c.p[j] = -1;
+    if (i < 0) return;
+    c.a = ldg(&t.bw_sa[i]);
+#pragma unroll
+    for (int j = 0; j < kBwPerLane; ++j) {
+        const int4 q = ldg(&t.bw_slot[(size_t)i * kBwSmallFanout + gl + j * kBwLanes]);
+        c.p[j] = q.x;
+        c.kd[j] = q.y;
+        c.so[j] = q.z;
+        c.sn[j] = q.w;
     }
 }
 
-constexpr int kBwNetsPerWarp = 32 / kBwSmallFanout;
+// the values that are final before the barrier that opens the net's level
+// (single launch): one round of loads
+template <typename R>
+__device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
+    if (c.a < 0) return;
+    c.ad = ldg(&s.arr[c.a]);
+#pragma unroll
+    for (int j = 0; j < kBwPerLane; ++j) {
+        if (c.p[j] < 0) continue;
+        c.tp[j] = ldg(&s.tnet[c.p[j]]);
+        if ((c.kd[j] & kKindMask) != PK_ENDPOINT) {
+            c.dn[j] = ldg(&s.dnet[c.sn[j]]);
+            c.ap[j] = ldg(&s.arr[c.p[j]]);
+            if (!(c.kd[j] & kKindPrev)) {
+                c.rq[j] = ldcg(&s.req[c.so[j]]);
+                c.old |= 1u << j;
+            }
+        }
+    }
+    c.vals = true;
+}
+
+// Required time of the net (Section II-B: min over its sinks of the sink's
+// required time minus its Elmore delay) and the sinks' required times and
+// slacks, on a group of kBwLanes lanes.  Every lane of the warp calls this.
+// COH: required times of sink cells were written by other blocks of the same
+// launch.
+template <typename R, bool COH>
+__device__ __forceinline__ void bwd_small_net(State<R> &s, const SinkPre<R> &c, int lane) {
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    A m = AC::pinf(), ad = AC::pinf();
+    if (c.a >= 0) ad = c.vals ? c.ad : ldg(&s.arr[c.a]);
+    if (c.a >= 0) {
+        A rq[kBwPerLane], ap[kBwPerLane];
+        R tp[kBwPerLane];
+#pragma unroll
+        for (int j = 0; j < kBwPerLane; ++j) {  // loads
+            if (c.p[j] < 0) continue;
+            tp[j] = c.vals ? c.tp[j] : ldg(&s.tnet[c.p[j]]);
+            if ((c.kd[j] & kKindMask) == PK_ENDPOINT) {
+                rq[j] = acc_from_double<R>(*s.T);
+            } else {
+                rq[j] = (c.old >> j) & 1u ? c.rq[j] : ldd<COH>(&s.req[c.so[j]]);
+                rq[j] = AC::add(rq[j], -(c.vals ? c.dn[j] : ldg(&s.dnet[c.sn[j]])));
+                ap[j] = c.vals ? c.ap[j] : ldg(&s.arr[c.p[j]]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBwPerLane; ++j) {  // stores
+            if (c.p[j] < 0) continue;
+            if ((c.kd[j] & kKindMask) == PK_ENDPOINT) {
+                ap[j] = AC::add(ad, tp[j]);
+                s.arr[c.p[j]] = ap[j];
+            }
+            s.req[c.p[j]] = rq[j];
+            s.slack[c.p[j]] = AC::diff(rq[j], ap[j]);
+            const A cand = AC::add(rq[j], -tp[j]);
+            if (AC::lt(cand, m)) m = cand;
+        }
+    }
+#pragma unroll
+    for (int o = kBwLanes / 2; o > 0; o >>= 1) {  // min is exact: any order gives the same value
+        const A other = shfl_x(m, o);
+        if (AC::lt(other, m)) m = other;
+    }
+    if (c.a >= 0 && (lane & (kBwLanes - 1)) == 0) {
+        s.req[c.a] = m;
+        s.slack[c.a] = AC::diff(m, ad);
+    }
+}
+
+template <typename R, bool COH>
+__device__ __forceinline__ void bwd_small(const Topo &t, State<R> &s, int i, int lane) {
+    SinkPre<R> c;
+    sink_topo(t, i, lane & (kBwLanes - 1), c);
+    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
+    bwd_small_net<R, COH>(s, c, lane);
+}
+
+constexpr int kBwNetsPerWarp = 32 / kBwLanes;
 
 // One warp-wide task w of a backward level: w < 8 ns is a chunk of
 // kBwNetsPerWarp small nets of the level's ns groups of 32 (from group s_lo);
@@ -658,13 +784,13 @@ __device__ __forceinline__ void bwd_task(const Topo &t, State<R> &s, int w, int 
     using A = typename AC::T;
     const int n_small = ns * (32 / kBwNetsPerWarp);
     if (w < n_small) {
-        bwd_small<R, COH>(t, s, s_lo * 32 + w * kBwNetsPerWarp + lane / kBwSmallFanout, lane);
+        bwd_small<R, COH>(t, s, s_lo * 32 + w * kBwNetsPerWarp + lane / kBwLanes, lane);
         return;
     }
     const BwTask task = t.bw_task[b_lo + (w - n_small)];
     const int a = task.drv;
     A ad;
-    A m = net_sinks_req<R, kPre, COH>(t, s, task.p0 + lane, task.p1, 32, a, ad);
+    A m = net_sinks_req<R, 2, COH>(t, s, task.p0 + lane, task.p1, 32, a, ad);
     for (int o = 16; o > 0; o >>= 1) {
         const A other = shfl_x(m, o);
         if (AC::lt(other, m)) m = other;
@@ -766,19 +892,41 @@ __global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
 }
 
 // The whole backward sweep and WNS / TNS in one cooperative launch: levels
-// from the deepest down to the startpoints' nets, tasks of a level spread
-// over all warps, a grid-wide barrier after each level.
+// from the deepest down to the startpoints' nets, a level's warp tasks on
+// block j mod gridDim, a grid-wide barrier after each level.  A warp carries
+// its first small-net task of the next two levels: between its arrival at
+// the barrier that closes level l and the wait, it loads the final values of
+// its level l - 1 task and the topology of its level l - 2 task.
 template <typename R>
-__global__ void __launch_bounds__(kPsThreads, kBwdBlocksPerSM) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
+    const int lane = threadIdx.x & 31, gl = lane & (kBwLanes - 1);
     const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // task j on block j mod gridDim
     const int wstride = (blockDim.x >> 5) * gridDim.x;
+    auto slot_of = [&](int l) {  // this lane's small-net slot in task w0 of level l, or -1
+        if (l < 0) return -1;
+        const int4 q = ldg(&t.bw_lv[l]);
+        return w0 < q.y * (32 / kBwNetsPerWarp) ? q.x * 32 + w0 * kBwNetsPerWarp + lane / kBwLanes : -1;
+    };
+    SinkPre<R> cur, nxt;
+    sink_topo(t, slot_of(t.depth), gl, cur);
+    sink_vals(s, cur);
+    sink_topo(t, slot_of(t.depth - 1), gl, nxt);
     unsigned n = 0;
     for (int l = t.depth; l >= 0; --l) {
         const int4 q = ldg(&t.bw_lv[l]);  // small groups (first, count), pieces (first, count)
         const int nt = bwd_tasks(q.y, q.w);
-        for (int w = w0; w < nt; w += wstride) bwd_task<R, true>(t, s, w, q.x, q.y, q.z, lane);
-        if (!grid_sync(gs, (++n) * gridDim.x)) return;
+        if (w0 < nt) {
+            if (w0 < q.y * (32 / kBwNetsPerWarp)) bwd_small_net<R, true>(s, cur, lane);
+            else bwd_task<R, true>(t, s, w0, q.x, q.y, q.z, lane);
+            for (int w = w0 + wstride; w < nt; w += wstride) bwd_task<R, true>(t, s, w, q.x, q.y, q.z, lane);
+        }
+        grid_arrive(gs);
+        if (l > 0) {
+            cur = nxt;
+            sink_vals(s, cur);  // required times of levels above l are final
+            sink_topo(t, slot_of(l - 2), gl, nxt);
+        }
+        if (!grid_wait(gs, (++n) * gridDim.x)) return;
     }
     wns_tns_blocks<R, true>(t, s);
 }
@@ -838,12 +986,12 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
 // Blocks of a cooperative launch of `kernel` that are resident at once (at
 // most kCoopMaxBlocks), cached per kernel; 0 if none.
 template <typename K>
-static int coop_grid(tdp_graph *g, K kernel) {
+static int coop_grid(tdp_graph *g, K kernel, int threads) {
     const void *key = reinterpret_cast<const void *>(kernel);
     for (auto &pr : g->coop_grid)
         if (pr.first == key) return pr.second;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kPsThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess) {
         cudaGetLastError();
         nb = 0;
     }
@@ -854,7 +1002,7 @@ static int coop_grid(tdp_graph *g, K kernel) {
 
 template <typename R>
 static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, GridSync), int grid,
-                               KernelId id) {
+                               int threads, KernelId id) {
     State<R> &s = state<R>(g);
     GridSync gs;
     gs.count = s.gsync;
@@ -862,7 +1010,7 @@ static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, Grid
     gs.timeout_ns = kSyncTimeoutNs;
     LaunchScope ls(g, id);
     TDP_CUDA(cudaMemsetAsync(s.gsync, 0, sizeof(unsigned), g->stream));
-    TDP_CUDA(launch_coop(kernel, grid, kPsThreads, g->stream, g->topo, s, gs));
+    TDP_CUDA(launch_coop(kernel, grid, threads, g->stream, g->topo, s, gs));
     return TDP_OK;
 }
 
@@ -883,8 +1031,8 @@ tdp_status forward_lists(tdp_graph *g) {
             case 15: kernel = k_fwd_sweep<R, 15>; break;
             default: kernel = k_fwd_sweep<R, 31>; break;
         }
-        const int grid = coop_grid(g, kernel);
-        if (grid > 0) return launch_sweep<R>(g, kernel, grid, KID_FWD_SWEEP);
+        const int grid = coop_grid(g, kernel, kFwdThreads);
+        if (grid > 0) return launch_sweep<R>(g, kernel, grid, kFwdThreads, KID_FWD_SWEEP);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
@@ -902,8 +1050,8 @@ tdp_status forward_lists(tdp_graph *g) {
 template <typename R>
 static tdp_status backward(tdp_graph *g) {
     if (g->single_launch) {
-        const int grid = coop_grid(g, k_bwd_sweep<R>);
-        if (grid > 0) return launch_sweep<R>(g, k_bwd_sweep<R>, grid, KID_BWD_SWEEP);
+        const int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
+        if (grid > 0) return launch_sweep<R>(g, k_bwd_sweep<R>, grid, kBwdThreads, KID_BWD_SWEEP);
         g->single_launch = false;
     }
     if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
