@@ -70,6 +70,13 @@ def reduce_max(value: float, world: int, device) -> float:
     return float(t.item())
 
 
+def aggregate(ms_local: float, steps: int, world: int, device) -> tuple:
+    """Slowest rank's time for `steps` steps, and whole-job iterations / s
+    (every rank runs its own replica of the workload)."""
+    ms = reduce_max(ms_local, world, device)
+    return ms, world * steps / (ms / 1000.0)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -148,7 +155,14 @@ LAUNCH_UNIT = {"fwd_sweep": "one forward level sweep (graph replay: one kernel p
 # DRAM bytes (read + write) per launch from an ncu capture of the 1.2M-cell
 # workload, with the SHA-256 of the kernel source they were taken on; the
 # figure is reported only while that source is unchanged.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    "fwd_sweep": {"bytes": 479974144, "source": "paper_2503_11674_b300/csrc/tdp_sta.cu",
+                  "sha256": "0c27149f8e7a6498a9eea4579eef930329ba8079a95c51348163e4ef8a56f78b",
+                  "profile": "profiles/fwd_sweep_1.2M.md"},
+    "bwd_sweep": {"bytes": 519554816, "source": "paper_2503_11674_b300/csrc/tdp_sta.cu",
+                  "sha256": "0c27149f8e7a6498a9eea4579eef930329ba8079a95c51348163e4ef8a56f78b",
+                  "profile": "profiles/bwd_sweep_1.2M.md"},
+}
 
 
 def profiled_traffic(kernel: str):
@@ -303,8 +317,7 @@ def run_ours(args):
     clk = clocks.stop()
     prof_n, prof_ms = G.tdp_profile_read()
     G.tdp_profile_kernel(None)
-    ms = reduce_max(ms_local, world, dev)
-    value = world * args.steps / (ms / 1000.0)
+    ms, value = aggregate(ms_local, args.steps, world, dev)
     n_pairs = G.attraction_get_pairs()[0].numel()
     info["pairs"] = n_pairs
     wns, tns = G.sta_propagate(xs[0], ys[0], T)

@@ -280,6 +280,19 @@ TDP_API tdp_status tdp_get_launch_count(tdp_graph *g, int64_t *n_out);
 TDP_API tdp_status tdp_profile_kernel(tdp_graph *g, const char *kernel_name);
 TDP_API tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, double *total_ms_out);
 
+/*
+ * tdp_selftest_grid_wait: test hook of the bounded grid-wide wait that the
+ * single-launch level sweeps use between levels (the paper has no
+ * counterpart).  Launches, on the current device and the legacy default
+ * stream, a cooperative kernel of two blocks whose barrier waits for one
+ * more arrival than there are blocks, so that the wait must give up after
+ * timeout_ms; synchronises, and sets *gave_up_out to 1 if the kernel
+ * recorded the timeout status, else 0.  Allocates and frees 8 bytes of
+ * device memory.  Errors: TDP_ERR_INVALID (NULL output, timeout_ms not in
+ * (0, 1000]), TDP_ERR_CUDA.
+ */
+TDP_API tdp_status tdp_selftest_grid_wait(double timeout_ms, int32_t *gave_up_out);
+
 /* Message for the last non-OK status returned on this host thread. */
 TDP_API const char *tdp_last_error(void);
 

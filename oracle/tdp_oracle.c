@@ -21,8 +21,8 @@
  *   or_loss         Eq. (9) quadratic pin-to-pin loss Q(i,j), and the PP sum
  *                   of Section III-D, with its analytic gradient.
  *
- * Readings where the paper is silent (delay model, ties, endpoints) follow
- * the design notes of this repository: single corner, late only, ideal clock
+ * Where the paper is silent (delay model, ties, endpoints) this file reads
+ * it as follows: single corner, late only, ideal clock
  * at t = 0, setup time 0; cell delay d = d0 + R_drv * C_load applies to every
  * input arc of the cell and is the clock-to-Q / launch delay of flip-flops and
  * primary inputs; argmax ties go to the lowest pin index; equal-slack paths

@@ -22,7 +22,7 @@ EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_g
            "attraction_update_pairs", "attraction_reset_pairs", "attraction_set_pairs",
            "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
            "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
-           "tdp_profile_kernel", "tdp_profile_read", "tdp_last_error"]
+           "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "tdp_last_error"]
 
 
 class NetlistDesc(C.Structure):
@@ -72,6 +72,7 @@ def load() -> C.CDLL:
         "tdp_get_launch_count": [P, P],
         "tdp_profile_kernel": [P, C.c_char_p],
         "tdp_profile_read": [P, P, P],
+        "tdp_selftest_grid_wait": [C.c_double, P],
         "tdp_last_error": [],
     }
     for name, args in sig.items():

@@ -1176,3 +1176,33 @@ extern "C" tdp_status sta_get_net_delays(tdp_graph *g, void *tnet_dev, void *clo
                ? get_net_delays_impl<float>(g, (float *)tnet_dev, (float *)cload_dev, (float *)dcell_dev)
                : get_net_delays_impl<double>(g, (double *)tnet_dev, (double *)cload_dev, (double *)dcell_dev);
 }
+
+namespace tdp {
+// every block waits for one more arrival than there are blocks
+__global__ void k_wait_selftest(GridSync gs) { grid_sync(gs, gridDim.x + 1u); }
+}  // namespace tdp
+
+extern "C" tdp_status tdp_selftest_grid_wait(double timeout_ms, int32_t *gave_up_out) {
+    if (!gave_up_out || !(timeout_ms > 0.0 && timeout_ms <= 1000.0)) {
+        set_error("tdp_selftest_grid_wait: NULL output or timeout_ms outside (0, 1000]");
+        return TDP_ERR_INVALID;
+    }
+    unsigned *w = nullptr;
+    TDP_CUDA(cudaMalloc(&w, 2 * sizeof(unsigned)));
+    GridSync gs;
+    gs.count = w;
+    gs.status = w + 1;
+    gs.timeout_ns = (unsigned long long)(timeout_ms * 1e6);
+    unsigned h[2] = {0u, 0u};
+    cudaError_t e = cudaMemset(w, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = launch_coop(k_wait_selftest, 2, 32, (cudaStream_t)0, gs);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(w);
+    if (e != cudaSuccess) {
+        set_error("tdp_selftest_grid_wait: %s", cudaGetErrorString(e));
+        return TDP_ERR_CUDA;
+    }
+    *gave_up_out = h[1] != 0u ? 1 : 0;
+    return TDP_OK;
+}

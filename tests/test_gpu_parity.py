@@ -409,3 +409,21 @@ def test_out_of_order_calls_return_state_errors():
         G.attraction_set_pairs(np.array([0], np.int32), np.array([1.0]))  # pin 0 is a driver
     assert ei.value.status == _abi.TDP_ERR_INVALID
 
+
+
+def test_grid_wait_gives_up_and_device_stays_usable():
+    """The grid-wide wait of the single-launch sweeps is bounded: a barrier
+    that can never complete records the timeout status and the kernel returns,
+    leaving the context usable."""
+    import ctypes as C
+    from paper_2503_11674_b300 import _abi
+    lib = _abi.load()
+    gave_up = C.c_int32(-1)
+    _abi.check("tdp_selftest_grid_wait", lib.tdp_selftest_grid_wait(2.0, C.addressof(gave_up)))
+    assert gave_up.value == 1
+    nl = netgen.generate("tiny", 3)
+    T = oracle.clock_period(nl, 0.9)
+    G = _graph(nl, "fp32")
+    x, y = _pos(nl, G.dtype)
+    G.sta_propagate(x, y, T)
+    check_sta(G, oracle.sta(nl, nl.x, nl.y, T), T, TOL32)
