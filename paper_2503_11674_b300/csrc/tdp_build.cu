@@ -84,9 +84,7 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_CUDA(cudaMemset(s.w, 0, sizeof(R) * t.n_pins));
     TDP_CUDA(cudaMemset(s.n_pairs, 0, sizeof(long long)));
     // backward sweep: partial minima of split nets and their counters
-    TDP_TRY(dalloc(g, &s.bw_part, std::max(t.n_bw_slots, 1)));
-    TDP_TRY(dalloc(g, &s.bw_cnt, std::max(t.n_bw_split, 1)));
-    TDP_CUDA(cudaMemset(s.bw_cnt, 0, sizeof(unsigned long long) * std::max(t.n_bw_split, 1)));
+    TDP_TRY(dalloc(g, &s.reqkey, t.n_nets));
     // loss
     TDP_TRY(dalloc(g, &s.gslot, 2 * (size_t)t.n_pins));
     TDP_TRY(dalloc(g, &s.loss_part, 1024));
@@ -306,64 +304,75 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             bl_net[small ? fs[l]++ : fb[l]++] = e;
         }
     }
-    // backward tasks per level: groups of 32 nets of at most kBwSmallFanout
-    // sinks (lane l of group q handles the net whose driver is bw_sa[32q + l]
-    // and whose pins end at bw_sb[32q + l]; -1 pads), and pieces of
-    // kBwPart sinks of the larger nets
-    std::vector<BwTask> bw;
-    std::vector<int32_t> bw_sa, bw_sb;
-    std::vector<int4> bw_slot;  // kBwSmallFanout per small-net slot
-    auto push_slots = [&](int a, int b) {
-        for (int gl = 0; gl < kBwSmallFanout; ++gl) {
-            const int p = a < 0 ? -1 : a + 1 + gl;
-            if (p < 0 || p >= b) {
-                bw_slot.push_back(make_int4(-1, 0, 0, 0));
-                continue;
-            }
-            int fl = kind[p];
-            if (kind[p] == PK_COMB_IN && level[d->pin_cell[p]] == net_level[pin_net[p]] + 1) fl |= kKindPrev;
-            bw_slot.push_back(make_int4(p, fl, sink_out[p], sink_onet[p]));
-        }
+    // backward warp tasks per level, deepest level first: tasks of
+    // kBwNetsPerTask small nets (at most kBwSmallFanout sinks; kBwLanes lanes
+    // a net, sinks j and j + kBwLanes of the net on its lane j), then pieces
+    // of kBwPiece sinks of the larger nets (sinks l and l + 32 of the piece on
+    // lane l).  Per task and lane: the net's driver pin (kBwSplit set when the
+    // net has several pieces; -1: none) and the net; per task and lane,
+    // kBwPerLane sink slots (pin, kind | kKindPrev, net driven by the sink's
+    // cell; pin -1: none).
+    std::vector<int2> bw_drv;
+    std::vector<int4> bw_slot;
+    const int4 no_slot = make_int4(-1, 0, 0, 0);
+    auto slot_of = [&](int p) {
+        int fl = kind[p];
+        if (kind[p] == PK_COMB_IN && level[d->pin_cell[p]] == net_level[pin_net[p]] + 1) fl |= kKindPrev;
+        return make_int4(p, fl, sink_onet[p], 0);
     };
-    int n_slots = 0, n_split = 0;
-    std::vector<int32_t> s_lo(D + 1), s_n(D + 1), b_lo(D + 1), b_n(D + 1);
+    std::vector<int4> bw_lv(D + 1);  // (first task, small-net tasks, piece tasks, 0)
+    int n_tasks = 0;
     for (int l = D; l >= 0; --l) {
-        s_lo[l] = (int32_t)(bw_sa.size() / 32);
-        b_lo[l] = (int32_t)bw.size();
+        const int first = n_tasks;
+        std::vector<int32_t> small, large;
         for (int q = bl_ptr[l]; q < bl_ptr[l + 1]; ++q) {
             const int e = bl_net[q];
+            (d->net_ptr[e + 1] - d->net_ptr[e] - 1 <= kBwSmallFanout ? small : large).push_back(e);
+        }
+        for (size_t i0 = 0; i0 < small.size(); i0 += kBwNetsPerTask, ++n_tasks) {
+            for (int ln = 0; ln < 32; ++ln) {
+                const size_t i = i0 + ln / kBwLanes;
+                if (i >= small.size()) {
+                    bw_drv.push_back(make_int2(-1, -1));
+                    for (int j = 0; j < kBwPerLane; ++j) bw_slot.push_back(no_slot);
+                    continue;
+                }
+                const int e = small[i], a = d->net_ptr[e], b = d->net_ptr[e + 1];
+                bw_drv.push_back(make_int2(a, e));
+                for (int j = 0; j < kBwPerLane; ++j) {
+                    const int p = a + 1 + ln % kBwLanes + j * kBwLanes;
+                    bw_slot.push_back(p < b ? slot_of(p) : no_slot);
+                }
+            }
+        }
+        const int n_small_tasks = n_tasks - first;
+        for (int e : large) {
             const int a = d->net_ptr[e], b = d->net_ptr[e + 1];
-            const int f = b - a - 1;
-            if (f <= kBwSmallFanout) {
-                bw_sa.push_back(a);
-                bw_sb.push_back(b);
-                push_slots(a, b);
-                continue;
+            const int parts = (b - a - 1 + kBwPiece - 1) / kBwPiece;
+            for (int j = 0; j < parts; ++j, ++n_tasks) {
+                const int p0 = a + 1 + j * kBwPiece, p1 = std::min(b, p0 + kBwPiece);
+                for (int ln = 0; ln < 32; ++ln) {
+                    bw_drv.push_back(make_int2(a | (parts > 1 ? kBwSplit : 0), e));
+                    for (int jj = 0; jj < kBwPerLane; ++jj) {
+                        const int p = p0 + ln + jj * 32;
+                        bw_slot.push_back(p < p1 ? slot_of(p) : no_slot);
+                    }
+                }
             }
-            const int parts = (f + kBwPart - 1) / kBwPart;
-            const int cnt = parts > 1 ? n_split++ : -1;
-            for (int j = 0; j < parts; ++j) {
-                const int p0 = a + 1 + j * kBwPart;
-                const int p1 = std::min(b, p0 + kBwPart);
-                bw.push_back(BwTask{a, p0, p1, parts > 1 ? n_slots + j : -1, parts, cnt, j, 0});
-            }
-            if (parts > 1) n_slots += parts;
         }
-        while (bw_sa.size() % 32) {
-            bw_sa.push_back(-1);
-            bw_sb.push_back(-1);
-            push_slots(-1, -1);
-        }
-        s_n[l] = (int32_t)(bw_sa.size() / 32) - s_lo[l];
-        b_n[l] = (int32_t)bw.size() - b_lo[l];
+        bw_lv[l] = make_int4(first, n_small_tasks, n_tasks - first - n_small_tasks, 0);
     }
-    t.n_bw_tasks = (int32_t)bw.size();
-    t.n_bw_slots = n_slots;
-    t.n_bw_split = n_split;
-    TDP_TRY(upload(g, &t.bw_task, bw));
-    TDP_TRY(upload(g, &t.bw_sa, bw_sa));
-    TDP_TRY(upload(g, &t.bw_sb, bw_sb));
+    t.n_bw_tasks = n_tasks;
+    TDP_TRY(upload(g, &t.bw_drv, bw_drv));
     TDP_TRY(upload(g, &t.bw_slot, bw_slot));
+    TDP_TRY(upload(g, &t.bw_lv, bw_lv));
+    std::vector<int32_t> s_lo(D + 1), s_n(D + 1), b_lo(D + 1), b_n(D + 1);
+    for (int l = 0; l <= D; ++l) {
+        s_lo[l] = bw_lv[l].x;
+        s_n[l] = bw_lv[l].y;
+        b_lo[l] = bw_lv[l].x + bw_lv[l].y;
+        b_n[l] = bw_lv[l].z;
+    }
     t.n_cells = nc;
     t.n_pins = np;
     t.n_nets = nn;
@@ -377,12 +386,7 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     g->lv.bw_s_n = s_n;
     g->lv.bw_b_lo = b_lo;
     g->lv.bw_b_n = b_n;
-    {
-        std::vector<int4> bw_lv(D + 1);
-        for (int l = 0; l <= D; ++l) bw_lv[l] = make_int4(s_lo[l], s_n[l], b_lo[l], b_n[l]);
-        TDP_TRY(upload(g, &t.bw_lv, bw_lv));
-        TDP_TRY(upload(g, &t.lvl_ptr, lvl_ptr));
-    }
+    TDP_TRY(upload(g, &t.lvl_ptr, lvl_ptr));
     std::vector<int32_t> pc(d->pin_cell, d->pin_cell + np), nptr(d->net_ptr, d->net_ptr + nn + 1);
     std::vector<uint8_t> fixed(d->cell_fixed, d->cell_fixed + nc);
     TDP_TRY(upload(g, &t.pin_cell, pc));

@@ -278,15 +278,15 @@ inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, cu
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// One warp's piece of a net with more than kBwSmallFanout sinks in the
-// backward sweep: sinks [p0, p1) of the net driven by pin drv.  When the net
-// is split into nparts pieces, piece `part` writes its minimum to `slot` and
-// the last piece to finish (counter `cnt`) combines the slots.
-struct BwTask {
-    int32_t drv, p0, p1, slot, nparts, cnt, part, pad;
-};
-constexpr int kBwSmallFanout = 8;    // nets up to this fanout are handled one per lane
-constexpr int kBwPart = 128;         // sinks per warp task of a larger net
+// Backward sweep work: a warp task is either kBwNetsPerTask nets of at most
+// kBwSmallFanout sinks (kBwLanes lanes a net) or a piece of kBwPiece sinks of
+// a larger net; either way a lane holds kBwPerLane sinks.
+constexpr int kBwSmallFanout = 8;
+constexpr int kBwLanes = 4;
+constexpr int kBwPerLane = kBwSmallFanout / kBwLanes;
+constexpr int kBwNetsPerTask = 32 / kBwLanes;
+constexpr int kBwPiece = 32 * kBwPerLane;
+constexpr int kBwSplit = 1 << 30;  // on a task's driver pin: the net has several pieces
 
 // ------------------------------------------------------------ the graph ---
 // Device arrays common to both precisions (topology, built once).
@@ -317,17 +317,15 @@ struct Topo {
     int32_t *cp = nullptr;         // [n_pins]
     int32_t *slot_of_pin = nullptr;// [n_pins] position of a pin in cp
     uint8_t *cell_fixed = nullptr; // [n_cells]
-    // backward sweep, highest level first: groups of 32 small nets given by
-    // driver pin / end pin per lane (-1 pads), and pieces of larger nets
-    int32_t *bw_sa = nullptr, *bw_sb = nullptr;
-    // per small-net slot, kBwSmallFanout sink slots (pin, kind | kKindPrev,
-    // its cell's output pin, net driven by its cell; pin -1: none)
-    int4 *bw_slot = nullptr;
-    BwTask *bw_task = nullptr;
-    int32_t n_bw_tasks = 0, n_bw_slots = 0, n_bw_split = 0;
+    // backward sweep warp tasks, deepest level first: per task and lane the
+    // net's driver pin (| kBwSplit) and the net, and kBwPerLane sink slots
+    // (pin, kind | kKindPrev, net driven by the sink's cell; pin -1: none)
+    int2 *bw_drv = nullptr;  // [n_bw_tasks * 32]
+    int4 *bw_slot = nullptr; // [n_bw_tasks * 32 * kBwPerLane]
+    int32_t n_bw_tasks = 0;
     // device copies of the level structure for the single-launch sweeps:
-    // lvl_ptr [depth+1] as in Levels, bw_lv [depth+1] = (small-group first,
-    // count, piece first, count) of each level
+    // lvl_ptr [depth+1] as in Levels, bw_lv [depth+1] = (first task,
+    // small-net tasks, piece tasks, 0) of each level
     int32_t *lvl_ptr = nullptr;
     int4 *bw_lv = nullptr;
 };
@@ -335,8 +333,8 @@ struct Topo {
 // Host copies of the launch structure of the level sweeps.
 struct Levels {
     std::vector<int32_t> lvl_ptr;   // comb cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
-    // backward sweep of level l: small-net groups [bw_s_lo[l], +bw_s_n[l]),
-    // pieces of larger nets [bw_b_lo[l], +bw_b_n[l])
+    // backward sweep of level l: small-net tasks [bw_s_lo[l], +bw_s_n[l]),
+    // then pieces of larger nets [bw_b_lo[l], +bw_b_n[l])
     std::vector<int32_t> bw_s_lo, bw_s_n, bw_b_lo, bw_b_n;
 };
 
@@ -357,8 +355,9 @@ struct State {
     double *wns_tns = nullptr;    // [2]
     double *red_part = nullptr;   // [2 * chunks] WNS / TNS partials per kRedChunk endpoints
     unsigned *red_count = nullptr;
-    A *bw_part = nullptr;         // [n_bw_slots] partial minima of split nets
-    unsigned long long *bw_cnt = nullptr;  // [n_bw_split] finished parts (monotone)
+    // [n_nets] required time of each net's driver during the backward sweep,
+    // as an order-preserving integer key (pieces of a net combine by atomicMin)
+    unsigned long long *reqkey = nullptr;
     // extraction
     uint64_t *sort_a = nullptr, *sort_b = nullptr;  // (key, pin) items, ping-pong
     int32_t *nviol = nullptr;     // device count of failing endpoints

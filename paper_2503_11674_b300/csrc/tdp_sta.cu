@@ -585,110 +585,69 @@ __device__ __forceinline__ fx2 shfl_x(fx2 v, int o) {
     return fx2{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
-// req / slack of the sinks first, first+step, ... < b of the net driven by
-// pin a, NP sinks per round of loads; returns min over them of req(s) - t(s)
-// and the driver's arrival in ad.  The first round's topology loads are
-// issued before pdl_wait() (level launches); COH: required times of sink
-// cells were written by other blocks of the same launch.
-template <typename R, int NP, bool COH>
-__device__ __forceinline__ typename Acc<R>::T net_sinks_req(const Topo &t, State<R> &s, int first,
-                                                            int b, int step, int a,
-                                                            typename Acc<R>::T &ad) {
-    using AC = Acc<R>;
-    using A = typename AC::T;
-    A m = AC::pinf();
-    uint8_t kd[NP];
-    int so[NP], sn[NP];
-    auto topo_loads = [&](int p0) {
-#pragma unroll
-        for (int u = 0; u < NP; ++u) {
-            const int p = p0 + u * step;
-            if (p < b) {
-                kd[u] = ldg(&t.pin_kind[p]);
-                so[u] = ldg(&t.sink_out[p]);
-                sn[u] = ldg(&t.sink_onet[p]);
-            }
-        }
-    };
-    topo_loads(first);
-    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
-    ad = ldg(&s.arr[a]);
-    const A Tacc = acc_from_double<R>(*s.T);
-    for (int p0 = first; p0 < b; p0 += NP * step) {
-        if (p0 != first) topo_loads(p0);
-        R tp[NP];
-#pragma unroll
-        for (int u = 0; u < NP; ++u) {
-            const int p = p0 + u * step;
-            if (p < b) tp[u] = ldg(&s.tnet[p]);
-        }
-        A rq[NP], ap[NP];
-#pragma unroll
-        for (int u = 0; u < NP; ++u) {
-            const int p = p0 + u * step;
-            if (p < b) {
-                if (kd[u] == PK_ENDPOINT) {
-                    ap[u] = AC::add(ad, tp[u]);
-                    rq[u] = Tacc;
-                } else {
-                    rq[u] = AC::add(ldd<COH>(&s.req[so[u]]), -ldg(&s.dnet[sn[u]]));
-                    ap[u] = ldg(&s.arr[p]);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < NP; ++u) {
-            const int p = p0 + u * step;
-            if (p < b) {
-                if (kd[u] == PK_ENDPOINT) s.arr[p] = ap[u];
-                s.req[p] = rq[u];
-                s.slack[p] = AC::diff(rq[u], ap[u]);
-                const A cand = AC::add(rq[u], -tp[u]);
-                if (AC::lt(cand, m)) m = cand;
-            }
-        }
-    }
-    return m;
+// A net's required time travels as an order-preserving 64-bit key, so that
+// the pieces of a large net combine with one integer atomicMin (exact, and
+// independent of their order): FP32 pairs as (hi bits, lo bits), which
+// orders them as Acc<float>::lt does; FP64 as its own bits.  All ones stands
+// for +inf (a net with no sink).
+constexpr unsigned long long kKeyNone = ~0ull;
+__device__ __forceinline__ unsigned long long acc_key(fx2 v) {
+    return ((unsigned long long)ord_bits(v.hi) << 32) | ord_bits(v.lo);
+}
+__device__ __forceinline__ unsigned long long acc_key(double v) { return ord_bits(v); }
+__device__ __forceinline__ double from_ord64(uint64_t o) {
+    return (o & 0x8000000000000000ull) ? __longlong_as_double((long long)(o & 0x7fffffffffffffffull))
+                                       : __longlong_as_double((long long)~o);
+}
+template <typename R>
+__device__ __forceinline__ typename Acc<R>::T acc_unkey(unsigned long long k);
+template <>
+__device__ __forceinline__ fx2 acc_unkey<float>(unsigned long long k) {
+    if (k == kKeyNone) return Acc<float>::pinf();
+    return fx2{from_ord((uint32_t)(k >> 32)), from_ord((uint32_t)k)};
+}
+template <>
+__device__ __forceinline__ double acc_unkey<double>(unsigned long long k) {
+    if (k == kKeyNone) return Acc<double>::pinf();
+    return from_ord64(k);
 }
 
-// Small nets (at most kBwSmallFanout sinks) go kBwLanes lanes to a net,
-// kBwPerLane sinks to a lane: sinks j = gl, gl + kBwLanes, ... of the net.
-constexpr int kBwLanes = 4;
-constexpr int kBwPerLane = kBwSmallFanout / kBwLanes;
-
-// One lane's share of the net in slot i of the small-net table (i < 0 or
-// a < 0: none): the driver pin a, the lane's sinks (pin -1: none) with their
-// kind and their cell's output pin and net, and, once loaded (vals), the
-// values that stay fixed during the sweep and, for sinks whose cell is two or
-// more levels up (bit j of old), their required time.
+// One lane's share of a backward task (task w, lane): the net's driver pin a
+// (a < 0: none) and net e, whether the net is split into pieces, the lane's
+// sinks (pin -1: none) with their kind and the net their cell drives, and,
+// once loaded (vals), the values that stay fixed during the sweep and, for
+// sinks whose cell is two or more levels up (bit j of old), that cell's
+// required time.
 template <typename R>
 struct SinkPre {
     using A = typename Acc<R>::T;
-    int a;
-    int p[kBwPerLane], kd[kBwPerLane], so[kBwPerLane], sn[kBwPerLane];
+    int a, e;
+    bool split, vals;
+    int p[kBwPerLane], kd[kBwPerLane], sn[kBwPerLane];
     unsigned old;
-    bool vals;
     R tp[kBwPerLane], dn[kBwPerLane];
     A ad, ap[kBwPerLane], rq[kBwPerLane];
 };
 
-// topology: one round of loads
+// topology: one round of loads (task < 0: none)
 template <typename R>
-__device__ __forceinline__ void sink_topo(const Topo &t, int i, int gl, SinkPre<R> &c) {
-    c.vals = false;
+__device__ __forceinline__ void sink_topo(const Topo &t, int task, int lane, SinkPre<R> &c) {
+    c.vals = c.split = false;
     c.old = 0u;
     c.a = -1;
 #pragma unroll
     for (int j = 0; j < kBwPerLane; ++j) c.p[j] = -1;
-    if (i < 0) return;
-    c.a = ldg(&t.bw_sa[i]);
+    if (task < 0) return;
+    const int2 d = ldg(&t.bw_drv[(size_t)task * 32 + lane]);
+    c.a = d.x < 0 ? -1 : (d.x & ~kBwSplit);
+    c.split = d.x >= 0 && (d.x & kBwSplit);
+    c.e = d.y;
 #pragma unroll
     for (int j = 0; j < kBwPerLane; ++j) {
-        const int4 q = ldg(&t.bw_slot[(size_t)i * kBwSmallFanout + gl + j * kBwLanes]);
+        const int4 q = ldg(&t.bw_slot[((size_t)task * 32 + lane) * kBwPerLane + j]);
         c.p[j] = q.x;
         c.kd[j] = q.y;
-        c.so[j] = q.z;
-        c.sn[j] = q.w;
+        c.sn[j] = q.z;
     }
 }
 
@@ -706,7 +665,7 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
             c.dn[j] = ldg(&s.dnet[c.sn[j]]);
             c.ap[j] = ldg(&s.arr[c.p[j]]);
             if (!(c.kd[j] & kKindPrev)) {
-                c.rq[j] = ldcg(&s.req[c.so[j]]);
+                c.rq[j] = acc_unkey<R>(ldcg(&s.reqkey[c.sn[j]]));
                 c.old |= 1u << j;
             }
         }
@@ -714,18 +673,20 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
     c.vals = true;
 }
 
-// Required time of the net (Section II-B: min over its sinks of the sink's
-// required time minus its Elmore delay) and the sinks' required times and
-// slacks, on a group of kBwLanes lanes.  Every lane of the warp calls this.
-// COH: required times of sink cells were written by other blocks of the same
-// launch.
+// Required and slack times of the task's sinks, and the net's required time
+// (Section II-B: min over its sinks of the sink's required time minus its
+// Elmore delay) into reqkey (stored, or atomicMin for the pieces of a split
+// net).  PIECE: the warp holds one piece (min over 32 lanes), else
+// kBwNetsPerTask nets (min over kBwLanes lanes).  Every lane of the warp
+// calls this.  COH: required times of sink cells were written by other
+// blocks of the same launch.
 template <typename R, bool COH>
-__device__ __forceinline__ void bwd_small_net(State<R> &s, const SinkPre<R> &c, int lane) {
+__device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int lane, bool piece) {
     using AC = Acc<R>;
     using A = typename AC::T;
-    A m = AC::pinf(), ad = AC::pinf();
-    if (c.a >= 0) ad = c.vals ? c.ad : ldg(&s.arr[c.a]);
+    A m = AC::pinf();
     if (c.a >= 0) {
+        const A ad = c.vals ? c.ad : ldg(&s.arr[c.a]);
         A rq[kBwPerLane], ap[kBwPerLane];
         R tp[kBwPerLane];
 #pragma unroll
@@ -735,7 +696,7 @@ __device__ __forceinline__ void bwd_small_net(State<R> &s, const SinkPre<R> &c, 
             if ((c.kd[j] & kKindMask) == PK_ENDPOINT) {
                 rq[j] = acc_from_double<R>(*s.T);
             } else {
-                rq[j] = (c.old >> j) & 1u ? c.rq[j] : ldd<COH>(&s.req[c.so[j]]);
+                rq[j] = (c.old >> j) & 1u ? c.rq[j] : acc_unkey<R>(ldd<COH>(&s.reqkey[c.sn[j]]));
                 rq[j] = AC::add(rq[j], -(c.vals ? c.dn[j] : ldg(&s.dnet[c.sn[j]])));
                 ap[j] = c.vals ? c.ap[j] : ldg(&s.arr[c.p[j]]);
             }
@@ -753,81 +714,46 @@ __device__ __forceinline__ void bwd_small_net(State<R> &s, const SinkPre<R> &c, 
             if (AC::lt(cand, m)) m = cand;
         }
     }
-#pragma unroll
-    for (int o = kBwLanes / 2; o > 0; o >>= 1) {  // min is exact: any order gives the same value
+    // min is exact: any order gives the same value
+    for (int o = piece ? 16 : kBwLanes / 2; o > 0; o >>= 1) {
         const A other = shfl_x(m, o);
         if (AC::lt(other, m)) m = other;
     }
-    if (c.a >= 0 && (lane & (kBwLanes - 1)) == 0) {
-        s.req[c.a] = m;
-        s.slack[c.a] = AC::diff(m, ad);
+    if (c.a >= 0 && (lane & (piece ? 31 : kBwLanes - 1)) == 0) {
+        if (c.split) atomicMin(&s.reqkey[c.e], acc_key(m));
+        else s.reqkey[c.e] = acc_key(m);
     }
 }
 
+// Required time and slack of every net's driver pin, from reqkey.
 template <typename R, bool COH>
-__device__ __forceinline__ void bwd_small(const Topo &t, State<R> &s, int i, int lane) {
-    SinkPre<R> c;
-    sink_topo(t, i, lane & (kBwLanes - 1), c);
-    if constexpr (!COH) pdl_wait();  // everything below reads values earlier kernels wrote
-    bwd_small_net<R, COH>(s, c, lane);
-}
-
-constexpr int kBwNetsPerWarp = 32 / kBwLanes;
-
-// One warp-wide task w of a backward level: w < 8 ns is a chunk of
-// kBwNetsPerWarp small nets of the level's ns groups of 32 (from group s_lo);
-// after that, piece b_lo + (w - 8 ns) of a larger net (lanes stride its sinks).
-template <typename R, bool COH>
-__device__ __forceinline__ void bwd_task(const Topo &t, State<R> &s, int w, int s_lo, int ns, int b_lo,
-                                         int lane) {
+__device__ __forceinline__ void bwd_drivers(const Topo &t, State<R> &s, int i, int stride) {
     using AC = Acc<R>;
-    using A = typename AC::T;
-    const int n_small = ns * (32 / kBwNetsPerWarp);
-    if (w < n_small) {
-        bwd_small<R, COH>(t, s, s_lo * 32 + w * kBwNetsPerWarp + lane / kBwLanes, lane);
-        return;
+    for (int e = i; e < t.n_nets; e += stride) {
+        const int a = ldg(&t.net_ptr[e]);
+        const typename AC::T r = acc_unkey<R>(ldd<COH>(&s.reqkey[e]));
+        s.req[a] = r;
+        s.slack[a] = AC::diff(r, ldg(&s.arr[a]));
     }
-    const BwTask task = t.bw_task[b_lo + (w - n_small)];
-    const int a = task.drv;
-    A ad;
-    A m = net_sinks_req<R, 2, COH>(t, s, task.p0 + lane, task.p1, 32, a, ad);
-    for (int o = 16; o > 0; o >>= 1) {
-        const A other = shfl_x(m, o);
-        if (AC::lt(other, m)) m = other;
-    }
-    if (lane != 0) return;
-    if (task.nparts > 1) {
-        // several warps share this net: each leaves its minimum in a slot,
-        // and the last one to finish combines them (the counter only grows)
-        s.bw_part[task.slot] = m;
-        __threadfence();
-        const unsigned long long done = atomicAdd(&s.bw_cnt[task.cnt], 1ull) + 1ull;
-        if (done % (unsigned long long)task.nparts != 0ull) return;
-        __threadfence();
-        const int base = task.slot - task.part;
-        m = ldcg(&s.bw_part[base]);
-        for (int j = 1; j < task.nparts; ++j) {
-            const A v = ldcg(&s.bw_part[base + j]);
-            if (AC::lt(v, m)) m = v;
-        }
-    }
-    s.req[a] = m;
-    s.slack[a] = AC::diff(m, ad);
-}
-
-// warp tasks of a backward level
-__host__ __device__ __forceinline__ int bwd_tasks(int ns, int nb) {
-    return ns * (32 / kBwNetsPerWarp) + nb;
 }
 
 // One launch per level (captured in a CUDA graph): a warp per task.
 template <typename R>
-__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int s_lo, int ns,
-                                                          int b_lo, int nb) {
+__global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int first, int n_small,
+                                                          int n_piece) {
     pdl_trigger();
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (w >= bwd_tasks(ns, nb)) return;
-    bwd_task<R, false>(t, s, w, s_lo, ns, b_lo, threadIdx.x & 31);
+    if (w >= n_small + n_piece) return;
+    SinkPre<R> c;
+    sink_topo(t, first + w, threadIdx.x & 31, c);
+    pdl_wait();  // everything below reads values earlier kernels wrote
+    bwd_net<R, false>(s, c, threadIdx.x & 31, w >= n_small);
+}
+
+template <typename R>
+__global__ void k_bwd_drivers(Topo t, State<R> s) {
+    pdl_wait();
+    bwd_drivers<R, false>(t, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------- WNS / TNS ---
@@ -894,40 +820,45 @@ __global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
 // The whole backward sweep and WNS / TNS in one cooperative launch: levels
 // from the deepest down to the startpoints' nets, a level's warp tasks on
 // block j mod gridDim, a grid-wide barrier after each level.  A warp carries
-// its first small-net task of the next two levels: between its arrival at
-// the barrier that closes level l and the wait, it loads the final values of
-// its level l - 1 task and the topology of its level l - 2 task.
+// its first task of the next two levels: between its arrival at the barrier
+// that closes level l and the wait, it loads the final values of its level
+// l - 1 task and the topology of its level l - 2 task.  After the last
+// level, the driver pins' required times and slacks, and WNS / TNS.
 template <typename R>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
-    const int lane = threadIdx.x & 31, gl = lane & (kBwLanes - 1);
+    const int lane = threadIdx.x & 31;
     const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // task j on block j mod gridDim
     const int wstride = (blockDim.x >> 5) * gridDim.x;
-    auto slot_of = [&](int l) {  // this lane's small-net slot in task w0 of level l, or -1
+    auto task_of = [&](int l) {  // task w0 of level l, or -1
         if (l < 0) return -1;
         const int4 q = ldg(&t.bw_lv[l]);
-        return w0 < q.y * (32 / kBwNetsPerWarp) ? q.x * 32 + w0 * kBwNetsPerWarp + lane / kBwLanes : -1;
+        return w0 < q.y + q.z ? q.x + w0 : -1;
     };
     SinkPre<R> cur, nxt;
-    sink_topo(t, slot_of(t.depth), gl, cur);
+    sink_topo(t, task_of(t.depth), lane, cur);
     sink_vals(s, cur);
-    sink_topo(t, slot_of(t.depth - 1), gl, nxt);
+    sink_topo(t, task_of(t.depth - 1), lane, nxt);
     unsigned n = 0;
     for (int l = t.depth; l >= 0; --l) {
-        const int4 q = ldg(&t.bw_lv[l]);  // small groups (first, count), pieces (first, count)
-        const int nt = bwd_tasks(q.y, q.w);
+        const int4 q = ldg(&t.bw_lv[l]);  // (first task, small-net tasks, piece tasks)
+        const int nt = q.y + q.z;
         if (w0 < nt) {
-            if (w0 < q.y * (32 / kBwNetsPerWarp)) bwd_small_net<R, true>(s, cur, lane);
-            else bwd_task<R, true>(t, s, w0, q.x, q.y, q.z, lane);
-            for (int w = w0 + wstride; w < nt; w += wstride) bwd_task<R, true>(t, s, w, q.x, q.y, q.z, lane);
+            bwd_net<R, true>(s, cur, lane, w0 >= q.y);
+            for (int w = w0 + wstride; w < nt; w += wstride) {
+                SinkPre<R> c;
+                sink_topo(t, q.x + w, lane, c);
+                bwd_net<R, true>(s, c, lane, w >= q.y);
+            }
         }
         grid_arrive(gs);
         if (l > 0) {
             cur = nxt;
             sink_vals(s, cur);  // required times of levels above l are final
-            sink_topo(t, slot_of(l - 2), gl, nxt);
+            sink_topo(t, task_of(l - 2), lane, nxt);
         }
         if (!grid_wait(gs, (++n) * gridDim.x)) return;
     }
+    bwd_drivers<R, true>(t, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
     wns_tns_blocks<R, true>(t, s);
 }
 
@@ -950,18 +881,20 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
         }
         ok = cudaGetLastError() == cudaSuccess;
     }
+    if (bwd) ok = cudaMemsetAsync(s.reqkey, 0xff, sizeof(unsigned long long) * t.n_nets, cs) == cudaSuccess;
     for (int l = t.depth; bwd && l >= 0 && ok; --l) {
         const int ns = g->lv.bw_s_n[l], nb = g->lv.bw_b_n[l];
         if (ns + nb > 0) {
-            launch_pdl(k_bwd_level<R>, div_up((int64_t)bwd_tasks(ns, nb) * 32, kLvThreads), kLvThreads, cs, t, s,
-                       g->lv.bw_s_lo[l], ns, g->lv.bw_b_lo[l], nb);
+            launch_pdl(k_bwd_level<R>, div_up((int64_t)(ns + nb) * 32, kLvThreads), kLvThreads, cs, t, s,
+                       g->lv.bw_s_lo[l], ns, nb);
             ++nk;
         }
         ok = cudaGetLastError() == cudaSuccess;
     }
     if (bwd && ok) {
+        launch_pdl(k_bwd_drivers<R>, 4 * 148, 256, cs, t, s);
         launch_pdl(k_wns_tns<R>, kRedBlocks, kRedThreads, cs, t, s);
-        ++nk;
+        nk += 2;
         ok = cudaGetLastError() == cudaSuccess;
     }
     cudaGraph_t graph = nullptr;
@@ -1051,7 +984,11 @@ template <typename R>
 static tdp_status backward(tdp_graph *g) {
     if (g->single_launch) {
         const int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
-        if (grid > 0) return launch_sweep<R>(g, k_bwd_sweep<R>, grid, kBwdThreads, KID_BWD_SWEEP);
+        if (grid > 0) {
+            State<R> &s = state<R>(g);
+            TDP_CUDA(cudaMemsetAsync(s.reqkey, 0xff, sizeof(unsigned long long) * g->topo.n_nets, g->stream));
+            return launch_sweep<R>(g, k_bwd_sweep<R>, grid, kBwdThreads, KID_BWD_SWEEP);
+        }
         g->single_launch = false;
     }
     if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
