@@ -57,8 +57,10 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_CUDA(cudaMemset(s.tnet, 0, sizeof(R) * t.n_pins));
     // static per-net path data of startpoints: no worst input, chain length 1
     std::vector<int32_t> pred(t.n_nets, -1), plen(t.n_nets, 1);
-    TDP_TRY(upload(g, &s.pred_in, pred));
-    TDP_TRY(upload(g, &s.pred_net, pred));
+    {
+        std::vector<int2> pr(t.n_nets, make_int2(-1, -1));
+        TDP_TRY(upload(g, &s.pred, pr));
+    }
     TDP_TRY(upload(g, &s.plen, plen));
     // extraction
     TDP_TRY(dalloc(g, &s.sort_a, 2 * (size_t)std::max(t.n_ep, 1)));
@@ -83,10 +85,20 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_CUDA(cudaMemset(s.in_p, 0, t.n_pins));
     TDP_CUDA(cudaMemset(s.w, 0, sizeof(R) * t.n_pins));
     TDP_CUDA(cudaMemset(s.n_pairs, 0, sizeof(long long)));
-    // backward sweep: partial minima of split nets and their counters
+    // backward sweep: required time keys of the nets
     TDP_TRY(dalloc(g, &s.reqkey, t.n_nets));
     // loss
+    TDP_TRY(dalloc(g, &s.net_pf, (size_t)t.n_nets + 32));
+    TDP_TRY(dalloc(g, &s.cell_pf, (size_t)t.n_cells + 32));
+    TDP_TRY(dalloc(g, &s.pnets, t.n_nets));
+    TDP_TRY(dalloc(g, &s.pcells, t.n_cells));
+    TDP_TRY(dalloc(g, &s.pcnt, 2));
+    TDP_TRY(dalloc(g, &s.cmp_blk, std::max(t.n_nets, t.n_cells) / kCompactItems + 2));
+    TDP_CUDA(cudaMemset(s.net_pf, 0, (size_t)t.n_nets + 32));
+    TDP_CUDA(cudaMemset(s.cell_pf, 0, (size_t)t.n_cells + 32));
+    TDP_CUDA(cudaMemset(s.pcnt, 0, 2 * sizeof(int32_t)));
     TDP_TRY(dalloc(g, &s.gslot, 2 * (size_t)t.n_pins));
+    TDP_CUDA(cudaMemset(s.gslot, 0, 2 * sizeof(R) * (size_t)t.n_pins));
     TDP_TRY(dalloc(g, &s.loss_part, 1024));
     TDP_TRY(dalloc(g, &s.loss_count, 1));
     TDP_CUDA(cudaMemset(s.loss_count, 0, sizeof(unsigned)));

@@ -150,18 +150,18 @@ __device__ bool cand_before(const Topo &t, const State<R> &s, const int *par, co
         if (ea && eb) return false;
         if (ea) {
             const int x = B[nb - 1 - k];
-            return s.pred_in[t.sink_onet[x]] < x;
+            return s.pred[t.sink_onet[x]].x < x;
         }
         if (eb) {
             const int x = A[na - 1 - k];
-            return x < s.pred_in[t.sink_onet[x]];
+            return x < s.pred[t.sink_onet[x]].x;
         }
         const int x = A[na - 1 - k], y = B[nb - 1 - k];
         if (x == y) continue;
         const int vx = t.sink_onet[x], vy = t.sink_onet[y];
         if (vx == vy) return x < y;
-        if (t.net_level[vx] > t.net_level[vy]) return x < s.pred_in[vx];
-        return s.pred_in[vy] < y;
+        if (t.net_level[vx] > t.net_level[vy]) return x < s.pred[vx].x;
+        return s.pred[vy].x < y;
     }
 }
 
@@ -353,14 +353,15 @@ __device__ __forceinline__ void walk_path(const Topo &t, const State<R> &s, int 
     int j = nsides - 1;  // sides[] holds the deepest sidetrack first
     for (;;) {
         visit(t.net_ptr[e], false);
-        int pi = s.pred_in[e];
+        const int2 pr = s.pred[e];
+        int pi = pr.x;
         if (pi < 0) break;
         int nx;
         if (j >= 0 && t.sink_onet[sides[j]] == e) {
             pi = sides[j--];
             nx = t.pin_net[pi];
         } else {
-            nx = s.pred_net[e];
+            nx = pr.y;
         }
         visit(pi, true);
         e = nx;

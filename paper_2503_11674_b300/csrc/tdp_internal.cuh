@@ -40,6 +40,8 @@ constexpr int kMaxFanin = 32;      // inputs of a combinational cell
 constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole block
 constexpr int kPre = 4;            // inputs / sinks whose loads are issued together
 constexpr int kRedChunk = 1024;     // endpoints per partial of the WNS / TNS reduction
+constexpr int kCompactItems = 8192; // flags per block of the stream compaction
+constexpr uint8_t kPfSmall = 1, kPfLarge = 2;  // net holds a pair sink; fanout <= / > kBigFanout
 constexpr double kQScale = 16777216.0;  // 2^24: fixed point of slack/WNS in the pair update
 constexpr double kQClamp = 32768.0;     // |slack/WNS| is clamped here before conversion
 
@@ -347,8 +349,7 @@ struct State {
     R *dnet = nullptr;    // [n_nets] delay of the driving cell
     A *arr = nullptr, *req = nullptr;  // [n_pins]
     R *slack = nullptr;   // [n_pins]
-    int32_t *pred_in = nullptr;   // [n_nets] worst input pin of the driving cell (-1: startpoint)
-    int32_t *pred_net = nullptr;  // [n_nets] net of that input
+    int2 *pred = nullptr;         // [n_nets] worst input pin of the driving cell (-1: startpoint), its net
     int32_t *plen = nullptr;      // [n_nets] pins from the driver back to its startpoint
     double *T = nullptr;          // device clock period
     unsigned *gsync = nullptr;    // [2] grid barrier counter, sticky timeout status
@@ -373,8 +374,18 @@ struct State {
     uint8_t *touch = nullptr, *in_p = nullptr;   // [n_pins]
     R *w = nullptr;                               // [n_pins]
     long long *n_pairs = nullptr;
+    // pairs, compacted for the loss: nets holding a sink of P, cells with a
+    // pin in such a net's pair (sink in P or the net's driver); the lists are
+    // ascending, counts in pcnt[0] (nets of at most kBigFanout sinks) and
+    // pcnt[1] (cells)
+    uint8_t *net_pf = nullptr;    // [n_nets] 0, kPfSmall or kPfLarge
+    uint8_t *cell_pf = nullptr;   // [n_cells]
+    int32_t *pnets = nullptr;     // [n_nets]
+    int32_t *pcells = nullptr;    // [n_cells]
+    int32_t *pcnt = nullptr;      // [2]
+    int32_t *cmp_blk = nullptr;   // per-block counts of the compaction
     // loss
-    R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y)
+    R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y); zero outside P
     double *loss_part = nullptr;
     unsigned *loss_count = nullptr;
 };
@@ -454,6 +465,10 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
 // reads and clears the sticky status of the grid barriers (synchronises the
 // stream); TDP_ERR_TIMEOUT if a wait gave up since the last check
 tdp_status check_sync_status(tdp_graph *g);
+
+// rebuild the compacted pair lists (pnets, pcells, pcnt) from net_pf / cell_pf
+template <typename R>
+tdp_status compact_pairs(tdp_graph *g);
 
 // exclusive scan of n int32 counts into int64 offsets (out has n+1 entries)
 tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_t n,

@@ -3,17 +3,20 @@
 //   PP = beta * sum over sinks s in P of w_s * ((x_s - x_d)^2 + (y_s - y_d)^2)
 //
 // with (x_d, y_d) the driver pin of s's net; pin coordinates are the cell
-// position plus the pin offset.  Both passes walk the nets (thread per net up
-// to 32 sinks, warp per net above) so a net's sinks are read contiguously and
-// a driver's gradient is summed in one place, in FP64, in a fixed order.
+// position plus the pin offset.  Both passes walk only the nets that hold a
+// sink of P (the compacted list pnets, thread per net, for nets of at most
+// kBigFanout sinks; a warp per net of the static list of larger nets, which
+// skips nets without one), so a net's sinks are read contiguously and a
+// driver's gradient is summed in one place, in FP64, in a fixed order.
 //
 //   k_pp_fwd       terms in the working precision, FP64 total; fixed grid and
 //                  fixed-order block / grid reduction (deterministic)
-//   k_pp_bwd_net   pin gradients 2 beta w (p_s - p_d) of every sink, minus
-//                  their sum on the driver; written to the pin's slot in the
-//                  cell -> pins order (zero for pins outside P)
-//   k_pp_bwd_cell  per cell, the FP64 sum of its pins' slots times the
-//                  incoming gradient scale; fixed cells get 0
+//   k_pp_bwd_net   pin gradients 2 beta w (p_s - p_d) of the net's sinks in
+//                  P, minus their sum on the driver, into the pins' slots in
+//                  the cell -> pins order (slots outside P stay zero)
+//   k_pp_bwd_cell  per cell of the compacted list pcells, the FP64 sum of its
+//                  pins' slots times the incoming gradient scale (fixed cells
+//                  0); every other cell's gradient is 0
 #include "tdp_internal.cuh"
 
 namespace tdp {
@@ -43,6 +46,8 @@ __device__ __forceinline__ double net_pp(const Topo &t, const State<R> &s, const
     return acc;
 }
 
+// warp tasks of both loss passes: warps [0, nsw) take 32 consecutive entries
+// of pnets (a lane per net), warps [nsw, nsw + n_big) one larger net each
 template <typename R>
 __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
                                                          const R *__restrict__ y, double beta,
@@ -50,20 +55,21 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nsw = (t.n_nets + 31) >> 5;
+    const int np = s.pcnt[0];
+    const int nsw = (np + 31) >> 5;
     const int tasks = nsw + t.n_big;
     const int nwarps = gridDim.x * (kLossThreads / 32);
     double acc = 0.0;
     for (int task = blockIdx.x * (kLossThreads / 32) + wib; task < tasks; task += nwarps) {
         if (task < nsw) {
-            const int e = task * 32 + lane;
-            if (e < t.n_nets) {
-                const int a = t.net_ptr[e], b = t.net_ptr[e + 1];
-                if (b - a - 1 <= kBigFanout) acc += net_pp(t, s, x, y, a, b, 0, 1);
+            const int i = task * 32 + lane;
+            if (i < np) {
+                const int e = s.pnets[i];
+                acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], 0, 1);
             }
         } else {
             const int e = t.big_nets[task - nsw];
-            acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], lane, 32);
+            if (s.net_pf[e]) acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], lane, 32);
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -99,15 +105,13 @@ __device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x,
     const int cd = t.pin_cell[a];
     const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
     for (int p = a + 1 + first; p < b; p += step) {
-        R gx = 0, gy = 0;
-        if (s.in_p[p]) {
-            const int cs = t.pin_cell[p];
-            const R k = (R)two_beta * s.w[p];
-            gx = k * (x[cs] + s.pin_dx[p] - xd);
-            gy = k * (y[cs] + s.pin_dy[p] - yd);
-            sx += (double)gx;
-            sy += (double)gy;
-        }
+        if (!s.in_p[p]) continue;
+        const int cs = t.pin_cell[p];
+        const R k = (R)two_beta * s.w[p];
+        const R gx = k * (x[cs] + s.pin_dx[p] - xd);
+        const R gy = k * (y[cs] + s.pin_dy[p] - yd);
+        sx += (double)gx;
+        sy += (double)gy;
         const int slot = t.slot_of_pin[p];
         s.gslot[2 * slot] = gx;
         s.gslot[2 * slot + 1] = gy;
@@ -116,52 +120,58 @@ __device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x,
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
-                                                    const R *__restrict__ y, double beta, int nsw) {
-    const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+                                                    const R *__restrict__ y, double beta) {
     const int lane = threadIdx.x & 31;
     const double two_beta = 2.0 * beta;
-    double sx = 0.0, sy = 0.0;
-    int a;
-    if (gw < nsw) {
-        const int e = gw * 32 + lane;
-        if (e >= t.n_nets) return;
-        a = t.net_ptr[e];
-        const int b = t.net_ptr[e + 1];
-        if (b - a - 1 > kBigFanout) return;
-        net_grad(t, s, x, y, a, b, 0, 1, two_beta, sx, sy);
-    } else {
-        if (gw - nsw >= t.n_big) return;
-        const int e = t.big_nets[gw - nsw];
-        a = t.net_ptr[e];
-        net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, two_beta, sx, sy);
-        for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    const int np = s.pcnt[0];
+    const int nsw = (np + 31) >> 5;
+    const int tasks = nsw + t.n_big;
+    const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    for (int task = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); task < tasks; task += nwarps) {
+        double sx = 0.0, sy = 0.0;
+        int a;
+        if (task < nsw) {
+            const int i = task * 32 + lane;
+            if (i >= np) continue;
+            const int e = s.pnets[i];
+            a = t.net_ptr[e];
+            net_grad(t, s, x, y, a, t.net_ptr[e + 1], 0, 1, two_beta, sx, sy);
+        } else {
+            const int e = t.big_nets[task - nsw];
+            if (!s.net_pf[e]) continue;  // warp-uniform
+            a = t.net_ptr[e];
+            net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, two_beta, sx, sy);
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lane != 0) continue;
         }
-        if (lane != 0) return;
+        const int slot = t.slot_of_pin[a];
+        s.gslot[2 * slot] = (R)(-sx);
+        s.gslot[2 * slot + 1] = (R)(-sy);
     }
-    const int slot = t.slot_of_pin[a];
-    s.gslot[2 * slot] = (R)(-sx);
-    s.gslot[2 * slot + 1] = (R)(-sy);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const double *gscale,
                                                      R *__restrict__ gx, R *__restrict__ gy) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= t.n_cells) return;
-    double ax = 0.0, ay = 0.0;
-    if (!t.cell_fixed[c]) {
-        for (int k = t.cp_ptr[c]; k < t.cp_ptr[c + 1]; ++k) {
-            ax += (double)s.gslot[2 * k];
-            ay += (double)s.gslot[2 * k + 1];
+    const int nc = s.pcnt[1];
+    const double g = gscale ? *gscale : 1.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const int c = s.pcells[i];
+        double ax = 0.0, ay = 0.0;
+        if (!t.cell_fixed[c]) {
+            for (int k = t.cp_ptr[c]; k < t.cp_ptr[c + 1]; ++k) {
+                ax += (double)s.gslot[2 * k];
+                ay += (double)s.gslot[2 * k + 1];
+            }
+            ax *= g;
+            ay *= g;
         }
-        const double g = gscale ? *gscale : 1.0;
-        ax *= g;
-        ay *= g;
+        gx[c] = (R)ax;
+        gy[c] = (R)ay;
     }
-    gx[c] = (R)ax;
-    gy[c] = (R)ay;
 }
 
 template <typename R>
@@ -177,15 +187,15 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
                          R *gx, R *gy) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    const int nsw = div_up(t.n_nets, 32);
-    const int64_t threads = (int64_t)(nsw + t.n_big) * 32;
+    TDP_CUDA(cudaMemsetAsync(gx, 0, sizeof(R) * t.n_cells, g->stream));
+    TDP_CUDA(cudaMemsetAsync(gy, 0, sizeof(R) * t.n_cells, g->stream));
     {
         LaunchScope ls(g, KID_PP_BWD_NET);
-        k_pp_bwd_net<R><<<div_up(threads, 256), 256, 0, g->stream>>>(t, s, x, y, beta, nsw);
+        k_pp_bwd_net<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, x, y, beta);
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
-        k_pp_bwd_cell<R><<<div_up(t.n_cells, 256), 256, 0, g->stream>>>(t, s, gs, gx, gy);
+        k_pp_bwd_cell<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
     }
     TDP_LAUNCH_CHECK();
     return TDP_OK;

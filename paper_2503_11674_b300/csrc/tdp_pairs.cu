@@ -12,6 +12,7 @@
 // slack), so
 //     new pair:      w = w0 + w1 * (sum q - max q)
 //     pair in P:     w = w  + w1 * sum q.
+#include <algorithm>
 #include <climits>
 
 #include "tdp_internal.cuh"
@@ -69,7 +70,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> 
         for (;;) {
             int pin = -1 - lane;  // distinct per lane when not on a sink
             if (walking) {
-                int pi = s.pred_in[e];
+                const int2 pr = s.pred[e];
+                int pi = pr.x;
                 if (pi < 0) {
                     walking = false;
                 } else {
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> 
                         pi = sides[j--];
                         nx = t.pin_net[pi];
                     } else {
-                        nx = s.pred_net[e];
+                        nx = pr.y;
                     }
                     pin = pi;
                     e = nx;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> 
 }
 
 template <typename R>
-__global__ void k_pair_finish(State<R> s, int n_pins, double w0, double w1) {
+__global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pins || !s.touch[p]) return;
     const double sq = (double)s.sumq[p] / kQScale;
@@ -118,11 +120,122 @@ __global__ void k_pair_finish(State<R> s, int n_pins, double w0, double w1) {
         s.w[p] = (R)(w0 + w1 * (sq - mq));
         s.in_p[p] = 1;
         atomicAdd((unsigned long long *)s.n_pairs, 1ull);
+        // flags for the loss lists (set only; threads of one net write the same value)
+        const int e = t.pin_net[p];
+        const int a = t.net_ptr[e];
+        s.net_pf[e] = t.net_ptr[e + 1] - a - 1 <= kBigFanout ? kPfSmall : kPfLarge;
+        s.cell_pf[t.pin_cell[p]] = 1;
+        s.cell_pf[t.pin_cell[a]] = 1;
     }
     s.sumq[p] = 0;
     s.maxq[p] = LLONG_MIN;
     s.touch[p] = 0;
 }
+
+// ------------------------------------------------------- compaction ---
+// Indices i < n with flag[i] == val, ascending.  A thread takes 32
+// consecutive flags (two 16-byte loads), a block kCompactItems; each block
+// counts, one block scans the counts, and each block writes its indices in
+// order.
+
+constexpr int kCmpThreads = kCompactItems / 32;
+
+__device__ __forceinline__ unsigned match_bits(const uint8_t *f, int base, int n, uint8_t val) {
+    unsigned bits = 0u;
+    if (base + 32 <= n) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(f + base);
+        const uint4 q0 = __ldg(v), q1 = __ldg(v + 1);
+        const unsigned w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (((w[k >> 2] >> (8 * (k & 3))) & 0xffu) == val) bits |= 1u << k;
+    } else {
+        for (int k = 0; k < 32 && base + k < n; ++k)
+            if (f[base + k] == val) bits |= 1u << k;
+    }
+    return bits;
+}
+
+__device__ __forceinline__ int block_excl_sum(int v, int *sh, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    total = sh[(blockDim.x >> 5) - 1];
+    const int before = (w > 0 ? sh[w - 1] : 0) + x - v;
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_cmp_count(const uint8_t *f, uint8_t val, int n, int32_t *blk) {
+    __shared__ int sh[32];
+    const int base = blockIdx.x * kCompactItems + threadIdx.x * 32;
+    int total;
+    block_excl_sum(__popc(match_bits(f, base, n, val)), sh, total);
+    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_cmp_scan(int32_t *blk, int nb, int32_t *total) {
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        int t;
+        const int ex = block_excl_sum(i < nb ? blk[i] : 0, sh, t);
+        if (i < nb) blk[i] = carry + ex;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_cmp_write(const uint8_t *f, uint8_t val, int n, const int32_t *blk,
+                                                          int32_t *out) {
+    __shared__ int sh[32];
+    const int base = blockIdx.x * kCompactItems + threadIdx.x * 32;
+    unsigned bits = match_bits(f, base, n, val);
+    int total;
+    int pos = blk[blockIdx.x] + block_excl_sum(__popc(bits), sh, total);
+    while (bits) {
+        const int k = __ffs(bits) - 1;
+        out[pos++] = base + k;
+        bits &= bits - 1u;
+    }
+}
+
+static void compact(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, int32_t *out, int32_t *count) {
+    int32_t *blk = g->prec == TDP_FP32 ? g->s32.cmp_blk : g->s64.cmp_blk;
+    const int nb = std::max(div_up(n, kCompactItems), 1);
+    k_cmp_count<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk);
+    k_cmp_scan<<<1, 1024, 0, g->stream>>>(blk, nb, count);
+    k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, out);
+    g->n_launch += 3;
+}
+
+template <typename R>
+tdp_status compact_pairs(tdp_graph *g) {
+    const Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    compact(g, s.net_pf, kPfSmall, t.n_nets, s.pnets, s.pcnt);
+    compact(g, s.cell_pf, 1, t.n_cells, s.pcells, s.pcnt + 1);
+    TDP_LAUNCH_CHECK();
+    return TDP_OK;
+}
+
+template tdp_status compact_pairs<float>(tdp_graph *);
+template tdp_status compact_pairs<double>(tdp_graph *);
 
 template <typename R>
 tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
@@ -136,10 +249,10 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
     }
     {
         LaunchScope ls(g, KID_PAIR_FINISH);
-        k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(s, t.n_pins, w0, w1);
+        k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(t, s, t.n_pins, w0, w1);
     }
     TDP_LAUNCH_CHECK();
-    return TDP_OK;
+    return compact_pairs<R>(g);
 }
 
 template tdp_status update_pairs_impl<float>(tdp_graph *, double, double);
@@ -217,12 +330,28 @@ static tdp_status set_pairs_impl(tdp_graph *g, int64_t n, const int32_t *pins, c
         in_p[p] = 1;
         wv[p] = (R)w[k];
     }
+    // loss flags: nets holding a pair sink, cells of pair sinks and of their drivers
+    const Topo &t = g->topo;
+    std::vector<int32_t> ptr(t.n_nets + 1), pcell(np);
+    TDP_CUDA(cudaMemcpy(ptr.data(), t.net_ptr, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+    TDP_CUDA(cudaMemcpy(pcell.data(), t.pin_cell, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> npf(t.n_nets, 0), cpf(t.n_cells, 0);
+    for (int e = 0; e < t.n_nets; ++e)
+        for (int p = ptr[e] + 1; p < ptr[e + 1]; ++p)
+            if (in_p[p]) {
+                npf[e] = ptr[e + 1] - ptr[e] - 1 <= kBigFanout ? kPfSmall : kPfLarge;
+                cpf[pcell[p]] = 1;
+                cpf[pcell[ptr[e]]] = 1;
+            }
     long long cnt = n;
     TDP_CUDA(cudaStreamSynchronize(g->stream));
     TDP_CUDA(cudaMemcpy(s.in_p, in_p.data(), np, cudaMemcpyHostToDevice));
     TDP_CUDA(cudaMemcpy(s.w, wv.data(), sizeof(R) * np, cudaMemcpyHostToDevice));
     TDP_CUDA(cudaMemcpy(s.n_pairs, &cnt, sizeof(cnt), cudaMemcpyHostToDevice));
-    return TDP_OK;
+    TDP_CUDA(cudaMemcpy(s.net_pf, npf.data(), t.n_nets, cudaMemcpyHostToDevice));
+    TDP_CUDA(cudaMemcpy(s.cell_pf, cpf.data(), t.n_cells, cudaMemcpyHostToDevice));
+    TDP_CUDA(cudaMemset(s.gslot, 0, 2 * sizeof(R) * (size_t)np));
+    return compact_pairs<R>(g);
 }
 
 template <typename R>
@@ -232,6 +361,10 @@ static tdp_status reset_pairs_impl(tdp_graph *g) {
     TDP_CUDA(cudaMemsetAsync(s.in_p, 0, np, g->stream));
     TDP_CUDA(cudaMemsetAsync(s.w, 0, sizeof(R) * np, g->stream));
     TDP_CUDA(cudaMemsetAsync(s.n_pairs, 0, sizeof(long long), g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.net_pf, 0, g->topo.n_nets, g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.cell_pf, 0, g->topo.n_cells, g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.pcnt, 0, 2 * sizeof(int32_t), g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.gslot, 0, 2 * sizeof(R) * (size_t)np, g->stream));
     return TDP_OK;
 }
 

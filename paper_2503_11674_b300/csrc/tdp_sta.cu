@@ -226,8 +226,7 @@ __device__ __noinline__ void fwd_cell_wide(const Topo &t, State<R> &s, int k, in
     const int bn = ldg(&t.lv_in_net[bp]);
     const bool bc = (ldg(&t.lv_in_flags[bp]) & kInComb) != 0;
     s.arr[o] = AC::add(best, ldg(&s.dnet[e]));
-    s.pred_in[e] = bi;
-    s.pred_net[e] = bn;
+    s.pred[e] = make_int2(bi, bn);
     s.plen[e] = ldd<COH>(&s.plen[bn]) + 2;
     if constexpr (L > 0) {
         BEnt<R> *out = s.blist + (size_t)e * G;
@@ -480,8 +479,7 @@ __device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, const CellP
     for (int u = 0; u < kPre; ++u)
         if (u < nin) s.arr[c.ip[u]] = av[u];
     s.arr[c.o] = AC::add(best, dcell);
-    s.pred_in[c.e] = bi;
-    s.pred_net[c.e] = bn;
+    s.pred[c.e] = make_int2(bi, bn);
     s.plen[c.e] = bl + 2;
     if constexpr (L > 0) {
         constexpr int G = list_group(L);
