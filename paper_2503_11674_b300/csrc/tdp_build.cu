@@ -1,6 +1,7 @@
 // sta_build / sta_destroy: validate the netlist, levelize the combinational
 // cells (the timing graph of Section II-B is a DAG once flip-flops cut it),
 // and lay the level-ordered CSR arrays out in device memory.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -67,6 +68,8 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(dalloc(g, &s.sort_b, 2 * (size_t)std::max(t.n_ep, 1)));
     TDP_TRY(dalloc(g, &s.nviol, 1));
     TDP_TRY(dalloc(g, &s.viol, std::max(t.n_ep, 1)));
+    TDP_TRY(dalloc(g, &s.ep_flag, (size_t)t.n_ep + 32));
+    TDP_CUDA(cudaMemset(s.ep_flag, 0, (size_t)t.n_ep + 32));
     TDP_TRY(dalloc(g, &s.bcnt, t.n_nets));
     TDP_CUDA(cudaMemset(s.bcnt, 0, sizeof(int32_t) * t.n_nets));
     TDP_TRY(dalloc(g, &s.p_count, std::max(t.n_ep, 1)));

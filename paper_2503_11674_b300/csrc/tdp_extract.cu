@@ -131,6 +131,48 @@ __global__ void k_sort_finish(State<R> s, const SortItem *items) {
     if (i < *s.nviol) s.viol[i] = (int)items[i].pin;
 }
 
+// flag of endpoint i: it fails
+template <typename R>
+__global__ void k_viol_flags(Topo t, State<R> s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.n_ep) s.ep_flag[i] = (double)s.slack[t.ep[i]] < 0.0 ? 1 : 0;
+}
+
+// sort items of the failing endpoints listed by pin
+template <typename R>
+__global__ void k_viol_items(State<R> s, SortItem *items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *s.nviol) {
+        const int p = s.viol[i];
+        items[i] = SortItem{ordered_bits((double)s.slack[p]), (unsigned long long)p};
+    }
+}
+
+// record k of the sorted order from record i of the pin order (viol ascending)
+template <typename R>
+__global__ void k_permute_records(State<R> s, const SortItem *sorted, int K, int32_t *viol, int32_t *cnt,
+                                  int32_t *par, int32_t *side, int32_t *len, R *cost) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = *s.nviol;
+    if (k >= n) return;
+    const int pin = (int)sorted[k].pin;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s.viol[mid] < pin) lo = mid + 1;
+        else hi = mid;
+    }
+    const int i = lo;
+    viol[k] = pin;
+    cnt[k] = s.p_count[i];
+    for (int r = 0; r < K; ++r) {
+        par[(size_t)k * K + r] = s.p_parent[(size_t)i * K + r];
+        side[(size_t)k * K + r] = s.p_side[(size_t)i * K + r];
+        len[(size_t)k * K + r] = s.p_len[(size_t)i * K + r];
+        cost[(size_t)k * K + r] = s.p_cost[(size_t)i * K + r];
+    }
+}
+
 // Is candidate a (parent path pa + sidetrack pin sa) ordered before candidate
 // b (pb + sb) when both have the same slack?  Paths are compared by their pin
 // sequences read from the endpoint; two paths first differ at the first
@@ -293,6 +335,62 @@ static tdp_status ensure_path_buffers(tdp_graph *g, int K) {
     return TDP_OK;
 }
 
+// sort the *nviol items of a (at most n) by (key, pin); the result ends in a
+static void sort_items(SortItem *&a, SortItem *&b, const int *nviol, int n, cudaStream_t st) {
+    k_tile_sort<<<div_up(n, kTile), 1024, 0, st>>>(a, nviol);
+    for (int run = kTile; run < n; run *= 2) {
+        k_merge_pass<<<div_up(n, 256), 256, 0, st>>>(a, b, nviol, run);
+        std::swap(a, b);
+    }
+}
+
+// failing endpoints listed by pin, and their path records: into (slack, pin)
+// order
+template <typename R>
+static tdp_status sort_viol(tdp_graph *g) {
+    if (g->viol_sorted) return TDP_OK;
+    State<R> &s = state<R>(g);
+    const Topo &t = g->topo;
+    cudaStream_t st = g->stream;
+    const int K = g->K;
+    const size_t slots = (size_t)std::max(t.n_ep, 1) * K;
+    SortItem *a = reinterpret_cast<SortItem *>(s.sort_a);
+    SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
+    int32_t *viol = nullptr, *cnt = nullptr, *par = nullptr, *side = nullptr, *len = nullptr;
+    R *cost = nullptr;
+    bool ok = cudaMallocAsync(&viol, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
+              cudaMallocAsync(&cnt, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
+              cudaMallocAsync(&par, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              cudaMallocAsync(&side, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              cudaMallocAsync(&len, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              cudaMallocAsync(&cost, sizeof(R) * slots, st) == cudaSuccess;
+    tdp_status rc = TDP_OK;
+    if (!ok) {
+        set_error("sta_get_paths: temporary allocation failed");
+        rc = TDP_ERR_OOM;
+    } else {
+        g->n_launch += 2;
+        k_viol_items<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
+        sort_items(a, b, s.nviol, t.n_ep, st);
+        k_permute_records<R><<<div_up(t.n_ep, 128), 128, 0, st>>>(s, a, K, viol, cnt, par, side, len, cost);
+        cudaMemcpyAsync(s.viol, viol, sizeof(int32_t) * t.n_ep, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s.p_count, cnt, sizeof(int32_t) * t.n_ep, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s.p_parent, par, sizeof(int32_t) * slots, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s.p_side, side, sizeof(int32_t) * slots, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s.p_len, len, sizeof(int32_t) * slots, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s.p_cost, cost, sizeof(R) * slots, cudaMemcpyDeviceToDevice, st);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("sta_get_paths: sorting the failing endpoints failed");
+            rc = TDP_ERR_CUDA;
+        } else {
+            g->viol_sorted = true;
+        }
+    }
+    for (void *q : {(void *)viol, (void *)cnt, (void *)par, (void *)side, (void *)len, (void *)cost})
+        if (q) cudaFreeAsync(q, st);
+    return rc;
+}
+
 template <typename R>
 tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     Topo &t = g->topo;
@@ -304,17 +402,21 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
     TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
     TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
-    if (t.n_ep > 0) {
+    if (t.n_ep > 0 && n_endpoints < 0) {
+        // all failing endpoints: their order does not change the paths, so
+        // they are listed by pin here and sorted when the paths are read
+        LaunchScope ls(g, KID_VIOL_SORT, 4);
+        k_viol_flags<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s);
+        compact_u8(g, s.ep_flag, 1, t.n_ep, t.ep, s.viol, s.nviol);
+        g->viol_sorted = false;
+    } else if (t.n_ep > 0) {
         int passes = 0;
         for (int run = kTile; run < t.n_ep; run *= 2) ++passes;
         LaunchScope ls(g, KID_VIOL_SORT, 3 + passes);
         k_viol_collect<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s, a);
-        k_tile_sort<<<div_up(t.n_ep, kTile), 1024, 0, st>>>(a, s.nviol);
-        for (int run = kTile; run < t.n_ep; run *= 2) {
-            k_merge_pass<<<div_up(t.n_ep, 256), 256, 0, st>>>(a, b, s.nviol, run);
-            std::swap(a, b);
-        }
+        sort_items(a, b, s.nviol, t.n_ep, st);
         k_sort_finish<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
+        g->viol_sorted = true;
     }
     TDP_LAUNCH_CHECK();
     // 2. sidetrack lists: the next sweeps build K - 1 entries per node; if the
@@ -411,6 +513,7 @@ tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, in
     State<R> &s = state<R>(g);
     const Topo &t = g->topo;
     cudaStream_t st = g->stream;
+    TDP_TRY(sort_viol<R>(g));
     int nv = 0;
     long long np = 0;
     TDP_CUDA(cudaMemcpyAsync(&nv, s.nviol, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -362,7 +362,8 @@ struct State {
     // extraction
     uint64_t *sort_a = nullptr, *sort_b = nullptr;  // (key, pin) items, ping-pong
     int32_t *nviol = nullptr;     // device count of failing endpoints
-    int32_t *viol = nullptr;      // [n_ep] failing endpoints sorted by (slack, pin)
+    int32_t *viol = nullptr;      // [n_ep] failing endpoints, by (slack, pin) or by pin (see viol_sorted)
+    uint8_t *ep_flag = nullptr;   // [n_ep + 32] endpoint fails
     BEnt<R> *blist = nullptr;     // [n_nets * kMaxK] sidetrack lists, list_group(list_L) apart
     int32_t *bcnt = nullptr;      // [n_nets] entries in each sidetrack list
     int32_t *p_parent = nullptr, *p_side = nullptr, *p_len = nullptr;  // [n_ep * K]
@@ -403,6 +404,9 @@ struct tdp_graph {
     double r = 0, c = 0, d0 = 0;
     int K = 0, keep_nonneg = 0, n_endpoints = -1;
     bool propagated = false, extracted = false;
+    // failing endpoints: sorted by (slack, pin), or (extraction of all of
+    // them) by pin until sta_get_paths sorts them and their path records
+    bool viol_sorted = true;
     // sidetrack lists are built by the forward sweep: list_L entries per node
     // (the K - 1 of the last extraction), lists_valid_L of them are current
     int list_L = 0, lists_valid_L = 0;
@@ -465,6 +469,12 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
 // reads and clears the sticky status of the grid barriers (synchronises the
 // stream); TDP_ERR_TIMEOUT if a wait gave up since the last check
 tdp_status check_sync_status(tdp_graph *g);
+
+// indices i < n (or map[i]) with flags[i] == val, ascending, into out, and
+// their number into the device word count (3 launches; flags padded to a
+// multiple of 32 bytes)
+void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
+                int32_t *count);
 
 // rebuild the compacted pair lists (pnets, pcells, pcnt) from net_pf / cell_pf
 template <typename R>

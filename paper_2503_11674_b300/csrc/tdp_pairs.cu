@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(1024) k_cmp_scan(int32_t *blk, int nb, int32_t
 }
 
 __global__ void __launch_bounds__(kCmpThreads) k_cmp_write(const uint8_t *f, uint8_t val, int n, const int32_t *blk,
-                                                          int32_t *out) {
+                                                          const int32_t *map, int32_t *out) {
     __shared__ int sh[32];
     const int base = blockIdx.x * kCompactItems + threadIdx.x * 32;
     unsigned bits = match_bits(f, base, n, val);
@@ -210,26 +210,27 @@ __global__ void __launch_bounds__(kCmpThreads) k_cmp_write(const uint8_t *f, uin
     int pos = blk[blockIdx.x] + block_excl_sum(__popc(bits), sh, total);
     while (bits) {
         const int k = __ffs(bits) - 1;
-        out[pos++] = base + k;
+        out[pos++] = map ? map[base + k] : base + k;
         bits &= bits - 1u;
     }
 }
 
-static void compact(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, int32_t *out, int32_t *count) {
+void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
+                int32_t *count) {
     int32_t *blk = g->prec == TDP_FP32 ? g->s32.cmp_blk : g->s64.cmp_blk;
     const int nb = std::max(div_up(n, kCompactItems), 1);
     k_cmp_count<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk);
     k_cmp_scan<<<1, 1024, 0, g->stream>>>(blk, nb, count);
-    k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, out);
-    g->n_launch += 3;
+    k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, map, out);
 }
 
 template <typename R>
 tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    compact(g, s.net_pf, kPfSmall, t.n_nets, s.pnets, s.pcnt);
-    compact(g, s.cell_pf, 1, t.n_cells, s.pcells, s.pcnt + 1);
+    compact_u8(g, s.net_pf, kPfSmall, t.n_nets, nullptr, s.pnets, s.pcnt);
+    compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1);
+    g->n_launch += 6;
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
