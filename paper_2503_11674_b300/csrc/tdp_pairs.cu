@@ -21,48 +21,54 @@ namespace tdp {
 
 constexpr int kWalkWarps = 4;
 
-// One warp per failing endpoint; lane r walks the endpoint's path of rank r
+// A warp takes 32 / KP failing endpoints (KP: K rounded up to a power of
+// two); lane g * KP + r walks the path of rank r of the warp's endpoint g
 // from the endpoint back to its startpoint, one net arc per step.  Paths of
 // one endpoint share their first arcs, and lanes standing on the same sink
 // in the same step are merged (__match_any_sync): the lowest such lane adds
-// the group's summed q and raises the maximum once for all of them.
+// the group's summed q and raises the maximum once for all of them (sums and
+// maxima do not depend on how the lanes are grouped).
 template <typename R>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> s, int K, int n_cap) {
+__global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> s, int K, int KP, int n_cap) {
     __shared__ long long shQ[kWalkWarps][32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per = 32 / KP, g = lane / KP, r = lane % KP;
     const int nv = min(*s.nviol, n_cap);
     const double wns = s.wns_tns[0];
     if (!(wns < 0.0)) return;
-    for (int i = blockIdx.x * kWalkWarps + w; i < nv; i += gridDim.x * kWalkWarps) {
-        const int ep = s.viol[i];
-        const int cnt = s.p_count[i];
-        const bool on = lane < cnt;
-        const size_t base = (size_t)i * K;
+    const int n_tasks = (nv + per - 1) / per;
+    for (int task = blockIdx.x * kWalkWarps + w; task < n_tasks; task += gridDim.x * kWalkWarps) {
+        const int i = task * per + g;
+        const bool have = i < nv;
+        const int ep = have ? s.viol[i] : -1;
+        const int cnt = have ? s.p_count[i] : 0;
+        const bool on = r < cnt;
+        const size_t base = (size_t)(have ? i : 0) * K;
         long long Q = 0;
         int sides[kMaxK];
         int ns = 0;
         if (on) {
-            const R sigma = s.slack[ep] + s.p_cost[base + lane];
+            const R sigma = s.slack[ep] + s.p_cost[base + r];
             double q = (double)sigma / wns;
             q = fmin(fmax(q, -kQClamp), kQClamp);
             Q = __double2ll_rn(q * kQScale);
-            for (int x = lane; x > 0; x = s.p_parent[base + x]) sides[ns++] = s.p_side[base + x];
+            for (int x = r; x > 0; x = s.p_parent[base + x]) sides[ns++] = s.p_side[base + x];
         }
         shQ[w][lane] = Q;
         __syncwarp();
-        // the endpoint's own net arc is on every path
-        if (lane == 0) {
+        // the endpoint's own net arc is on every path of the endpoint
+        if (r == 0 && have) {
             long long sum = 0, mx = LLONG_MIN;
             for (int l = 0; l < cnt; ++l) {
-                sum += shQ[w][l];
-                mx = max(mx, shQ[w][l]);
+                sum += shQ[w][g * KP + l];
+                mx = max(mx, shQ[w][g * KP + l]);
             }
             atomicAdd((unsigned long long *)&s.sumq[ep], (unsigned long long)sum);
             atomicMax(&s.maxq[ep], mx);
             s.touch[ep] = 1;
         }
-        int e = t.pin_net[ep];
+        int e = on ? t.pin_net[ep] : 0;
         int j = ns - 1;  // sides[] holds the deepest sidetrack first
         bool walking = on;
         unsigned last_mask = 0;
@@ -245,8 +251,10 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
     const int n_cap = g->n_endpoints < 0 ? INT_MAX : g->n_endpoints;
     if (t.n_ep > 0) {
         LaunchScope ls(g, KID_PAIR_WALK);
-        const int blocks = std::min(div_up(t.n_ep, kWalkWarps), 148 * 16);
-        k_pair_walk<R><<<blocks, kWalkWarps * 32, 0, g->stream>>>(t, s, g->K, n_cap);
+        int KP = 1;
+        while (KP < g->K) KP *= 2;
+        const int blocks = std::min(div_up(div_up(t.n_ep, 32 / KP), kWalkWarps), 148 * 16);
+        k_pair_walk<R><<<blocks, kWalkWarps * 32, 0, g->stream>>>(t, s, g->K, KP, n_cap);
     }
     {
         LaunchScope ls(g, KID_PAIR_FINISH);
