@@ -13,7 +13,7 @@
 //      resulting paths would be (read from the endpoint).  The forward sweep
 //      builds lists as long as the last extraction needed (K - 1); when an
 //      extraction needs longer lists it reruns the forward sweep first.
-// 3. k_topk: one warp per failing endpoint.  The worst path follows worst
+// 3. k_topk: a group of lanes per failing endpoint.  The worst path follows worst
 //      inputs from the endpoint; every other path is its parent path plus one
 //      sidetrack taken on the parent's last worst-input chain.  A candidate
 //      (parent p, index j) is entry j of the list at the head of p's chain;
@@ -209,31 +209,41 @@ __device__ bool cand_before(const Topo &t, const State<R> &s, const int *par, co
 
 constexpr int kTopkWarps = 4;
 
+// A warp takes 32 / KP failing endpoints (KP: K rounded up to a power of
+// two); the group of KP lanes g * KP .. g * KP + KP - 1 searches endpoint g,
+// its frontier one candidate per lane, its paths in shared slots g * KP + r.
+// Reductions, ballots and the tie order stay within a group; the warp loops
+// until every group is done.
 template <typename R>
-__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int G,
+__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int KP, int G,
                                                           int keep_nonneg, int n_cap) {
-    __shared__ int sh_par[kTopkWarps][kMaxK], sh_side[kTopkWarps][kMaxK];
-    __shared__ int sh_len[kTopkWarps][kMaxK];
-    __shared__ R sh_cost[kTopkWarps][kMaxK];
+    __shared__ int sh_par[kTopkWarps][32], sh_side[kTopkWarps][32];
+    __shared__ int sh_len[kTopkWarps][32];
+    __shared__ R sh_cost[kTopkWarps][32];
     __shared__ int ct_par[kTopkWarps][32], ct_side[kTopkWarps][32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per = 32 / KP, g = lane / KP, gl = lane % KP, gb = g * KP;
+    const unsigned gmask = (KP == 32 ? FULL : ((1u << KP) - 1u)) << gb;
     const R INF = (R)__longlong_as_double(0x7ff0000000000000ll);
     const int nv = min(*s.nviol, n_cap);
-    for (int i = blockIdx.x * kTopkWarps + w; i < nv; i += gridDim.x * kTopkWarps) {
-        const int ep = s.viol[i];
-        const R se = s.slack[ep];
-        const int e0 = t.pin_net[ep];
-        if (lane == 0) {
-            sh_par[w][0] = -1;
-            sh_side[w][0] = -1;
-            sh_len[w][0] = 1 + s.plen[e0];
-            sh_cost[w][0] = R(0);
+    const int n_tasks = (nv + per - 1) / per;
+    for (int task = blockIdx.x * kTopkWarps + w; task < n_tasks; task += gridDim.x * kTopkWarps) {
+        const int i = task * per + g;
+        const bool have = i < nv;
+        const int ep = have ? s.viol[i] : 0;
+        const R se = have ? s.slack[ep] : R(0);
+        const int e0 = have ? t.pin_net[ep] : 0;
+        if (gl == 0 && have) {
+            sh_par[w][gb] = -1;
+            sh_side[w][gb] = -1;
+            sh_len[w][gb] = 1 + s.plen[e0];
+            sh_cost[w][gb] = R(0);
         }
         bool cv = false;
         int cpar = 0, cj = 0, ctail = 0;
         R ccost = R(0);
-        if (lane == 0 && K > 1 && s.bcnt[e0] > 0) {
+        if (gl == 0 && have && K > 1 && s.bcnt[e0] > 0) {
             const R d = s.blist[(size_t)e0 * G].delta;
             if (keep_nonneg || se + d < R(0)) {
                 cv = true;
@@ -243,46 +253,52 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
         }
         __syncwarp();
         int n = 1;
-        for (; n < K; ++n) {
+        bool done = !have;  // the same in every lane of a group
+        for (int step = 1; step < K; ++step) {
             R mn = cv ? ccost : INF;
-            for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(FULL, mn, o));
-            if (!(mn < INF)) break;
-            const unsigned tied = __ballot_sync(FULL, cv && ccost == mn);
-            int win = __ffs(tied) - 1;
-            if (__popc(tied) > 1) {  // equal slack: order by pin sequence
+            for (int o = KP / 2; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(FULL, mn, o));
+            if (!(mn < INF)) done = true;
+            if (__all_sync(FULL, done)) break;
+            const unsigned tied = __ballot_sync(FULL, !done && cv && ccost == mn) & gmask;
+            int win = tied ? __ffs(tied) - 1 : lane;
+            if (__any_sync(FULL, __popc(tied) > 1)) {  // equal slack: order by pin sequence
                 if (cv) {
                     ct_par[w][lane] = cpar;
                     ct_side[w][lane] = s.blist[(size_t)ctail * G + cj].pin;
                 }
                 __syncwarp();
                 int best = win;
-                if (lane == 0) {
-                    for (int l = win + 1; l < 32; ++l) {
+                if (gl == 0 && __popc(tied) > 1) {
+                    for (int l = win + 1; l < gb + KP; ++l) {
                         if (!((tied >> l) & 1u)) continue;
-                        if (cand_before<R>(t, s, sh_par[w], sh_side[w], ct_par[w][l], ct_side[w][l],
+                        if (cand_before<R>(t, s, &sh_par[w][gb], &sh_side[w][gb], ct_par[w][l], ct_side[w][l],
                                            ct_par[w][best], ct_side[w][best]))
                             best = l;
                     }
                 }
-                win = __shfl_sync(FULL, best, 0);
+                win = __shfl_sync(FULL, best, gb);
+                __syncwarp();
             }
             const int wpar = __shfl_sync(FULL, cpar, win);
             const int wj = __shfl_sync(FULL, cj, win);
             const int wtail = __shfl_sync(FULL, ctail, win);
             const R wcost = __shfl_sync(FULL, ccost, win);
-            const int sp = s.blist[(size_t)wtail * G + wj].pin;
-            const int tn = t.pin_net[sp];
-            const int len = sh_len[w][wpar] - s.plen[t.sink_onet[sp]] + 2 + s.plen[tn];
-            if (lane == 0) {
-                sh_par[w][n] = wpar;
-                sh_side[w][n] = sp;
-                sh_len[w][n] = len;
-                sh_cost[w][n] = wcost;
+            int sp = 0, tn = 0, len = 0;
+            if (!done) {
+                sp = s.blist[(size_t)wtail * G + wj].pin;
+                tn = t.pin_net[sp];
+                len = sh_len[w][gb + wpar] - s.plen[t.sink_onet[sp]] + 2 + s.plen[tn];
             }
-            if (lane == win) {  // replace the popped candidate by its next sibling
+            if (gl == 0 && !done) {
+                sh_par[w][gb + n] = wpar;
+                sh_side[w][gb + n] = sp;
+                sh_len[w][gb + n] = len;
+                sh_cost[w][gb + n] = wcost;
+            }
+            if (!done && lane == win) {  // replace the popped candidate by its next sibling
                 cv = false;
                 if (wj + 1 < min(s.bcnt[wtail], K - 1)) {  // lists may be longer than K - 1
-                    const R c2 = sh_cost[w][wpar] + s.blist[(size_t)wtail * G + wj + 1].delta;
+                    const R c2 = sh_cost[w][gb + wpar] + s.blist[(size_t)wtail * G + wj + 1].delta;
                     if (keep_nonneg || se + c2 < R(0)) {
                         cv = true;
                         cj = wj + 1;
@@ -292,11 +308,11 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
             }
             bool add_child = false;
             R cc = R(0);
-            if (n + 1 < K && s.bcnt[tn] > 0) {
+            if (!done && n + 1 < K && s.bcnt[tn] > 0) {
                 cc = wcost + s.blist[(size_t)tn * G].delta;
                 add_child = keep_nonneg || se + cc < R(0);
             }
-            const unsigned freem = __ballot_sync(FULL, !cv);
+            const unsigned freem = __ballot_sync(FULL, !cv) & gmask;
             if (add_child && lane == __ffs(freem) - 1) {
                 cv = true;
                 cpar = n;
@@ -304,16 +320,17 @@ __global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, in
                 ctail = tn;
                 ccost = cc;
             }
+            if (!done) ++n;
             __syncwarp();
         }
-        for (int r = lane; r < n; r += 32) {
+        for (int r = gl; have && r < n; r += KP) {
             const size_t slot = (size_t)i * K + r;
-            s.p_parent[slot] = sh_par[w][r];
-            s.p_side[slot] = sh_side[w][r];
-            s.p_len[slot] = sh_len[w][r];
-            s.p_cost[slot] = sh_cost[w][r];
+            s.p_parent[slot] = sh_par[w][gb + r];
+            s.p_side[slot] = sh_side[w][gb + r];
+            s.p_len[slot] = sh_len[w][gb + r];
+            s.p_cost[slot] = sh_cost[w][gb + r];
         }
-        if (lane == 0) {
+        if (gl == 0 && have) {
             s.p_count[i] = n;
             atomicAdd((unsigned long long *)s.n_paths, (unsigned long long)n);
         }
@@ -431,9 +448,11 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     // 3. K paths per endpoint
     if (t.n_ep > 0) {
         int n_cap = n_endpoints < 0 ? INT_MAX : n_endpoints;
-        int blocks = std::min(div_up(t.n_ep, kTopkWarps), 148 * 16);
+        int KP = 1;
+        while (KP < K) KP *= 2;
+        int blocks = std::min(div_up(div_up(t.n_ep, 32 / KP), kTopkWarps), 148 * 16);
         LaunchScope ls(g, KID_TOPK);
-        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, list_group(g->lists_valid_L), keep_nonneg,
+        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, KP, list_group(g->lists_valid_L), keep_nonneg,
                                                       n_cap);
         TDP_LAUNCH_CHECK();
     }
