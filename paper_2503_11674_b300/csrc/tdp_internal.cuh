@@ -252,7 +252,9 @@ __device__ __forceinline__ bool grid_wait(const GridSync &gs, unsigned target) {
             }
         }
         if (!good) atomicExch(gs.status, 1u);
-        __threadfence();
+        // no fence here: the acquire load orders this thread, the block
+        // barrier below the others, and every value written during a sweep
+        // is read from L2 (ld.global.cg), never from a stale L1 line
         ok = good;
     }
     __syncthreads();
