@@ -436,7 +436,27 @@ def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
         torch.cuda.synchronize()
         for i, k in enumerate(names):
             tot[k] += ev[i].elapsed_time(ev[i + 1])
-    return {k: round(v / reps, 4) for k, v in tot.items()}
+    out = {k: round(v / reps, 4) for k, v in tot.items()}
+    # the loss variants of the ablation (same pair set, same placement)
+    kinds = {}
+    for kind in ("quadratic", "hpwl", "euclid"):
+        G.attraction_set_loss_kind(kind)
+        f = b = 0.0
+        for r in range(reps):
+            x, y = xs[r % len(xs)], ys[r % len(ys)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
+            ev[1].record(stream)
+            G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            f += ev[0].elapsed_time(ev[1])
+            b += ev[1].elapsed_time(ev[2])
+        kinds[kind] = {"fwd_ms": round(f / reps, 4), "bwd_ms": round(b / reps, 4)}
+    G.attraction_set_loss_kind("quadratic")
+    out["loss_kinds"] = kinds
+    return out
 
 
 # ------------------------------------------------------------ CPU oracle --

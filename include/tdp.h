@@ -57,6 +57,13 @@ typedef enum {
 
 typedef enum { TDP_FP32 = 0, TDP_FP64 = 1 } tdp_precision;
 
+/* pin-pair distance term of the attraction loss */
+typedef enum {
+    TDP_LOSS_QUADRATIC = 0, /* Q(i,j) = dx^2 + dy^2, Eq. (9) (default)          */
+    TDP_LOSS_HPWL = 1,      /* |dx| + |dy|       (ablation, Section IV)          */
+    TDP_LOSS_EUCLID = 2     /* sqrt(dx^2 + dy^2) (ablation, Section IV)          */
+} tdp_loss_kind;
+
 /* cell_type values */
 enum { TDP_CELL_COMB = 0, TDP_CELL_FF = 1, TDP_CELL_PI = 2, TDP_CELL_PO = 3 };
 
@@ -231,6 +238,17 @@ TDP_API tdp_status attraction_loss_fwd(tdp_graph *g, const void *x_dev, const vo
  */
 TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
                                const double *grad_scale_dev, void *gx_dev, void *gy_dev);
+
+/*
+ * attraction_set_loss_kind: the pair term Q(i, j) of later
+ * attraction_loss_fwd / _bwd calls on g.  TDP_LOSS_QUADRATIC (the default)
+ * is Eq. (9).  TDP_LOSS_HPWL (|dx| + |dy|, pin gradient beta w_s sign(dx),
+ * sign(dy), 0 at 0) and TDP_LOSS_EUCLID (sqrt(dx^2 + dy^2), pin gradient
+ * beta w_s (dx, dy) / d, 0 when the pins coincide) are the alternatives the
+ * ablation of Section IV compares; the paper names them without formulas.
+ * Errors: TDP_ERR_INVALID (NULL graph, unknown kind).
+ */
+TDP_API tdp_status attraction_set_loss_kind(tdp_graph *g, tdp_loss_kind kind);
 
 /*
  * attraction_loss_fwd for callers that cannot allocate device memory (no

@@ -64,6 +64,9 @@ def _load():
         lib.or_loss.restype = C.c_double
         lib.or_loss.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P,
                                 C.c_double, C.c_int, P, P]
+        lib.or_loss_kind.restype = C.c_double
+        lib.or_loss_kind.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P,
+                                     C.c_double, C.c_int, C.c_int, P, P]
         _lib = lib
     return _lib
 
@@ -167,16 +170,23 @@ def update_pairs(nl, paths: dict, wns: float, w0: float, w1: float, in_p=None, w
     return in_p, w
 
 
-def loss(nl, in_p, w, beta: float = 1.0, x=None, y=None, drop_fixed: bool = True):
-    """PP = beta * sum_{(i,j) in P} w_ij Q(i,j) (Eq. (9)); returns (PP, gx, gy)."""
+LOSS_KINDS = {"quadratic": 0, "hpwl": 1, "euclid": 2}
+
+
+def loss(nl, in_p, w, beta: float = 1.0, x=None, y=None, drop_fixed: bool = True,
+         kind: str = "quadratic"):
+    """PP = beta * sum_{(i,j) in P} w_ij Q(i,j) (Eq. (9)); returns (PP, gx, gy).
+
+    kind "hpwl" / "euclid" replaces Q(i,j) by the pair's HPWL or linear
+    Euclidean distance (the ablation of Section IV)."""
     lib = _load()
     x = _f64(nl.x if x is None else x)
     y = _f64(nl.y if y is None else y)
     gx = np.zeros(nl.n_cells)
     gy = np.zeros(nl.n_cells)
-    pp = lib.or_loss(nl.n_cells, nl.n_pins, nl.n_nets, _p(_i32(nl.pin_cell)), _p(_i32(nl.net_ptr)),
-                     _p(_f64(nl.pin_dx)), _p(_f64(nl.pin_dy)),
-                     _p(np.ascontiguousarray(nl.cell_fixed, dtype=np.uint8)), _p(x), _p(y),
-                     _p(np.ascontiguousarray(in_p, dtype=np.uint8)), _p(_f64(w)), float(beta),
-                     int(bool(drop_fixed)), _p(gx), _p(gy))
+    pp = lib.or_loss_kind(nl.n_cells, nl.n_pins, nl.n_nets, _p(_i32(nl.pin_cell)), _p(_i32(nl.net_ptr)),
+                          _p(_f64(nl.pin_dx)), _p(_f64(nl.pin_dy)),
+                          _p(np.ascontiguousarray(nl.cell_fixed, dtype=np.uint8)), _p(x), _p(y),
+                          _p(np.ascontiguousarray(in_p, dtype=np.uint8)), _p(_f64(w)), float(beta),
+                          int(bool(drop_fixed)), LOSS_KINDS[kind], _p(gx), _p(gy))
     return float(pp), gx, gy

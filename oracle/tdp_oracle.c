@@ -19,7 +19,9 @@
  *   or_update_pairs Section III-D, Eq. (w_ij): the literal traversal of the
  *                   extracted paths, worst path first.
  *   or_loss         Eq. (9) quadratic pin-to-pin loss Q(i,j), and the PP sum
- *                   of Section III-D, with its analytic gradient.
+ *                   of Section III-D, with its analytic gradient;
+ *                   or_loss_kind also the HPWL and linear Euclidean pair
+ *                   distances of the ablation (Section IV).
  *
  * Where the paper is silent (delay model, ties, endpoints) this file reads
  * it as follows: single corner, late only, ideal clock
@@ -521,10 +523,16 @@ int or_update_pairs(int n_pins, const uint8_t *pin_dir, int64_t n_paths, const d
  * (cell position plus pin offset).  Gradients with respect to cell x / y are
  * added into gx / gy (zeroed first); fixed cells get zero when drop_fixed.
  */
-double or_loss(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
-               const int32_t *net_ptr, const double *pin_dx, const double *pin_dy,
-               const uint8_t *cell_fixed, const double *x, const double *y, const uint8_t *in_p,
-               const double *w, double beta, int drop_fixed, double *gx, double *gy) {
+/* Pin-pair distance term of the loss, kind 0: the quadratic Q(i,j) of
+ * Eq. (9).  Kinds 1 and 2 are the two alternatives of the ablation
+ * (Section IV), which the paper names but does not write out: kind 1 the
+ * pair's HPWL |dx| + |dy|, kind 2 its linear Euclidean distance
+ * sqrt(dx^2 + dy^2).  Their gradients: sign(dx), sign(dy) (0 at 0) for
+ * HPWL; dx / d, dy / d (0 when the pins coincide) for the distance. */
+double or_loss_kind(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
+                    const int32_t *net_ptr, const double *pin_dx, const double *pin_dy,
+                    const uint8_t *cell_fixed, const double *x, const double *y, const uint8_t *in_p,
+                    const double *w, double beta, int drop_fixed, int kind, double *gx, double *gy) {
     double pp = 0.0;
     for (int c = 0; c < n_cells; ++c) { gx[c] = 0.0; gy[c] = 0.0; }
     (void)n_pins;
@@ -537,8 +545,21 @@ double or_loss(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
             int cs = pin_cell[s];
             double xs = x[cs] + pin_dx[s], ys = y[cs] + pin_dy[s];
             double ddx = xs - xd, ddy = ys - yd;
-            pp += w[s] * (ddx * ddx + ddy * ddy);
-            double gxs = 2.0 * beta * w[s] * ddx, gys = 2.0 * beta * w[s] * ddy;
+            double term, gxs, gys;
+            if (kind == 1) {
+                term = fabs(ddx) + fabs(ddy);
+                gxs = beta * w[s] * (double)((ddx > 0.0) - (ddx < 0.0));
+                gys = beta * w[s] * (double)((ddy > 0.0) - (ddy < 0.0));
+            } else if (kind == 2) {
+                term = sqrt(ddx * ddx + ddy * ddy);
+                gxs = term > 0.0 ? beta * w[s] * ddx / term : 0.0;
+                gys = term > 0.0 ? beta * w[s] * ddy / term : 0.0;
+            } else {
+                term = ddx * ddx + ddy * ddy;
+                gxs = 2.0 * beta * w[s] * ddx;
+                gys = 2.0 * beta * w[s] * ddy;
+            }
+            pp += w[s] * term;
             gx[cs] += gxs; gy[cs] += gys;
             gx[cd] -= gxs; gy[cd] -= gys;
         }
@@ -547,4 +568,12 @@ double or_loss(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
         for (int c = 0; c < n_cells; ++c)
             if (cell_fixed[c]) { gx[c] = 0.0; gy[c] = 0.0; }
     return beta * pp;
+}
+
+double or_loss(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
+               const int32_t *net_ptr, const double *pin_dx, const double *pin_dy,
+               const uint8_t *cell_fixed, const double *x, const double *y, const uint8_t *in_p,
+               const double *w, double beta, int drop_fixed, double *gx, double *gy) {
+    return or_loss_kind(n_cells, n_pins, n_nets, pin_cell, net_ptr, pin_dx, pin_dy, cell_fixed, x, y,
+                        in_p, w, beta, drop_fixed, 0, gx, gy);
 }

@@ -405,6 +405,7 @@ struct tdp_graph {
     tdp::State<double> s64;
     double r = 0, c = 0, d0 = 0;
     int K = 0, keep_nonneg = 0, n_endpoints = -1;
+    int loss_kind = 0;  // tdp_loss_kind of the attraction loss
     bool propagated = false, extracted = false;
     // failing endpoints: sorted by (slack, pin), or (extraction of all of
     // them) by pin until sta_get_paths sorts them and their path records

@@ -2,6 +2,9 @@
 //
 //   PP = beta * sum over sinks s in P of w_s * ((x_s - x_d)^2 + (y_s - y_d)^2)
 //
+// or, as set by attraction_set_loss_kind, with the pair's HPWL or linear
+// Euclidean distance in place of the quadratic term (the ablation of
+// Section IV).
 // with (x_d, y_d) the driver pin of s's net; pin coordinates are the cell
 // position plus the pin offset.  Both passes walk only the nets that hold a
 // sink of P (the compacted list pnets, thread per net, for nets of at most
@@ -24,9 +27,33 @@ namespace tdp {
 constexpr int kLossBlocks = 148 * 4;
 constexpr int kLossThreads = 256;
 
+// Pair distance term (kind 0: Q(i,j) of Eq. (9); 1: |dx| + |dy|; 2:
+// sqrt(dx^2 + dy^2), the ablation's alternatives) and its gradient with
+// respect to the sink's position, per unit weight and beta.
+template <typename R>
+__device__ __forceinline__ R pair_term(R dx, R dy, int kind) {
+    if (kind == 1) return fabs(dx) + fabs(dy);
+    if (kind == 2) return sqrt(dx * dx + dy * dy);
+    return dx * dx + dy * dy;
+}
+template <typename R>
+__device__ __forceinline__ void pair_grad(R dx, R dy, int kind, R &gx, R &gy) {
+    if (kind == 1) {
+        gx = (R)((dx > R(0)) - (dx < R(0)));
+        gy = (R)((dy > R(0)) - (dy < R(0)));
+    } else if (kind == 2) {
+        const R d = sqrt(dx * dx + dy * dy);
+        gx = d > R(0) ? dx / d : R(0);
+        gy = d > R(0) ? dy / d : R(0);
+    } else {
+        gx = R(2) * dx;
+        gy = R(2) * dy;
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ double net_pp(const Topo &t, const State<R> &s, const R *x, const R *y,
-                                         int a, int b, int first, int step) {
+                                         int a, int b, int first, int step, int kind) {
     double acc = 0.0;
     bool have = false;
     R xd = 0, yd = 0;
@@ -41,7 +68,7 @@ __device__ __forceinline__ double net_pp(const Topo &t, const State<R> &s, const
         const int cs = t.pin_cell[p];
         const R dx = x[cs] + s.pin_dx[p] - xd;
         const R dy = y[cs] + s.pin_dy[p] - yd;
-        acc += (double)(s.w[p] * (dx * dx + dy * dy));
+        acc += (double)(s.w[p] * pair_term(dx, dy, kind));
     }
     return acc;
 }
@@ -51,7 +78,7 @@ __device__ __forceinline__ double net_pp(const Topo &t, const State<R> &s, const
 template <typename R>
 __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
                                                          const R *__restrict__ y, double beta,
-                                                         double *loss) {
+                                                         int kind, double *loss) {
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -65,11 +92,11 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
             const int i = task * 32 + lane;
             if (i < np) {
                 const int e = s.pnets[i];
-                acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], 0, 1);
+                acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], 0, 1, kind);
             }
         } else {
             const int e = t.big_nets[task - nsw];
-            if (s.net_pf[e]) acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], lane, 32);
+            if (s.net_pf[e]) acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], lane, 32, kind);
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -100,16 +127,18 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
 // is large; the driver's sum is returned to the caller (partial per lane).
 template <typename R>
 __device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x, const R *y,
-                                         int a, int b, int first, int step, double two_beta,
+                                         int a, int b, int first, int step, double beta, int kind,
                                          double &sx, double &sy) {
     const int cd = t.pin_cell[a];
     const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
     for (int p = a + 1 + first; p < b; p += step) {
         if (!s.in_p[p]) continue;
         const int cs = t.pin_cell[p];
-        const R k = (R)two_beta * s.w[p];
-        const R gx = k * (x[cs] + s.pin_dx[p] - xd);
-        const R gy = k * (y[cs] + s.pin_dy[p] - yd);
+        const R k = (R)beta * s.w[p];
+        R ux, uy;
+        pair_grad(x[cs] + s.pin_dx[p] - xd, y[cs] + s.pin_dy[p] - yd, kind, ux, uy);
+        const R gx = k * ux;
+        const R gy = k * uy;
         sx += (double)gx;
         sy += (double)gy;
         const int slot = t.slot_of_pin[p];
@@ -120,9 +149,8 @@ __device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x,
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
-                                                    const R *__restrict__ y, double beta) {
+                                                    const R *__restrict__ y, double beta, int kind) {
     const int lane = threadIdx.x & 31;
-    const double two_beta = 2.0 * beta;
     const int np = s.pcnt[0];
     const int nsw = (np + 31) >> 5;
     const int tasks = nsw + t.n_big;
@@ -135,12 +163,12 @@ __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R 
             if (i >= np) continue;
             const int e = s.pnets[i];
             a = t.net_ptr[e];
-            net_grad(t, s, x, y, a, t.net_ptr[e + 1], 0, 1, two_beta, sx, sy);
+            net_grad(t, s, x, y, a, t.net_ptr[e + 1], 0, 1, beta, kind, sx, sy);
         } else {
             const int e = t.big_nets[task - nsw];
             if (!s.net_pf[e]) continue;  // warp-uniform
             a = t.net_ptr[e];
-            net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, two_beta, sx, sy);
+            net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, beta, kind, sx, sy);
             for (int o = 16; o > 0; o >>= 1) {
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
@@ -177,7 +205,8 @@ __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const d
 template <typename R>
 tdp_status loss_fwd_impl(tdp_graph *g, const R *x, const R *y, double beta, double *loss) {
     LaunchScope ls(g, KID_PP_FWD);
-    k_pp_fwd<R><<<kLossBlocks, kLossThreads, 0, g->stream>>>(g->topo, state<R>(g), x, y, beta, loss);
+    k_pp_fwd<R><<<kLossBlocks, kLossThreads, 0, g->stream>>>(g->topo, state<R>(g), x, y, beta, g->loss_kind,
+                                                              loss);
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
@@ -191,7 +220,7 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
     TDP_CUDA(cudaMemsetAsync(gy, 0, sizeof(R) * t.n_cells, g->stream));
     {
         LaunchScope ls(g, KID_PP_BWD_NET);
-        k_pp_bwd_net<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, x, y, beta);
+        k_pp_bwd_net<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind);
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
@@ -321,4 +350,13 @@ extern "C" tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const
                                       grad_scale_dev, (float *)gx_dev, (float *)gy_dev)
                : loss_bwd_impl<double>(g, (const double *)x_dev, (const double *)y_dev, beta,
                                        grad_scale_dev, (double *)gx_dev, (double *)gy_dev);
+}
+
+extern "C" tdp_status attraction_set_loss_kind(tdp_graph *g, tdp_loss_kind kind) {
+    if (!g || (kind != TDP_LOSS_QUADRATIC && kind != TDP_LOSS_HPWL && kind != TDP_LOSS_EUCLID)) {
+        set_error("attraction_set_loss_kind: NULL graph or unknown kind");
+        return TDP_ERR_INVALID;
+    }
+    g->loss_kind = (int)kind;
+    return TDP_OK;
 }

@@ -149,6 +149,15 @@ class TimingGraph:
                    self.lib.attraction_update_pairs(self.handle, float(w0), float(w1), None))
         return None
 
+    LOSS_KINDS = {"quadratic": 0, "hpwl": 1, "euclid": 2}
+
+    def attraction_set_loss_kind(self, kind: str):
+        """Pair term of the attraction loss: "quadratic" (Eq. (9), default),
+        "hpwl" or "euclid" (the ablation's alternatives)."""
+        if kind not in self.LOSS_KINDS:
+            raise ValueError(f"unknown loss kind {kind!r}")
+        _abi.check("attraction_set_loss_kind", self.lib.attraction_set_loss_kind(self.handle, self.LOSS_KINDS[kind]))
+
     def attraction_reset_pairs(self):
         _abi.check("attraction_reset_pairs", self.lib.attraction_reset_pairs(self.handle))
 

@@ -245,6 +245,47 @@ def test_loss_parity(cfg, seed, prec):
     assert rel_l2 <= (1e-5 if prec == "fp32" else 1e-12), rel_l2
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["hpwl", "euclid", "quadratic"])
+def test_loss_kind_parity(kind, prec):
+    """HPWL and linear Euclidean pair distances (the ablation's losses) against
+    the oracle; gradients compared away from pairs whose |dx|, |dy| or
+    distance is within 1e-3 um of the kink (where FP32 rounding can flip a
+    sign)."""
+    nl = netgen.generate("diff", 7)
+    G = _graph(nl, prec)
+    x, y = _pos(nl, G.dtype)
+    pins, w, in_p, wfull = _random_pairs(nl, 7)
+    if prec == "fp32":
+        w = w.astype(np.float32).astype(np.float64)
+        wfull[pins] = w
+    G.attraction_set_pairs(pins, w)
+    G.attraction_set_loss_kind(kind)
+    beta = 2.5e-5
+    xr, yr = _np(x), _np(y)
+    pp, gx_r, gy_r = oracle.loss(nl, in_p, wfull, beta, x=xr, y=yr, kind=kind)
+    loss = G.attraction_loss_fwd(x, y, beta).item()
+    gx, gy = (_np(t) for t in G.attraction_loss_bwd(x, y, beta))
+    assert loss == pytest.approx(pp, rel=1e-6 if prec == "fp32" else 1e-12)
+    pc, nptr = nl.pin_cell, nl.net_ptr
+    px = xr[pc] + nl.pin_dx.astype(np.float64)
+    py = yr[pc] + nl.pin_dy.astype(np.float64)
+    near = np.zeros(nl.n_cells, bool)
+    drv = np.repeat(nptr[:-1], np.diff(nptr))
+    dx, dy = px - px[drv], py - py[drv]
+    bad = (in_p > 0) & ((np.abs(dx) < 1e-3) | (np.abs(dy) < 1e-3) | (np.hypot(dx, dy) < 1e-3))
+    near[pc[bad]] = True
+    near[pc[drv[bad]]] = True
+    ok = ~near
+    g = np.concatenate([gx[ok], gy[ok]])
+    gr = np.concatenate([gx_r[ok], gy_r[ok]])
+    rel_l2 = np.linalg.norm(g - gr) / np.linalg.norm(gr)
+    assert rel_l2 <= (1e-5 if prec == "fp32" else 1e-12), rel_l2
+    G.attraction_set_loss_kind("quadratic")
+    assert G.attraction_loss_fwd(x, y, beta).item() == pytest.approx(
+        oracle.loss(nl, in_p, wfull, beta, x=xr, y=yr)[0], rel=1e-6 if prec == "fp32" else 1e-12)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_autograd_finite_differences(prec):
     """attraction_loss_bwd behind torch.autograd vs central differences, 1,000 cells."""

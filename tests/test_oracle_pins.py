@@ -15,6 +15,9 @@
 * Eq. (9) loss: central differences (exact for a quadratic up to rounding),
   sum of gradients = 0 (translation invariance), Euler's identity
   sum(x dPP/dx + y dPP/dy) = 2 PP (PP homogeneous of degree 2, zero offsets).
+* HPWL and linear Euclidean pair distances (the ablation of Section IV): a
+  hand-computed 3-4-5 pair, Euler's identity of degree 1, translation
+  invariance and central differences away from the kinks.
 """
 import itertools
 
@@ -291,3 +294,58 @@ def test_loss_translation_and_euler():
     assert not gxd[nl.cell_fixed > 0].any() and not gyd[nl.cell_fixed > 0].any()
     mv = nl.cell_fixed == 0
     np.testing.assert_array_equal(gxd[mv], gx[mv])
+
+
+# ---------------------------------------------------- loss variants -------
+
+def test_loss_kinds_hand_pair():
+    """One pair: driver at (0, 0), sink at (3, 4), w = 2, beta = 1.5."""
+    cells = [{"type": "FF", "x": 0.0, "y": 0.0, "rdrv": 1.0}, {"type": "FF", "x": 3.0, "y": 4.0, "rdrv": 1.0}]
+    nl = netgen.from_lists(cells, [[(0, 0.0), (1, 1.0)]])
+    in_p = np.array([0, 1], np.uint8)
+    w = np.array([0.0, 2.0])
+    x, y = np.array([0.0, 3.0]), np.array([0.0, 4.0])
+    exp = {"quadratic": (1.5 * 2 * 25, 1.5 * 2 * 2 * 3, 1.5 * 2 * 2 * 4),
+           "hpwl": (1.5 * 2 * 7, 1.5 * 2 * 1, 1.5 * 2 * 1),
+           "euclid": (1.5 * 2 * 5, 1.5 * 2 * 3 / 5, 1.5 * 2 * 4 / 5)}
+    for kind, (pp_e, gxs, gys) in exp.items():
+        pp, gx, gy = oracle.loss(nl, in_p, w, 1.5, x, y, drop_fixed=False, kind=kind)
+        assert pp == pytest.approx(pp_e, rel=1e-15)
+        np.testing.assert_allclose(gx, [-gxs, gxs], rtol=1e-15)
+        np.testing.assert_allclose(gy, [-gys, gys], rtol=1e-15)
+    # coinciding pins: distance 0, gradient 0 for the non-smooth kinds
+    for kind in ("hpwl", "euclid"):
+        pp, gx, gy = oracle.loss(nl, in_p, w, 1.5, np.zeros(2), np.zeros(2), drop_fixed=False, kind=kind)
+        assert pp == 0.0 and not gx.any() and not gy.any()
+
+
+@pytest.mark.parametrize("kind", ["hpwl", "euclid"])
+def test_loss_kinds_euler_translation_differences(kind):
+    nl = netgen.generate("tiny", 6)          # zero pin offsets
+    in_p, w = _pairs(nl, 6)
+    x, y = nl.x.astype(float), nl.y.astype(float)
+    pp, gx, gy = oracle.loss(nl, in_p, w, 1.0, x, y, drop_fixed=False, kind=kind)
+    # degree 1: sum(x dPP/dx + y dPP/dy) = PP; translation invariance
+    assert (x * gx + y * gy).sum() == pytest.approx(pp, rel=1e-10)
+    assert abs(gx.sum()) < 1e-9 * np.abs(gx).sum() and abs(gy.sum()) < 1e-9 * np.abs(gy).sum()
+    assert oracle.loss(nl, in_p, w, 1.0, x + 11.0, y - 5.0, kind=kind)[0] == pytest.approx(pp, rel=1e-12)
+    # central differences on cells whose pairs stay away from dx = 0 / dy = 0
+    h = 1e-4
+    pc, nptr = nl.pin_cell, nl.net_ptr
+    near = np.zeros(nl.n_cells, bool)
+    for e in range(nl.n_nets):
+        d = nptr[e]
+        for s_ in range(d + 1, nptr[e + 1]):
+            if in_p[s_] and (abs(x[pc[s_]] - x[pc[d]]) < 10 * h or abs(y[pc[s_]] - y[pc[d]]) < 10 * h):
+                near[pc[s_]] = near[pc[d]] = True
+    rng = np.random.default_rng(6)
+    cand = np.nonzero(~near)[0]
+    for c in rng.choice(cand, 40, replace=False):
+        for axis in (0, 1):
+            xp, yp, xm, ym = x.copy(), y.copy(), x.copy(), y.copy()
+            (xp if axis == 0 else yp)[c] += h
+            (xm if axis == 0 else ym)[c] -= h
+            fd = (oracle.loss(nl, in_p, w, 1.0, xp, yp, kind=kind)[0] -
+                  oracle.loss(nl, in_p, w, 1.0, xm, ym, kind=kind)[0]) / (2 * h)
+            g = (gx if axis == 0 else gy)[c]
+            assert fd == pytest.approx(g, rel=1e-5, abs=1e-9 * pp / h)
