@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--roofline-kernel", default=ROOFLINE_KERNEL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stages", action="store_true", help="also time each entry point (diagnostic)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-on-GPU comparison run")
     return ap.parse_args()
 
 
@@ -362,6 +363,7 @@ def run_ours(args):
     stages = None
     if args.stages:
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
+    fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
 
     # -------------------------------------------------------------- report --
     result = None
@@ -403,6 +405,8 @@ def run_ours(args):
         }
         if stages:
             result["stages_ms"] = stages
+        if fp64:
+            result["fp64_gpu"] = fp64
         if world == 1 and not args.no_cpu_baseline:
             pos = (xs[0].cpu().numpy(), ys[0].cpu().numpy())
             result["cpu_baseline"] = cpu_baseline(nl, cfg, T, pos, sample_frac=0.5, offset=0)
@@ -411,6 +415,44 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def fp64_run(nl, xs, ys, T, K, dev, stream, wns32, tns32, steps=20):
+    """The same timing iteration on an FP64 graph (same kernels in double
+    precision): throughput, and the FP32 run's WNS / TNS against it."""
+    import torch
+    from paper_2503_11674_b300 import TimingGraph
+    G = TimingGraph(nl, "fp64", device=dev)
+    n = nl.n_cells
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
+    gx = torch.empty(n, dtype=torch.float64, device=dev)
+    gy = torch.empty(n, dtype=torch.float64, device=dev)
+    x64, y64 = xs.double(), ys.double()
+
+    def step(k):
+        x, y = x64[k % N_POS_SETS], y64[k % N_POS_SETS]
+        G.sta_propagate(x, y, T, sync=False)
+        G.extract_critical_paths(-1, K, False, sync=False)
+        G.attraction_update_pairs(W0, W1, sync=False)
+        G.attraction_loss_fwd(x, y, BETA, out=loss)
+        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+
+    for k in range(3):
+        step(k)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        step(3 + k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    wns64, tns64 = G.sta_propagate(x64[0], y64[0], T)
+    del G
+    return {"value": round(1000.0 / ms, 2), "unit": UNIT, "ms_per_step": round(ms, 4), "steps": steps,
+            "wns_ps": wns64, "tns_ps": tns64,
+            "fp32_wns_rel_diff": abs(wns32 - wns64) / max(abs(wns64), 1e-30),
+            "fp32_tns_rel_diff": abs(tns32 - tns64) / max(abs(tns64), 1e-30)}
 
 
 def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
