@@ -148,20 +148,22 @@ def workload_desc(cfg, nl):
 
 # ------------------------------------------------------ algorithmic bytes --
 
-# A level sweep is one CUDA-graph replay of one kernel per logic level; its
-# "launch" for the roofline is the whole replay.
-LAUNCH_UNIT = {"fwd_sweep": "one forward level sweep (graph replay: one kernel per logic level)",
-               "bwd_sweep": "one backward level sweep plus WNS/TNS (graph replay)"}
+# A level sweep is one cooperative launch over all logic levels (or, with
+# TDP_LEVEL_GRAPHS=1, one CUDA-graph replay of a kernel per level); its
+# "launch" for the roofline is the whole sweep.
+LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single cooperative launch)",
+               "bwd_sweep": "one backward sweep over all logic levels plus WNS/TNS (a single cooperative launch)"}
 
 # DRAM bytes (read + write) per launch from an ncu capture of the 1.2M-cell
-# workload, with the SHA-256 of the kernel source they were taken on; the
-# figure is reported only while that source is unchanged.
+# workload, with the SHA-256 of the sources the kernel was built from when it
+# was taken; the figure is reported only while those sources are unchanged.
+SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
-    "fwd_sweep": {"bytes": 470534400, "source": "paper_2503_11674_b300/csrc/tdp_sta.cu",
-                  "sha256": "05981538222f1322d3f4f58a92b3280feaff54fea9c21f1042ef11b8c1293b87",
+    "fwd_sweep": {"bytes": 471028480, "sources": SWEEP_SOURCES,
+                  "sha256": "e80a3679614024bad7457193c3d265cf42d096ebf529043ed21e6187119c9585",
                   "profile": "profiles/fwd_sweep_1.2M.md"},
-    "bwd_sweep": {"bytes": 670304768, "source": "paper_2503_11674_b300/csrc/tdp_sta.cu",
-                  "sha256": "05981538222f1322d3f4f58a92b3280feaff54fea9c21f1042ef11b8c1293b87",
+    "bwd_sweep": {"bytes": 667237120, "sources": SWEEP_SOURCES,
+                  "sha256": "e80a3679614024bad7457193c3d265cf42d096ebf529043ed21e6187119c9585",
                   "profile": "profiles/bwd_sweep_1.2M.md"},
 }
 
@@ -171,9 +173,12 @@ def profiled_traffic(kernel: str):
     rec = PROFILED_TRAFFIC.get(kernel)
     if rec is None:
         return None
-    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
-            return None
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec["sha256"]:
+        return None
     return rec["bytes"]
 
 
