@@ -8,6 +8,8 @@
  *   extract_critical_paths   Section III-B, report_timing_endpoint(n, k)
  *   attraction_update_pairs  Section III-D, Eq. (w_ij)
  *   attraction_loss_fwd/bwd  Eq. (9) and the PP sum of Section III-D
+ * and report_timing (Section III-B, Table I) is the global extraction that
+ * report_timing_endpoint is compared against.
  *
  * Conventions shared by every entry point:
  *  - All pointers are plain C pointers.  "_dev" arguments are CUDA device
@@ -165,6 +167,29 @@ TDP_API tdp_status sta_get_net_delays(tdp_graph *g, void *tnet_dev, void *cload_
  */
 TDP_API tdp_status extract_critical_paths(tdp_graph *g, int32_t n_endpoints, int32_t K,
                                   int32_t keep_nonneg, int64_t *n_paths_out);
+
+/*
+ * report_timing(n) (Section III-B, Table I; OpenTimer's semantics): the n
+ * worst endpoints, the n worst paths of each, and of those n^2 paths the n
+ * of lowest slack -- which are the n lowest-slack startpoint-to-endpoint
+ * paths of the whole design.  With keep_nonneg == 0 only paths of negative
+ * slack are reported (fewer than n when the design has fewer); with
+ * keep_nonneg != 0 every endpoint takes part whatever its slack.  The
+ * paths are reported worst first; equal-slack paths are ordered
+ * deterministically by the search, not by pin sequence.  n >= 0 (n = 0:
+ * no path).  The search holds one record per candidate path; its memory
+ * grows with n and with the number of near-critical paths of the design.
+ * It replaces the last extraction: sta_get_paths_size / sta_get_paths
+ * return these paths (viol_dev: the failing endpoints, as for
+ * extract_critical_paths) and attraction_update_pairs takes them as its
+ * path set.  The paths stay valid until the next extraction or
+ * sta_propagate.  The search reads its sizes back between rounds, so this
+ * call synchronises the stream.  n_paths_out: host int64 or NULL.
+ * Errors: TDP_ERR_INVALID for n < 0; TDP_ERR_STATE before sta_propagate;
+ * TDP_ERR_OOM when the search needs more than 2^31 - 1 path records or
+ * the device memory for them.
+ */
+TDP_API tdp_status report_timing(tdp_graph *g, int32_t n, int32_t keep_nonneg, int64_t *n_paths_out);
 
 /*
  * Sizes of the last extraction (synchronises): number of failing endpoints,

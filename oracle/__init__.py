@@ -154,6 +154,44 @@ def topk(nl, timing: dict, n_endpoints: int = -1, K: int = 1, keep_nonneg: bool 
     return out
 
 
+# cell types of the netlist interface
+_FF, _PO = 1, 3
+
+
+def report_timing(nl, timing: dict, n: int, keep_nonneg: bool = False) -> dict:
+    """report_timing(n) as Section III-B describes OpenTimer's command (the
+    one Table I measures): take the n endpoints of lowest slack, the n
+    lowest-slack paths of each, and report the n paths of lowest slack among
+    those n x n, worst first.
+
+    Without ``keep_nonneg`` only failing endpoints and paths of negative slack
+    take part.  Equal slacks are ordered as in ``topk``, by the pin sequence
+    read from the endpoint: by endpoint pin, then by rank at the endpoint.
+    Returns ``ep, rank, slack, pin_ptr, pins`` of the reported paths.
+    """
+    n = int(n)
+    if n < 0:
+        raise ValueError("report_timing: n < 0")
+    ct = np.asarray(nl.cell_type)[np.asarray(nl.pin_cell)]
+    eps = np.nonzero((np.asarray(nl.pin_dir) == 0) & ((ct == _FF) | (ct == _PO)))[0]
+    es = timing["T"] - np.asarray(timing["arr"])[eps]
+    if not keep_nonneg:
+        eps, es = eps[es < 0.0], es[es < 0.0]
+    worst = eps[np.lexsort((eps, es))][:n]
+    empty = {"ep": np.zeros(0, np.int32), "rank": np.zeros(0, np.int32), "slack": np.zeros(0),
+             "pin_ptr": np.zeros(1, np.int64), "pins": np.zeros(0, np.int32)}
+    if n == 0 or len(worst) == 0:
+        return empty
+    P = topk(nl, timing, -1, n, keep_nonneg, endpoints=worst)
+    sel = np.lexsort((P["rank"], P["ep"], P["slack"]))[:n]
+    lens = np.diff(P["pin_ptr"])[sel]
+    ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pins = np.concatenate([P["pins"][P["pin_ptr"][k]:P["pin_ptr"][k + 1]] for k in sel]) if len(sel) \
+        else np.zeros(0, np.int32)
+    return {"ep": P["ep"][sel], "rank": P["rank"][sel], "slack": P["slack"][sel], "pin_ptr": ptr,
+            "pins": pins.astype(np.int32)}
+
+
 def update_pairs(nl, paths: dict, wns: float, w0: float, w1: float, in_p=None, w=None):
     """Eq. (w_ij): update the persistent pin-pair set P (by sink pin) and weights."""
     lib = _load()

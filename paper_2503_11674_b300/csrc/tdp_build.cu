@@ -445,7 +445,7 @@ namespace tdp {
 
 const char *const kKernelNames[KID_COUNT] = {"net_rc",    "fwd_sweep",   "bwd_sweep", "viol_sort",
                                               "topk",      "pair_walk",   "pair_finish", "pp_fwd",
-                                              "pp_bwd_net", "pp_bwd_cell"};
+                                              "pp_bwd_net", "pp_bwd_cell", "rt_expand"};
 
 static cudaEvent_t prof_event(tdp_graph *g) {
     if (!g->prof_free.empty()) {
@@ -554,6 +554,7 @@ extern "C" void sta_destroy(tdp_graph *g) {
         cudaEventDestroy(pr.second);
     }
     for (cudaEvent_t e : g->prof_free) cudaEventDestroy(e);
+    rt_free(g);
     for (void *p : g->allocs) cudaFree(p);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;

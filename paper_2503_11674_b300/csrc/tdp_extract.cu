@@ -27,11 +27,6 @@
 
 namespace tdp {
 
-struct SortItem {
-    unsigned long long key;  // slack bits, order-preserving as an unsigned integer
-    unsigned long long pin;
-};
-
 __device__ __forceinline__ bool item_less(const SortItem &a, const SortItem &b) {
     return a.key < b.key || (a.key == b.key && a.pin < b.pin);
 }
@@ -353,7 +348,7 @@ static tdp_status ensure_path_buffers(tdp_graph *g, int K) {
 }
 
 // sort the *nviol items of a (at most n) by (key, pin); the result ends in a
-static void sort_items(SortItem *&a, SortItem *&b, const int *nviol, int n, cudaStream_t st) {
+void sort_items(SortItem *&a, SortItem *&b, const int *nviol, int n, cudaStream_t st) {
     k_tile_sort<<<div_up(n, kTile), 1024, 0, st>>>(a, nviol);
     for (int run = kTile; run < n; run *= 2) {
         k_merge_pass<<<div_up(n, 256), 256, 0, st>>>(a, b, nviol, run);
@@ -408,6 +403,31 @@ static tdp_status sort_viol(tdp_graph *g) {
     return rc;
 }
 
+// failing endpoints sorted by (slack, pin) into viol (nviol cleared first)
+template <typename R>
+tdp_status sort_failing(tdp_graph *g) {
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    cudaStream_t st = g->stream;
+    TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
+    if (t.n_ep > 0) {
+        SortItem *a = reinterpret_cast<SortItem *>(s.sort_a);
+        SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
+        int passes = 0;
+        for (int run = kTile; run < t.n_ep; run *= 2) ++passes;
+        LaunchScope ls(g, KID_VIOL_SORT, 3 + passes);
+        k_viol_collect<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s, a);
+        sort_items(a, b, s.nviol, t.n_ep, st);
+        k_sort_finish<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
+    }
+    g->viol_sorted = true;
+    TDP_LAUNCH_CHECK();
+    return TDP_OK;
+}
+
+template tdp_status sort_failing<float>(tdp_graph *);
+template tdp_status sort_failing<double>(tdp_graph *);
+
 template <typename R>
 tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     Topo &t = g->topo;
@@ -415,8 +435,6 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     cudaStream_t st = g->stream;
     TDP_TRY(ensure_path_buffers<R>(g, K));
     // 1. failing endpoints sorted by (slack, pin)
-    SortItem *a = reinterpret_cast<SortItem *>(s.sort_a);
-    SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
     TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
     TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
     if (t.n_ep > 0 && n_endpoints < 0) {
@@ -427,13 +445,7 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
         compact_u8(g, s.ep_flag, 1, t.n_ep, t.ep, s.viol, s.nviol);
         g->viol_sorted = false;
     } else if (t.n_ep > 0) {
-        int passes = 0;
-        for (int run = kTile; run < t.n_ep; run *= 2) ++passes;
-        LaunchScope ls(g, KID_VIOL_SORT, 3 + passes);
-        k_viol_collect<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s, a);
-        sort_items(a, b, s.nviol, t.n_ep, st);
-        k_sort_finish<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(s, a);
-        g->viol_sorted = true;
+        TDP_TRY(sort_failing<R>(g));
     }
     TDP_LAUNCH_CHECK();
     // 2. sidetrack lists: the next sweeps build K - 1 entries per node; if the
@@ -463,31 +475,6 @@ template tdp_status extract_impl<float>(tdp_graph *, int, int, int);
 template tdp_status extract_impl<double>(tdp_graph *, int, int, int);
 
 // ---------------------------------------------------------- materialise ---
-
-// Walk one extracted path from its endpoint back to its startpoint, calling
-// visit(pin, is_sink) for every pin in that order.
-template <typename R, typename F>
-__device__ __forceinline__ void walk_path(const Topo &t, const State<R> &s, int ep,
-                                          const int *sides, int nsides, F &&visit) {
-    visit(ep, true);
-    int e = t.pin_net[ep];
-    int j = nsides - 1;  // sides[] holds the deepest sidetrack first
-    for (;;) {
-        visit(t.net_ptr[e], false);
-        const int2 pr = s.pred[e];
-        int pi = pr.x;
-        if (pi < 0) break;
-        int nx;
-        if (j >= 0 && t.sink_onet[sides[j]] == e) {
-            pi = sides[j--];
-            nx = t.pin_net[pi];
-        } else {
-            nx = pr.y;
-        }
-        visit(pi, true);
-        e = nx;
-    }
-}
 
 template <typename R>
 __global__ void k_path_lens(State<R> s, int K, int n_use, const int64_t *base, int32_t *lens) {
@@ -532,6 +519,15 @@ tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, in
     State<R> &s = state<R>(g);
     const Topo &t = g->topo;
     cudaStream_t st = g->stream;
+    if (g->rt_mode) {
+        if (viol) {
+            int nv = 0;
+            TDP_CUDA(cudaMemcpyAsync(&nv, s.nviol, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TDP_CUDA(cudaStreamSynchronize(st));
+            if (nv > 0) TDP_CUDA(cudaMemcpyAsync(viol, s.viol, sizeof(int32_t) * nv, cudaMemcpyDeviceToDevice, st));
+        }
+        return rt_get_paths<R>(g, ep, slack, pin_ptr, pins);
+    }
     TDP_TRY(sort_viol<R>(g));
     int nv = 0;
     long long np = 0;
@@ -594,6 +590,7 @@ extern "C" tdp_status extract_critical_paths(tdp_graph *g, int32_t n_endpoints, 
         return TDP_ERR_STATE;
     }
     keep_nonneg = keep_nonneg ? 1 : 0;
+    g->rt_mode = false;
     tdp_status st = g->prec == TDP_FP32 ? extract_impl<float>(g, n_endpoints, K, keep_nonneg)
                                         : extract_impl<double>(g, n_endpoints, K, keep_nonneg);
     if (st != TDP_OK) return st;
@@ -621,6 +618,10 @@ static tdp_status paths_size_impl(tdp_graph *g, int32_t *nv_out, int64_t *np_out
     TDP_CUDA(cudaMemcpyAsync(&np, s.n_paths, sizeof(long long), cudaMemcpyDeviceToHost, st));
     TDP_CUDA(cudaStreamSynchronize(st));
     if (nv_out) *nv_out = nv;
+    if (g->rt_mode) {
+        if (np_out) *np_out = g->rt_n_out;
+        return npin_out ? rt_paths_size<R>(g, npin_out) : TDP_OK;
+    }
     if (np_out) *np_out = np;
     if (npin_out) {
         const int n_use = std::min(nv, g->n_endpoints < 0 ? INT_MAX : g->n_endpoints);

@@ -61,7 +61,7 @@ constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 // the WNS / TNS reduction.
 enum KernelId {
     KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
-    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_COUNT
+    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -342,6 +342,18 @@ struct Levels {
     std::vector<int32_t> bw_s_lo, bw_s_n, bw_b_lo, bw_b_n;
 };
 
+// Nodes of the report_timing(n) prefix tree, one path each (structure of
+// arrays): parent node (-1 for an endpoint's worst path), the sidetrack pin
+// that the node adds to its parent (-1: none), endpoint, pins on the path,
+// sidetracks on the path, cost (slack gained over the endpoint's worst path)
+// and the order-preserving bits of the path slack.
+template <typename R>
+struct RtNodes {
+    int32_t *par = nullptr, *side = nullptr, *ep = nullptr, *len = nullptr, *nsd = nullptr;
+    R *cost = nullptr;
+    unsigned long long *key = nullptr;
+};
+
 template <typename R>
 struct State {
     using A = typename Acc<R>::T;
@@ -391,6 +403,13 @@ struct State {
     R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y); zero outside P
     double *loss_part = nullptr;
     unsigned *loss_count = nullptr;
+    // report_timing(n): the kept prefix-tree nodes, the report (node indices,
+    // worst first) and each reported path's sidetracks, deepest first, at
+    // rt_side_off[q] (grown on demand, freed by rt_free)
+    RtNodes<R> rt;
+    int32_t *rt_out = nullptr;
+    int64_t *rt_side_off = nullptr;
+    int32_t *rt_sides = nullptr;
 };
 
 }  // namespace tdp
@@ -413,6 +432,13 @@ struct tdp_graph {
     // sidetrack lists are built by the forward sweep: list_L entries per node
     // (the K - 1 of the last extraction), lists_valid_L of them are current
     int list_L = 0, lists_valid_L = 0;
+    // the last extraction was report_timing(n): rt_n_out paths in the rt
+    // buffers of the state (else report_timing_endpoint's per-endpoint records)
+    bool rt_mode = false;
+    int64_t rt_n_out = 0, rt_n_sides = 0;
+    int64_t rt_cap = 0, rt_out_cap = 0, rt_soff_cap = 0, rt_sides_cap = 0;  // buffer capacities
+    int rt_rounds = 0;                                     // expansion rounds of the last report
+    int64_t rt_nodes = 0;                                  // nodes the last report kept
     // level sweeps: one cooperative launch each (single_launch), else CUDA
     // graphs of one kernel per level
     bool single_launch = true;
@@ -463,6 +489,56 @@ tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, in
                           int32_t *pins);
 template <typename R>
 tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1);
+template <typename R>
+tdp_status report_impl(tdp_graph *g, int64_t n, int keep_nonneg);
+template <typename R>
+tdp_status rt_get_paths(tdp_graph *g, int32_t *ep, R *slack, int64_t *pin_ptr, int32_t *pins);
+template <typename R>
+tdp_status rt_paths_size(tdp_graph *g, int64_t *npin_out);
+// the pair update's walk over the reported paths (report_timing mode)
+template <typename R>
+void rt_pair_walk(tdp_graph *g);
+// frees the report_timing buffers of both states
+void rt_free(tdp_graph *g);
+
+// failing endpoints sorted by (slack, pin) into viol / nviol of the state
+template <typename R>
+tdp_status sort_failing(tdp_graph *g);
+
+// (key, index) items; sort_items sorts the first *count (at most n) of a by
+// (key, pin) and leaves the result in a (a and b are swapped as needed)
+struct SortItem {
+    unsigned long long key;  // order-preserving bits of a value
+    unsigned long long pin;
+};
+void sort_items(SortItem *&a, SortItem *&b, const int *count, int n, cudaStream_t st);
+
+// Walk one extracted path from its endpoint back to its startpoint, calling
+// visit(pin, is_sink) for every pin in that order.  The path leaves the
+// worst-input chain at its sidetracks, sides[nsides - 1] (nearest the
+// endpoint) first, sides[0] (deepest) last.
+template <typename R, typename F>
+__device__ __forceinline__ void walk_path(const Topo &t, const State<R> &s, int ep, const int *sides,
+                                          int nsides, F &&visit) {
+    visit(ep, true);
+    int e = t.pin_net[ep];
+    int j = nsides - 1;
+    for (;;) {
+        visit(t.net_ptr[e], false);
+        const int2 pr = s.pred[e];
+        int pi = pr.x;
+        if (pi < 0) break;
+        int nx;
+        if (j >= 0 && t.sink_onet[sides[j]] == e) {
+            pi = sides[j--];
+            nx = t.pin_net[pi];
+        } else {
+            nx = pr.y;
+        }
+        visit(pi, true);
+        e = nx;
+    }
+}
 template <typename R>
 tdp_status loss_fwd_impl(tdp_graph *g, const R *x, const R *y, double beta, double *loss);
 template <typename R>

@@ -249,7 +249,9 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
     const int n_cap = g->n_endpoints < 0 ? INT_MAX : g->n_endpoints;
-    if (t.n_ep > 0) {
+    if (g->rt_mode) {
+        rt_pair_walk<R>(g);
+    } else if (t.n_ep > 0) {
         LaunchScope ls(g, KID_PAIR_WALK);
         int KP = 1;
         while (KP < g->K) KP *= 2;

@@ -115,6 +115,14 @@ class TimingGraph:
                                                    int(bool(keep_nonneg)), None))
         return None
 
+    def report_timing(self, n: int, keep_nonneg: bool = False) -> int:
+        """report_timing(n): the n lowest-slack paths of the design, worst first;
+        returns their number (the call synchronises)."""
+        npth = C.c_int64()
+        _abi.check("report_timing", self.lib.report_timing(self.handle, int(n), int(bool(keep_nonneg)),
+                                                           C.byref(npth)))
+        return npth.value
+
     def sta_get_paths_size(self):
         nv, npth, npin = C.c_int32(), C.c_int64(), C.c_int64()
         _abi.check("sta_get_paths_size", self.lib.sta_get_paths_size(self.handle, C.byref(nv),

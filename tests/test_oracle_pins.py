@@ -349,3 +349,87 @@ def test_loss_kinds_euler_translation_differences(kind):
                   oracle.loss(nl, in_p, w, 1.0, xm, ym, kind=kind)[0]) / (2 * h)
             g = (gx if axis == 0 else gy)[c]
             assert fd == pytest.approx(g, rel=1e-5, abs=1e-9 * pp / h)
+
+
+# ------------------------------------------------------- report_timing(n) ----
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 5])
+@pytest.mark.parametrize("keep_nonneg", [False, True])
+@pytest.mark.parametrize("n", [1, 6, 45, 100_000])
+def test_report_timing_equals_brute_force(seed, keep_nonneg, n):
+    """report_timing(n): the n lowest-slack paths over every endpoint of the
+    design, brute force over all paths (n = 100000 exceeds their number)."""
+    nl = netgen.generate(SMALL, seed)
+    T = oracle.clock_period(nl, SMALL.t_factor)
+    tm = oracle.sta(nl, T=T)
+    arcs, launch = _in_arcs(nl, tm)
+    bf = []
+    for ep in _endpoints(nl):
+        bf += [(T - d, pins) for d, pins in _all_paths(arcs, launch, int(ep))]
+    assert len(bf) < 200_000
+    bf.sort(key=lambda t: (t[0], t[1][::-1]))
+    if not keep_nonneg:
+        bf = [t for t in bf if t[0] < 0]
+    exp = bf[:n]
+    R = oracle.report_timing(nl, tm, n, keep_nonneg)
+    mine = [(R["slack"][k], R["pins"][R["pin_ptr"][k]:R["pin_ptr"][k + 1]].tolist()) for k in range(len(R["ep"]))]
+    assert len(mine) == len(exp)
+    tol = 1e-9
+    np.testing.assert_allclose([m[0] for m in mine], [e[0] for e in exp], atol=tol)
+    for m, e in zip(mine, exp):
+        assert m[1][-1] == R["ep"][mine.index(m)]
+        near = [t[1] for t in bf if abs(t[0] - e[0]) <= tol]
+        if len(near) == 1:
+            assert m[1] == e[1]
+        else:
+            assert m[1] in near
+
+
+def test_report_timing_small_cases():
+    nl = netgen.generate(SMALL, 4)
+    T = oracle.clock_period(nl, SMALL.t_factor)
+    tm = oracle.sta(nl, T=T)
+    assert len(oracle.report_timing(nl, tm, 0)["ep"]) == 0
+    # n = 1: the worst path of the most critical endpoint
+    R1 = oracle.report_timing(nl, tm, 1)
+    P1 = oracle.topk(nl, tm, 1, 1)
+    assert R1["ep"].tolist() == P1["ep"].tolist()
+    assert R1["pins"].tolist() == P1["pins"].tolist()
+    # nothing fails at a large clock period, unless non-negative paths are kept
+    tm2 = oracle.sta(nl, T=10 * T)
+    assert len(oracle.report_timing(nl, tm2, 50)["ep"]) == 0
+    assert len(oracle.report_timing(nl, tm2, 50, keep_nonneg=True)["ep"]) == 50
+    with pytest.raises(ValueError):
+        oracle.report_timing(nl, tm, -1)
+
+
+def test_report_timing_spreads_over_endpoints():
+    """Eight one-path chains PI -> buffer -> PO of different lengths and one
+    PO behind a 3-input cell (three paths): at T = 0 every path fails, and
+    report_timing(n) must list the n lowest slacks over all nine endpoints --
+    n distinct endpoints when the chains are the most critical."""
+    cells, nets = [], []
+    for i in range(8):
+        L = 100.0 * (i + 1)
+        b = len(cells)
+        cells += [{"type": "PI", "x": 0.0, "y": 50.0 * i, "rdrv": 1.0},
+                  {"type": "COMB", "x": L, "y": 50.0 * i, "rdrv": 1.0},
+                  {"type": "PO", "x": 2 * L, "y": 50.0 * i}]
+        nets += [[(b, 0.0), (b + 1, 1.0)], [(b + 1, 0.0), (b + 2, 1.0)]]
+    b = len(cells)
+    cells += [{"type": "PI", "x": 0.0, "y": -50.0 * k - 50.0, "rdrv": 1.0} for k in range(3)]
+    cells += [{"type": "COMB", "x": 10.0, "y": -100.0, "rdrv": 1.0}, {"type": "PO", "x": 20.0, "y": -100.0}]
+    nets += [[(b + k, 0.0), (b + 3, 1.0)] for k in range(3)]
+    nets += [[(b + 3, 0.0), (b + 4, 1.0)]]
+    nl = netgen.from_lists(cells, nets)
+    tm = oracle.sta(nl, T=0.0)
+    arcs, launch = _in_arcs(nl, tm)
+    bf = sorted((-d, pins[-1]) for ep in _endpoints(nl) for d, pins in _all_paths(arcs, launch, int(ep)))
+    assert len(bf) == 11
+    for n in (1, 4, 8, 11):
+        R = oracle.report_timing(nl, tm, n)
+        assert len(R["ep"]) == n
+        np.testing.assert_allclose(R["slack"], [t[0] for t in bf[:n]], atol=1e-9)
+        assert sorted(R["ep"].tolist()) == sorted(t[1] for t in bf[:n])
+    # the 8 worst paths end at more than 4 different endpoints
+    assert len(set(t[1] for t in bf[:8])) > 4
