@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--roofline-kernel", default=ROOFLINE_KERNEL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stages", action="store_true", help="also time each entry point (diagnostic)")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip Table I's comparison of report_timing(n) with report_timing_endpoint(n, k)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-on-GPU comparison run")
     return ap.parse_args()
 
@@ -395,6 +397,7 @@ def run_ours(args):
     stages = None
     if args.stages:
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
+    t1 = table1(G, xs[0], ys[0], T) if not args.no_table1 else None
     fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
 
     # -------------------------------------------------------------- report --
@@ -437,6 +440,8 @@ def run_ours(args):
         }
         if stages:
             result["stages_ms"] = stages
+        if t1:
+            result["table1"] = t1
         if fp64:
             result["fp64_gpu"] = fp64
         if world == 1 and not args.no_cpu_baseline:
@@ -531,6 +536,47 @@ def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
     G.attraction_set_loss_kind("quadratic")
     out["loss_kinds"] = kinds
     return out
+
+
+def table1(G, x, y, T, reps=3):
+    """Table I's comparison on this workload: report_timing(n) with n = the
+    failing endpoints and 10 n, against report_timing_endpoint(n, 1) and
+    (n, 10).  Per command: paths, distinct endpoints, distinct pin pairs (the
+    pair set after one update from an empty set), and the time of the call
+    (median of `reps`, synchronised on both sides)."""
+    import torch
+    G.sta_propagate(x, y, T)
+    G.extract_critical_paths(-1, 1, False)
+    nv = G.sta_get_paths_size()[0]
+    cmds = [(f"report_timing({nv})", lambda: G.report_timing(nv), True),
+            (f"report_timing({10 * nv})", lambda: G.report_timing(10 * nv), True),
+            (f"report_timing_endpoint({nv},1)", lambda: G.extract_critical_paths(nv, 1, False), False),
+            (f"report_timing_endpoint({nv},10)", lambda: G.extract_critical_paths(nv, 10, False), False)]
+    rows = []
+    for name, fn, global_search in cmds:
+        times, n_paths, exp_ms = [], 0, None
+        for r in range(reps):
+            if global_search and r == reps - 1:
+                G.tdp_profile_kernel("rt_expand")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n_paths = fn()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            if global_search and r == reps - 1:
+                exp_ms = G.tdp_profile_read()
+                G.tdp_profile_kernel(None)
+        P = G.sta_get_paths()
+        n_ep = int(torch.unique(P["ep"]).numel())
+        G.attraction_reset_pairs()
+        n_pairs = G.attraction_update_pairs(W0, W1)
+        row = {"command": name, "paths": int(n_paths), "endpoints": n_ep, "pin_pairs": int(n_pairs),
+               "ms": round(1e3 * sorted(times)[len(times) // 2], 3)}
+        if exp_ms is not None:
+            row["rt_expand"] = {"launches": exp_ms[0], "ms": round(exp_ms[1], 3)}
+        rows.append(row)
+    G.attraction_reset_pairs()
+    return {"failing_endpoints": int(nv), "rows": rows}
 
 
 # ------------------------------------------------------------ CPU oracle --
