@@ -317,6 +317,7 @@ def run_ours(args):
     e0.record(stream)
     for k in range(args.steps):
         step(args.warmup + k)
+    G.sta_join()  # the last step's backward sweep (on the library's second stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -481,6 +482,7 @@ def fp64_run(nl, xs, ys, T, K, dev, stream, wns32, tns32, steps=20):
     e0.record(stream)
     for k in range(steps):
         step(3 + k)
+    G.sta_join()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
@@ -503,6 +505,7 @@ def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         ev[0].record(stream)
         G.sta_propagate(x, y, T, sync=False)
+        G.sta_join()  # the whole STA, backward sweep included
         ev[1].record(stream)
         G.extract_critical_paths(-1, K, False, sync=False)
         ev[2].record(stream)

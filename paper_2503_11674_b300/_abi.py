@@ -22,7 +22,7 @@ EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_g
            "attraction_update_pairs", "attraction_reset_pairs", "attraction_set_pairs",
            "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
            "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
-           "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "attraction_set_loss_kind", "report_timing",
+           "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "attraction_set_loss_kind", "report_timing", "sta_join",
            "tdp_last_error"]
 
 
@@ -76,6 +76,7 @@ def load() -> C.CDLL:
         "tdp_selftest_grid_wait": [C.c_double, P],
         "attraction_set_loss_kind": [P, C.c_int],
         "report_timing": [P, I32, I32, P],
+        "sta_join": [P],
         "tdp_last_error": [],
     }
     for name, args in sig.items():

@@ -53,8 +53,8 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     TDP_TRY(dalloc(g, &s.red_part, 2 * ((size_t)t.n_ep / kRedChunk + 1)));
     TDP_TRY(dalloc(g, &s.red_count, 1));
     TDP_CUDA(cudaMemset(s.red_count, 0, sizeof(unsigned)));
-    TDP_TRY(dalloc(g, &s.gsync, 2));
-    TDP_CUDA(cudaMemset(s.gsync, 0, 2 * sizeof(unsigned)));
+    TDP_TRY(dalloc(g, &s.gsync, 4));
+    TDP_CUDA(cudaMemset(s.gsync, 0, 4 * sizeof(unsigned)));
     TDP_CUDA(cudaMemset(s.tnet, 0, sizeof(R) * t.n_pins));
     // static per-net path data of startpoints: no worst input, chain length 1
     std::vector<int32_t> pred(t.n_nets, -1), plen(t.n_nets, 1);
@@ -432,6 +432,11 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
         TDP_TRY(upload(g, &t.lv_slot, slot));
     }
     TDP_TRY(upload(g, &t.ep, ep));
+    {
+        std::vector<int2> ep_pd(ep.size());
+        for (size_t i = 0; i < ep.size(); ++i) ep_pd[i] = make_int2(ep[i], d->net_ptr[pin_net[ep[i]]]);
+        TDP_TRY(upload(g, &t.ep_pd, ep_pd));
+    }
     TDP_TRY(upload(g, &t.cp_ptr, cp_ptr));
     TDP_TRY(upload(g, &t.cp, cp));
     TDP_TRY(upload(g, &t.slot_of_pin, slot));
@@ -445,7 +450,7 @@ namespace tdp {
 
 const char *const kKernelNames[KID_COUNT] = {"net_rc",    "fwd_sweep",   "bwd_sweep", "viol_sort",
                                               "topk",      "pair_walk",   "pair_finish", "pp_fwd",
-                                              "pp_bwd_net", "pp_bwd_cell", "rt_expand"};
+                                              "pp_bwd_net", "pp_bwd_cell", "rt_expand", "ep_wns"};
 
 static cudaEvent_t prof_event(tdp_graph *g) {
     if (!g->prof_free.empty()) {
@@ -458,11 +463,12 @@ static cudaEvent_t prof_event(tdp_graph *g) {
     return e;
 }
 
-LaunchScope::LaunchScope(tdp_graph *g_, KernelId id, int n_kernels) : g(g_), on(g_->prof_id == id) {
+LaunchScope::LaunchScope(tdp_graph *g_, KernelId id, int n_kernels, cudaStream_t st_)
+    : g(g_), on(g_->prof_id == id), st(st_ ? st_ : g_->stream) {
     g->n_launch += n_kernels;
     if (on) {
         a = prof_event(g);
-        if (a) cudaEventRecord(a, g->stream);
+        if (a) cudaEventRecord(a, st);
     }
 }
 
@@ -470,8 +476,14 @@ LaunchScope::~LaunchScope() {
     if (!on || !a) return;
     cudaEvent_t b = prof_event(g);
     if (!b) return;
-    cudaEventRecord(b, g->stream);
+    cudaEventRecord(b, st);
     g->prof_pending.emplace_back(a, b);
+}
+
+void join_side(tdp_graph *g) {
+    if (!g->bwd_pending) return;
+    cudaStreamWaitEvent(g->stream, g->ev_bwd, 0);
+    g->bwd_pending = false;
 }
 
 }  // namespace tdp
@@ -479,6 +491,7 @@ LaunchScope::~LaunchScope() {
 namespace tdp {
 
 tdp_status check_sync_status(tdp_graph *g) {
+    join_side(g);  // the status word covers the backward sweep too
     unsigned *w = g->prec == TDP_FP32 ? g->s32.gsync : g->s64.gsync;
     unsigned h = 0;
     TDP_CUDA(cudaMemcpyAsync(&h, w + 1, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -531,6 +544,7 @@ extern "C" tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, doub
         return TDP_ERR_INVALID;
     }
     TDP_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->side) TDP_CUDA(cudaStreamSynchronize(g->side));
     double total = 0.0;
     for (auto &pr : g->prof_pending) {
         float ms = 0.0f;
@@ -547,6 +561,7 @@ extern "C" tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, doub
 
 extern "C" void sta_destroy(tdp_graph *g) {
     if (!g) return;
+    if (g->side) cudaStreamSynchronize(g->side);
     if (g->fwd_graph) cudaGraphExecDestroy(g->fwd_graph);
     if (g->bwd_graph) cudaGraphExecDestroy(g->bwd_graph);
     for (auto &pr : g->prof_pending) {
@@ -557,6 +572,9 @@ extern "C" void sta_destroy(tdp_graph *g) {
     rt_free(g);
     for (void *p : g->allocs) cudaFree(p);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_fwd) cudaEventDestroy(g->ev_fwd);
+    if (g->ev_bwd) cudaEventDestroy(g->ev_bwd);
     delete g;
 }
 
@@ -588,10 +606,20 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
     tdp_status st = build_topology(g, netlist);
     if (st == TDP_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+        // the backward sweep's stream at the highest priority: its blocks are
+        // placed before those of the kernels queued beside it
+        int prio_lo = 0, prio_hi = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, prio_hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fwd, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_bwd, cudaEventDisableTiming);
         if (e != cudaSuccess) {
-            set_error("sta_build: cudaStreamCreate failed: %s", cudaGetErrorString(e));
+            set_error("sta_build: stream or event creation failed: %s", cudaGetErrorString(e));
             st = TDP_ERR_CUDA;
         }
+        // TDP_SERIAL_BWD=1: the backward sweep on the graph's stream, in order
+        const char *ser = getenv("TDP_SERIAL_BWD");
+        g->overlap_bwd = !(ser && ser[0] == '1');
     }
     if (st == TDP_OK)
         st = precision == TDP_FP32 ? build_state<float>(g, netlist) : build_state<double>(g, netlist);

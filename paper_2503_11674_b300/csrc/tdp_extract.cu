@@ -453,6 +453,7 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     if (K > 1 && t.n_ep > 0) {
         g->list_L = list_bucket(K - 1);
         if (g->lists_valid_L < K - 1) {
+            join_side(g);  // the rerun rewrites arrival times the backward sweep reads
             TDP_TRY(forward_lists<R>(g));
             g->lists_valid_L = g->list_L;
         }

@@ -39,7 +39,7 @@ constexpr int kMaxK = 32;          // paths per endpoint (one warp holds the fro
 constexpr int kMaxFanin = 32;      // inputs of a combinational cell
 constexpr int kBigFanout = 32;     // nets with more sinks are handled by a whole block
 constexpr int kPre = 4;            // inputs / sinks whose loads are issued together
-constexpr int kRedChunk = 1024;     // endpoints per partial of the WNS / TNS reduction
+constexpr int kRedChunk = 64;       // endpoints per partial of the WNS / TNS reduction
 constexpr int kCompactItems = 8192; // flags per block of the stream compaction
 constexpr uint8_t kPfSmall = 1, kPfLarge = 2;  // net holds a pair sink; fanout <= / > kBigFanout
 constexpr double kQScale = 16777216.0;  // 2^24: fixed point of slack/WNS in the pair update
@@ -61,7 +61,7 @@ constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 // the WNS / TNS reduction.
 enum KernelId {
     KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
-    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_COUNT
+    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_EP_WNS, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -317,6 +317,7 @@ struct Topo {
     int4 *lv_rec = nullptr;        // [n_comb]
     int4 *lv_slot = nullptr;       // [n_comb * kPre]
     int32_t *ep = nullptr;         // [n_ep] endpoint pins, ascending
+    int2 *ep_pd = nullptr;         // [n_ep] (endpoint pin, driver pin of its net)
     int32_t *cp_ptr = nullptr;     // [n_cells+1] cell -> pins CSR
     int32_t *cp = nullptr;         // [n_pins]
     int32_t *slot_of_pin = nullptr;// [n_pins] position of a pin in cp
@@ -418,6 +419,11 @@ struct tdp_graph {
     tdp_precision prec = TDP_FP32;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // stream used to capture CUDA graphs
+    // the backward sweep runs on `side` after the forward sweep (ev_fwd);
+    // ev_bwd marks its end, bwd_pending until the graph's stream waits for it
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fwd = nullptr, ev_bwd = nullptr;
+    bool overlap_bwd = true, bwd_pending = false;
     tdp::Topo topo;
     tdp::Levels lv;
     tdp::State<float> s32;
@@ -585,8 +591,12 @@ inline int list_bucket(int need) {
 struct LaunchScope {
     tdp_graph *g;
     bool on;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
-    LaunchScope(tdp_graph *g_, KernelId id, int n_kernels = 1);
+    LaunchScope(tdp_graph *g_, KernelId id, int n_kernels = 1, cudaStream_t st_ = nullptr);
     ~LaunchScope();
 };
+
+// the graph's stream waits for the last backward sweep (no-op if it already does)
+void join_side(tdp_graph *g);
 }  // namespace tdp

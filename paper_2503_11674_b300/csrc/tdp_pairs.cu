@@ -194,10 +194,14 @@ __global__ void __launch_bounds__(kCmpThreads) k_cmp_count(const uint8_t *f, uin
     if (threadIdx.x == 0) blk[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_cmp_scan(int32_t *blk, int nb, int32_t *total) {
+// one block of kCmpScanThreads (small, so that it finds room on an SM beside
+// the backward sweep that may run on the library's second stream)
+constexpr int kCmpScanThreads = 256;
+
+__global__ void __launch_bounds__(kCmpScanThreads) k_cmp_scan(int32_t *blk, int nb, int32_t *total) {
     __shared__ int sh[32];
     int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += 1024) {
+    for (int b0 = 0; b0 < nb; b0 += kCmpScanThreads) {
         const int i = b0 + threadIdx.x;
         int t;
         const int ex = block_excl_sum(i < nb ? blk[i] : 0, sh, t);
@@ -226,7 +230,7 @@ void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const in
     int32_t *blk = g->prec == TDP_FP32 ? g->s32.cmp_blk : g->s64.cmp_blk;
     const int nb = std::max(div_up(n, kCompactItems), 1);
     k_cmp_count<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk);
-    k_cmp_scan<<<1, 1024, 0, g->stream>>>(blk, nb, count);
+    k_cmp_scan<<<1, kCmpScanThreads, 0, g->stream>>>(blk, nb, count);
     k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, map, out);
 }
 

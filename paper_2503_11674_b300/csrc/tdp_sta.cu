@@ -8,15 +8,20 @@
 //                level by level (thread per combinational cell: max / argmax
 //                over its inputs), and, when asked, each cell's sidetrack list
 //                for report_timing_endpoint; grid-wide barrier between levels
+//   k_ep_wns     endpoints: arrival, required time (T) and slack, and WNS /
+//                TNS over them (FP64, fixed-order reduction); they need the
+//                forward sweep only
 //   k_bwd_sweep  the backward sweep in one cooperative launch: required times
 //                of the nets driven from each level, deepest first (lane per
 //                net of at most 8 sinks, warp per 128 sinks of larger nets,
-//                split nets combined by the last warp to finish), then WNS /
-//                TNS over the endpoints (FP64, fixed-order reduction)
+//                split nets combined by the last warp to finish), and the
+//                slacks of every other pin.  Nothing later in a timing
+//                iteration reads what it writes, so it runs on a second stream
+//                beside path extraction, the pair update and the loss.
 //
 // Where a cooperative launch cannot be made resident (or TDP_LEVEL_GRAPHS=1),
 // the same per-cell and per-task code runs as one launch per level
-// (k_fwd_level, k_bwd_level, k_wns_tns) captured in CUDA graphs; there every
+// (k_fwd_level, k_bwd_level) captured in CUDA graphs; there every
 // array a level reads was written by an earlier launch, so the reads use the
 // read-only path.  Inside one cooperative launch, values written before a
 // barrier are read from L2.  Either way all loads of a group of inputs /
@@ -624,7 +629,7 @@ struct SinkPre {
     int p[kBwPerLane], kd[kBwPerLane], sn[kBwPerLane];
     unsigned old;
     R tp[kBwPerLane], dn[kBwPerLane];
-    A ad, ap[kBwPerLane], rq[kBwPerLane];
+    A ap[kBwPerLane], rq[kBwPerLane];
 };
 
 // topology: one round of loads (task < 0: none)
@@ -654,7 +659,6 @@ __device__ __forceinline__ void sink_topo(const Topo &t, int task, int lane, Sin
 template <typename R>
 __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
     if (c.a < 0) return;
-    c.ad = ldg(&s.arr[c.a]);
 #pragma unroll
     for (int j = 0; j < kBwPerLane; ++j) {
         if (c.p[j] < 0) continue;
@@ -684,7 +688,6 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
     using A = typename AC::T;
     A m = AC::pinf();
     if (c.a >= 0) {
-        const A ad = c.vals ? c.ad : ldg(&s.arr[c.a]);
         A rq[kBwPerLane], ap[kBwPerLane];
         R tp[kBwPerLane];
 #pragma unroll
@@ -692,7 +695,7 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
             if (c.p[j] < 0) continue;
             tp[j] = c.vals ? c.tp[j] : ldg(&s.tnet[c.p[j]]);
             if ((c.kd[j] & kKindMask) == PK_ENDPOINT) {
-                rq[j] = acc_from_double<R>(*s.T);
+                rq[j] = acc_from_double<R>(*s.T);  // arrival and slack: k_ep_wns
             } else {
                 rq[j] = (c.old >> j) & 1u ? c.rq[j] : acc_unkey<R>(ldd<COH>(&s.reqkey[c.sn[j]]));
                 rq[j] = AC::add(rq[j], -(c.vals ? c.dn[j] : ldg(&s.dnet[c.sn[j]])));
@@ -702,12 +705,10 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
 #pragma unroll
         for (int j = 0; j < kBwPerLane; ++j) {  // stores
             if (c.p[j] < 0) continue;
-            if ((c.kd[j] & kKindMask) == PK_ENDPOINT) {
-                ap[j] = AC::add(ad, tp[j]);
-                s.arr[c.p[j]] = ap[j];
+            if ((c.kd[j] & kKindMask) != PK_ENDPOINT) {
+                s.req[c.p[j]] = rq[j];
+                s.slack[c.p[j]] = AC::diff(rq[j], ap[j]);
             }
-            s.req[c.p[j]] = rq[j];
-            s.slack[c.p[j]] = AC::diff(rq[j], ap[j]);
             const A cand = AC::add(rq[j], -tp[j]);
             if (AC::lt(cand, m)) m = cand;
         }
@@ -757,37 +758,71 @@ __global__ void k_bwd_drivers(Topo t, State<R> s) {
 // ---------------------------------------------------------- WNS / TNS ---
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 148;
+constexpr int kRedFinal = 1024;  // chunk partials the last block combines at once (a power of 2)
 constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
+constexpr int kBwdOverlapNum = 11;     // overlapped backward sweep: 11/16 of the resident grid
 
-// WNS = min over endpoints with negative slack, TNS = their sum (FP64;
-// Eqs. (3)-(4)).  The endpoints are cut into chunks of kRedChunk, a warp
-// reduces one chunk in a fixed order, and the last block to finish adds the
-// chunk partials in chunk order: the result does not depend on the grid, the
-// block size or scheduling.
-template <typename R, bool COH>
-__device__ __forceinline__ void wns_tns_blocks(const Topo &t, State<R> &s) {
+// Endpoints (FF D and PO pins): arrival = the driver's arrival + the pin's
+// Elmore delay, required time = T, slack = T - arrival; then WNS = min over
+// endpoints with negative slack, TNS = their sum (FP64; Eqs. (2)-(4)).
+// FP64 arithmetic is slow on this GPU, so the sums run as trees of fixed
+// shape: a warp takes a chunk of kRedChunk endpoints (two per lane, then a
+// butterfly over the lanes), and the last block to finish combines the
+// chunk partials in a pairwise tree over their index (kRedFinal at a time,
+// those in chunk order).  The result does not depend on the grid, the block
+// size or scheduling.  Needs the forward sweep only.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
+    using AC = Acc<R>;
+    using A = typename AC::T;
+    static_assert(kRedChunk == 64, "two endpoints per lane");
     __shared__ bool last;
+    __shared__ double part[2 * kRedFinal];
     const int lane = threadIdx.x & 31;
     const int n_chunks = div_up_dev(t.n_ep, kRedChunk);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < n_chunks; ch += nw) {
-        double mn = 0.0, sm = 0.0;
-        const int end = min((ch + 1) * kRedChunk, t.n_ep);
-        for (int i = ch * kRedChunk + lane; i < end; i += 32) {
-            const double v = (double)ldd<COH>(&s.slack[ldg(&t.ep[i])]);
-            if (v < 0.0) {
-                mn = fmin(mn, v);
-                sm += v;
+    const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const A rq = acc_from_double<R>(*s.T);
+    if (ch < n_chunks) {
+        double mn[2] = {0.0, 0.0}, sm[2] = {0.0, 0.0};
+        int2 pd[2];
+        A ad[2];
+        R tp[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ch * kRedChunk + 32 * u + lane;
+            if (i < t.n_ep) pd[u] = ldg(&t.ep_pd[i]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ch * kRedChunk + 32 * u + lane;
+            if (i < t.n_ep) {
+                ad[u] = s.arr[pd[u].y];
+                tp[u] = ldg(&s.tnet[pd[u].x]);
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ch * kRedChunk + 32 * u + lane;
+            if (i >= t.n_ep) continue;
+            const A ap = AC::add(ad[u], tp[u]);
+            const R sl = AC::diff(rq, ap);
+            s.arr[pd[u].x] = ap;
+            s.req[pd[u].x] = rq;
+            s.slack[pd[u].x] = sl;
+            const double v = (double)sl;
+            if (v < 0.0) {
+                mn[u] = v;
+                sm[u] = v;
+            }
+        }
+        double m = fmin(mn[0], mn[1]), a = sm[0] + sm[1];
+        for (int o = 16; o > 0; o >>= 1) {  // butterfly: the same pairs in every lane
+            m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+            a += __shfl_xor_sync(0xffffffffu, a, o);
         }
         if (lane == 0) {
-            s.red_part[2 * ch] = mn;
-            s.red_part[2 * ch + 1] = sm;
+            s.red_part[2 * ch] = m;
+            s.red_part[2 * ch + 1] = a;
         }
     }
     __syncthreads();
@@ -796,32 +831,43 @@ __device__ __forceinline__ void wns_tns_blocks(const Topo &t, State<R> &s) {
         last = atomicAdd(s.red_count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double bm = 0.0, bs = 0.0;
-        for (int k = 0; k < n_chunks; ++k) {
-            bm = fmin(bm, ldcg(&s.red_part[2 * k]));
-            bs += ldcg(&s.red_part[2 * k + 1]);
+    if (!last) return;
+    __threadfence();
+    double bm = 0.0, bs = 0.0;
+    for (int k0 = 0; k0 < n_chunks; k0 += kRedFinal) {
+        for (int k = threadIdx.x; k < kRedFinal; k += blockDim.x) {
+            const bool in = k0 + k < n_chunks;
+            part[2 * k] = in ? ldcg(&s.red_part[2 * (k0 + k)]) : 0.0;
+            part[2 * k + 1] = in ? ldcg(&s.red_part[2 * (k0 + k) + 1]) : 0.0;
         }
+        __syncthreads();
+        for (int h = kRedFinal / 2; h > 0; h >>= 1) {  // pairwise tree: k with k + h
+            for (int k = threadIdx.x; k < h; k += blockDim.x) {
+                part[2 * k] = fmin(part[2 * k], part[2 * (k + h)]);
+                part[2 * k + 1] += part[2 * (k + h) + 1];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            bm = fmin(bm, part[0]);
+            bs += part[1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         s.wns_tns[0] = bm;
         s.wns_tns[1] = bs;
         *s.red_count = 0u;
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_wns_tns(Topo t, State<R> s) {
-    pdl_wait();
-    wns_tns_blocks<R, false>(t, s);
-}
-
-// The whole backward sweep and WNS / TNS in one cooperative launch: levels
+// The whole backward sweep in one cooperative launch: levels
 // from the deepest down to the startpoints' nets, a level's warp tasks on
 // block j mod gridDim, a grid-wide barrier after each level.  A warp carries
 // its first task of the next two levels: between its arrival at the barrier
 // that closes level l and the wait, it loads the final values of its level
 // l - 1 task and the topology of its level l - 2 task.  After the last
-// level, the driver pins' required times and slacks, and WNS / TNS.
+// level, the driver pins' required times and slacks.
 template <typename R>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
     const int lane = threadIdx.x & 31;
@@ -857,7 +903,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s
         if (!grid_wait(gs, (++n) * gridDim.x)) return;
     }
     bwd_drivers<R, true>(t, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-    wns_tns_blocks<R, true>(t, s);
 }
 
 // ------------------------------------------------------------ launch ---
@@ -891,8 +936,7 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     }
     if (bwd && ok) {
         launch_pdl(k_bwd_drivers<R>, 4 * 148, 256, cs, t, s);
-        launch_pdl(k_wns_tns<R>, kRedBlocks, kRedThreads, cs, t, s);
-        nk += 2;
+        nk += 1;
         ok = cudaGetLastError() == cudaSuccess;
     }
     cudaGraph_t graph = nullptr;
@@ -931,17 +975,21 @@ static int coop_grid(tdp_graph *g, K kernel, int threads) {
     return grid;
 }
 
+// gsync words: [0] forward sweep's barrier count, [1] sticky timeout status
+// of both, [2] backward sweep's barrier count (the two sweeps may overlap
+// when an extraction reruns the forward sweep)
 template <typename R>
 static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, GridSync), int grid,
-                               int threads, KernelId id) {
+                               int threads, KernelId id, cudaStream_t st, int count_word,
+                               bool reset_count = true) {
     State<R> &s = state<R>(g);
     GridSync gs;
-    gs.count = s.gsync;
+    gs.count = s.gsync + count_word;
     gs.status = s.gsync + 1;
     gs.timeout_ns = kSyncTimeoutNs;
-    LaunchScope ls(g, id);
-    TDP_CUDA(cudaMemsetAsync(s.gsync, 0, sizeof(unsigned), g->stream));
-    TDP_CUDA(launch_coop(kernel, grid, threads, g->stream, g->topo, s, gs));
+    LaunchScope ls(g, id, 1, st);
+    if (reset_count) TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), st));
+    TDP_CUDA(launch_coop(kernel, grid, threads, st, g->topo, s, gs));
     return TDP_OK;
 }
 
@@ -963,7 +1011,7 @@ tdp_status forward_lists(tdp_graph *g) {
             default: kernel = k_fwd_sweep<R, 31>; break;
         }
         const int grid = coop_grid(g, kernel, kFwdThreads);
-        if (grid > 0) return launch_sweep<R>(g, kernel, grid, kFwdThreads, KID_FWD_SWEEP);
+        if (grid > 0) return launch_sweep<R>(g, kernel, grid, kFwdThreads, KID_FWD_SWEEP, g->stream, 0);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
@@ -977,27 +1025,65 @@ tdp_status forward_lists(tdp_graph *g) {
     return TDP_OK;
 }
 
-// Backward sweep and WNS / TNS: one cooperative launch, or one graph replay.
+// reqkey := +inf keys (all ones) for the backward sweep, and its barrier
+// count := 0: a kernel rather than memsets, so that the side stream holds
+// only kernels
+__global__ void k_bwd_reset(unsigned long long *reqkey, int n, unsigned *count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) reqkey[i] = ~0ull;
+    if (i == 0) *count = 0u;
+}
+
+// Backward sweep: one cooperative launch, or one graph replay, on the graph's
+// second stream after the forward sweep (or on its stream when the two are
+// serialised); sta_join and every call that needs its results wait for it.
 template <typename R>
 static tdp_status backward(tdp_graph *g) {
+    cudaStream_t st = g->stream;
+    if (g->overlap_bwd) {  // ev_fwd: recorded after the forward sweep
+        TDP_CUDA(cudaStreamWaitEvent(g->side, g->ev_fwd, 0));
+        st = g->side;
+    }
+    bool done = false;
     if (g->single_launch) {
-        const int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
+        // beside extraction, the pair update and the loss, the sweep leaves
+        // SMs to them: kBwdOverlapNum / 16 of the resident grid (the best
+        // split measured at 1.2M cells on 148 SMs: about 100 blocks)
+        int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
+        if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * kBwdOverlapNum / 16);
         if (grid > 0) {
             State<R> &s = state<R>(g);
-            TDP_CUDA(cudaMemsetAsync(s.reqkey, 0xff, sizeof(unsigned long long) * g->topo.n_nets, g->stream));
-            return launch_sweep<R>(g, k_bwd_sweep<R>, grid, kBwdThreads, KID_BWD_SWEEP);
+            ++g->n_launch;
+            k_bwd_reset<<<div_up(std::max(g->topo.n_nets, 1), 256), 256, 0, st>>>(s.reqkey, g->topo.n_nets,
+                                                                                 s.gsync + 2);
+            TDP_TRY(launch_sweep<R>(g, k_bwd_sweep<R>, grid, kBwdThreads, KID_BWD_SWEEP, st, 2, false));
+            done = true;
+        } else {
+            g->single_launch = false;
         }
-        g->single_launch = false;
     }
-    if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
-    LaunchScope ls(g, KID_BWD_SWEEP, g->bwd_graph_kernels);
-    TDP_CUDA(cudaGraphLaunch(g->bwd_graph, g->stream));
+    if (!done) {
+        if (!g->bwd_graph) TDP_TRY(capture<R>(g, &g->bwd_graph, &g->bwd_graph_kernels, false, true, 0));
+        LaunchScope ls(g, KID_BWD_SWEEP, g->bwd_graph_kernels, st);
+        TDP_CUDA(cudaGraphLaunch(g->bwd_graph, st));
+    }
+    if (g->overlap_bwd) {
+        TDP_CUDA(cudaEventRecord(g->ev_bwd, g->side));
+        g->bwd_pending = true;
+    }
     return TDP_OK;
 }
 
 template <typename R>
 static tdp_status sweep(tdp_graph *g) {
     TDP_TRY(forward_lists<R>(g));
+    if (g->overlap_bwd) TDP_CUDA(cudaEventRecord(g->ev_fwd, g->stream));
+    {
+        LaunchScope ls(g, KID_EP_WNS);
+        const int chunks = div_up(std::max(g->topo.n_ep, 1), kRedChunk);
+        k_ep_wns<R><<<div_up(chunks, kRedThreads / 32), kRedThreads, 0, g->stream>>>(g->topo, state<R>(g));
+    }
+    TDP_LAUNCH_CHECK();
     return backward<R>(g);
 }
 
@@ -1009,6 +1095,7 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
     const int nsb = div_up(t.n_nets, kRcThreads);
+    join_side(g);  // the last backward sweep reads what this propagation rewrites
     {
         LaunchScope ls(g, KID_NET_RC);
         k_net_rc<R><<<nsb + t.n_big, kRcThreads, 0, g->stream>>>(t, s, x, y, T, (R)g->r, (R)g->c,
@@ -1033,6 +1120,7 @@ template <typename R>
 static tdp_status get_timing_impl(tdp_graph *g, R *arr, R *req, R *slack) {
     State<R> &s = state<R>(g);
     int n = g->topo.n_pins;
+    join_side(g);
     g->n_launch += (arr ? 1 : 0) + (req ? 1 : 0);
     if (arr) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.arr, arr, n);
     if (req) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.req, req, n);
@@ -1080,6 +1168,15 @@ extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void 
         if (wns_out) *wns_out = h[0];
         if (tns_out) *tns_out = h[1];
     }
+    return TDP_OK;
+}
+
+extern "C" tdp_status sta_join(tdp_graph *g) {
+    if (!g) {
+        set_error("sta_join: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    join_side(g);
     return TDP_OK;
 }
 

@@ -115,6 +115,11 @@ class TimingGraph:
                                                    int(bool(keep_nonneg)), None))
         return None
 
+    def sta_join(self):
+        """The graph's stream waits for the last backward sweep (run on the
+        library's second stream)."""
+        _abi.check("sta_join", self.lib.sta_join(self.handle))
+
     def report_timing(self, n: int, keep_nonneg: bool = False) -> int:
         """report_timing(n): the n lowest-slack paths of the design, worst first;
         returns their number (the call synchronises)."""

@@ -393,6 +393,42 @@ def test_level_launches_match_single_launch_sweeps(prec, monkeypatch):
     _assert_same(one, lv)
 
 
+def _pipeline_async(nl, T, prec):
+    """Two timing iterations queued without host synchronisation (the backward
+    sweep overlaps extraction, the pair update and the loss), then every
+    result read back."""
+    G = _graph(nl, prec)
+    out = []
+    rng = np.random.default_rng(3)
+    for it in range(2):
+        x, y = _pos(nl, G.dtype, nl.x + (rng.normal(0, 2, nl.n_cells) if it else 0),
+                    nl.y + (rng.normal(0, 2, nl.n_cells) if it else 0))
+        G.sta_propagate(x, y, T, sync=False)
+        G.extract_critical_paths(-1, 8, False, sync=False)
+        G.attraction_update_pairs(10.0, 0.2, sync=False)
+        loss = G.attraction_loss_fwd(x, y, 2.5e-5)
+        gx, gy = G.attraction_loss_bwd(x, y, 2.5e-5)
+        timing = [t.cpu().numpy() for t in G.sta_get_timing()]
+        pins, w = G.attraction_get_pairs()
+        P = gpu_paths(G)
+        res = (pins.cpu().numpy(), w.cpu().numpy(), loss.item(), gx.cpu().numpy(), gy.cpu().numpy(), timing)
+        out.append((G.sta_propagate(x, y, T), P) + res)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_overlapped_backward_sweep_matches_serial(prec, monkeypatch):
+    """The backward sweep on the library's second stream (beside extraction,
+    pair update and loss) gives the same bits as the sweep in stream order."""
+    nl = netgen.generate("mid", 6)
+    T = oracle.clock_period(nl, 0.85)
+    over = _pipeline_async(nl, T, prec)
+    monkeypatch.setenv("TDP_SERIAL_BWD", "1")
+    ser = _pipeline_async(nl, T, prec)
+    for a, b in zip(over, ser):
+        _assert_same(a, b)
+
+
 # --------------------------------------------------------- edge cases ------
 
 def test_no_violation_and_empty_pairs():
