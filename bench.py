@@ -214,13 +214,17 @@ def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
         L = g_info["list_L"]
         return n_comb * (12 + 4 + 8 + 12 + 16 * L + 8) + n_in * (13 + 4 + 8) + N * (8 + 4)
     if kernel == "bwd_sweep":
-        # per sink: kind, cell output, its net (9), Elmore delay (4), required
-        # time and slack written (12); comb inputs read their arrival (8),
-        # endpoints write theirs (8); per net: pin range (8), driver arrival
-        # (8), driver required time and slack written (12), driving-cell delay
-        # (4); per comb output its required time read once (8); WNS / TNS read
-        # each endpoint index and slack (8)
-        return S * (9 + 4 + 12) + n_in * 8 + n_ep * 8 + N * (8 + 8 + 12 + 4) + n_comb * 8 + n_ep * 8
+        # per sink: kind, cell output, its net (9), Elmore delay (4); comb
+        # inputs read their arrival (8) and write required time and slack
+        # (12); endpoints (required time T) are written by ep_wns; per net:
+        # pin range (8), driver arrival (8), driver required time and slack
+        # written (12), driving-cell delay (4); per comb output its required
+        # time read once (8)
+        return S * (9 + 4) + n_in * (8 + 12) + N * (8 + 8 + 12 + 4) + n_comb * 8
+    if kernel == "ep_wns":
+        # per endpoint: (pin, driver pin) (8), driver arrival (8), Elmore delay
+        # (4), arrival, required time and slack written (20)
+        return n_ep * 40
     if kernel == "net_rc":
         return (4 * (N + 1) + 4 * P + 8 * P + 4 * S + 8 * C + 4 * N + N
                 + 4 * S + 4 * N + 4 * N + 8 * n_start)

@@ -114,8 +114,8 @@ static bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
 static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
     Topo &t = g->topo;
     const int nc = d->n_cells, np = d->n_pins, nn = d->n_nets;
-    if (nc <= 0 || np <= 0 || nn <= 0 || np >= (1 << 29)) {
-        set_error("sta_build: n_cells, n_pins and n_nets must be positive, n_pins below 2^29");
+    if (nc <= 0 || np <= 0 || nn <= 0 || np > kBwPinMask) {
+        set_error("sta_build: n_cells, n_pins and n_nets must be positive, n_pins below 2^28");
         return TDP_ERR_INVALID;
     }
     if (!d->pin_cell || !d->net_ptr || !d->pin_dir || !d->cell_type || !d->pin_dx ||
@@ -319,14 +319,16 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             bl_net[small ? fs[l]++ : fb[l]++] = e;
         }
     }
-    // backward warp tasks per level, deepest level first: tasks of
-    // kBwNetsPerTask small nets (at most kBwSmallFanout sinks; kBwLanes lanes
-    // a net, sinks j and j + kBwLanes of the net on its lane j), then pieces
-    // of kBwPiece sinks of the larger nets (sinks l and l + 32 of the piece on
-    // lane l).  Per task and lane: the net's driver pin (kBwSplit set when the
-    // net has several pieces; -1: none) and the net; per task and lane,
-    // kBwPerLane sink slots (pin, kind | kKindPrev, net driven by the sink's
-    // cell; pin -1: none).
+    // backward warp tasks per level, deepest level first: tasks of small nets
+    // (at most kBwSmallFanout sinks), a net on an aligned group of 1, 2 or 4
+    // lanes (kBwPerLane sinks a lane: sinks j and j + G of a net of G lanes
+    // on its lane j), the groups of 4 first, then of 2, then single lanes,
+    // packed 32 lanes a task; then pieces of kBwPiece sinks of the larger nets
+    // (sinks l and l + 32 of the piece on lane l).  Per task and lane: the
+    // net's driver pin (kBwSplit set when the net has several pieces, kBwG2 /
+    // kBwG4 for groups of 2 / 4 lanes; -1: none) and the net; per task and
+    // lane, kBwPerLane sink slots (pin, kind | kKindPrev, net driven by the
+    // sink's cell; pin -1: none).
     std::vector<int2> bw_drv;
     std::vector<int4> bw_slot;
     const int4 no_slot = make_int4(-1, 0, 0, 0);
@@ -344,21 +346,26 @@ static tdp_status build_topology(tdp_graph *g, const tdp_netlist_desc *d) {
             const int e = bl_net[q];
             (d->net_ptr[e + 1] - d->net_ptr[e] - 1 <= kBwSmallFanout ? small : large).push_back(e);
         }
-        for (size_t i0 = 0; i0 < small.size(); i0 += kBwNetsPerTask, ++n_tasks) {
-            for (int ln = 0; ln < 32; ++ln) {
-                const size_t i = i0 + ln / kBwLanes;
-                if (i >= small.size()) {
-                    bw_drv.push_back(make_int2(-1, -1));
-                    for (int j = 0; j < kBwPerLane; ++j) bw_slot.push_back(no_slot);
-                    continue;
+        int lane = 0;  // next lane of the current task
+        for (int G : {4, 2, 1}) {
+            for (int e : small) {
+                const int a = d->net_ptr[e], b = d->net_ptr[e + 1];
+                const int ns = b - a - 1;
+                if ((ns > 2 * kBwPerLane ? 4 : ns > kBwPerLane ? 2 : 1) != G) continue;
+                if (lane == 0) ++n_tasks;
+                for (int ln = 0; ln < G; ++ln) {
+                    bw_drv.push_back(make_int2(a | (G == 4 ? kBwG4 : G == 2 ? kBwG2 : 0), e));
+                    for (int j = 0; j < kBwPerLane; ++j) {
+                        const int p = a + 1 + ln + j * G;
+                        bw_slot.push_back(p < b ? slot_of(p) : no_slot);
+                    }
                 }
-                const int e = small[i], a = d->net_ptr[e], b = d->net_ptr[e + 1];
-                bw_drv.push_back(make_int2(a, e));
-                for (int j = 0; j < kBwPerLane; ++j) {
-                    const int p = a + 1 + ln % kBwLanes + j * kBwLanes;
-                    bw_slot.push_back(p < b ? slot_of(p) : no_slot);
-                }
+                lane = (lane + G) & 31;  // groups stay aligned: larger groups come first
             }
+        }
+        for (; lane != 0; lane = (lane + 1) & 31) {  // the last task's unused lanes
+            bw_drv.push_back(make_int2(-1, -1));
+            for (int j = 0; j < kBwPerLane; ++j) bw_slot.push_back(no_slot);
         }
         const int n_small_tasks = n_tasks - first;
         for (int e : large) {

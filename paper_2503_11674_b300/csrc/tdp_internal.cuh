@@ -282,15 +282,17 @@ inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, cu
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Backward sweep work: a warp task is either kBwNetsPerTask nets of at most
-// kBwSmallFanout sinks (kBwLanes lanes a net) or a piece of kBwPiece sinks of
-// a larger net; either way a lane holds kBwPerLane sinks.
+// Backward sweep work: a warp task is either nets of at most kBwSmallFanout
+// sinks (1, 2 or kBwLanes lanes a net, by fanout) or a piece of kBwPiece
+// sinks of a larger net; either way a lane holds kBwPerLane sinks.
 constexpr int kBwSmallFanout = 8;
-constexpr int kBwLanes = 4;
+constexpr int kBwLanes = 4;  // lanes of the largest small net
 constexpr int kBwPerLane = kBwSmallFanout / kBwLanes;
-constexpr int kBwNetsPerTask = 32 / kBwLanes;
 constexpr int kBwPiece = 32 * kBwPerLane;
 constexpr int kBwSplit = 1 << 30;  // on a task's driver pin: the net has several pieces
+constexpr int kBwG4 = 1 << 29;     // on a small net's driver pin: the net has 4 lanes
+constexpr int kBwG2 = 1 << 28;     // ... 2 lanes (else 1)
+constexpr int kBwPinMask = kBwG2 - 1;
 
 // ------------------------------------------------------------ the graph ---
 // Device arrays common to both precisions (topology, built once).

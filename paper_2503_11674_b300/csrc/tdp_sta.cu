@@ -624,7 +624,7 @@ __device__ __forceinline__ double acc_unkey<double>(unsigned long long k) {
 template <typename R>
 struct SinkPre {
     using A = typename Acc<R>::T;
-    int a, e;
+    int a, e, gl;  // gl: lanes of the net (small nets)
     bool split, vals;
     int p[kBwPerLane], kd[kBwPerLane], sn[kBwPerLane];
     unsigned old;
@@ -638,12 +638,14 @@ __device__ __forceinline__ void sink_topo(const Topo &t, int task, int lane, Sin
     c.vals = c.split = false;
     c.old = 0u;
     c.a = -1;
+    c.gl = 1;
 #pragma unroll
     for (int j = 0; j < kBwPerLane; ++j) c.p[j] = -1;
     if (task < 0) return;
     const int2 d = ldg(&t.bw_drv[(size_t)task * 32 + lane]);
-    c.a = d.x < 0 ? -1 : (d.x & ~kBwSplit);
+    c.a = d.x < 0 ? -1 : (d.x & kBwPinMask);
     c.split = d.x >= 0 && (d.x & kBwSplit);
+    c.gl = d.x >= 0 && (d.x & kBwG4) ? 4 : d.x >= 0 && (d.x & kBwG2) ? 2 : 1;
     c.e = d.y;
 #pragma unroll
     for (int j = 0; j < kBwPerLane; ++j) {
@@ -678,8 +680,8 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
 // Required and slack times of the task's sinks, and the net's required time
 // (Section II-B: min over its sinks of the sink's required time minus its
 // Elmore delay) into reqkey (stored, or atomicMin for the pieces of a split
-// net).  PIECE: the warp holds one piece (min over 32 lanes), else
-// kBwNetsPerTask nets (min over kBwLanes lanes).  Every lane of the warp
+// net).  PIECE: the warp holds one piece (min over 32 lanes), else small
+// nets on aligned groups of 1, 2 or 4 lanes (min over the group).  Every lane of the warp
 // calls this.  COH: required times of sink cells were written by other
 // blocks of the same launch.
 template <typename R, bool COH>
@@ -714,11 +716,13 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
         }
     }
     // min is exact: any order gives the same value
+    // (every lane shuffles; a small net's lanes take only partners in its group)
+    const int gl = piece ? 32 : c.gl;
     for (int o = piece ? 16 : kBwLanes / 2; o > 0; o >>= 1) {
         const A other = shfl_x(m, o);
-        if (AC::lt(other, m)) m = other;
+        if (o < gl && AC::lt(other, m)) m = other;
     }
-    if (c.a >= 0 && (lane & (piece ? 31 : kBwLanes - 1)) == 0) {
+    if (c.a >= 0 && (lane & (gl - 1)) == 0) {
         if (c.split) atomicMin(&s.reqkey[c.e], acc_key(m));
         else s.reqkey[c.e] = acc_key(m);
     }
@@ -760,7 +764,7 @@ __global__ void k_bwd_drivers(Topo t, State<R> s) {
 constexpr int kRedThreads = 256;
 constexpr int kRedFinal = 1024;  // chunk partials the last block combines at once (a power of 2)
 constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
-constexpr int kBwdOverlapNum = 11;     // overlapped backward sweep: 11/16 of the resident grid
+constexpr int kBwdOverlapNum = 10;     // overlapped backward sweep: 10/16 of the resident grid
 
 // Endpoints (FF D and PO pins): arrival = the driver's arrival + the pin's
 // Elmore delay, required time = T, slack = T - arrival; then WNS = min over
@@ -1048,7 +1052,7 @@ static tdp_status backward(tdp_graph *g) {
     if (g->single_launch) {
         // beside extraction, the pair update and the loss, the sweep leaves
         // SMs to them: kBwdOverlapNum / 16 of the resident grid (the best
-        // split measured at 1.2M cells on 148 SMs: about 100 blocks)
+        // split measured at 1.2M cells on 148 SMs: 80 to 100 blocks)
         int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
         if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * kBwdOverlapNum / 16);
         if (grid > 0) {
