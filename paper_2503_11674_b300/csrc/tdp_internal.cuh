@@ -410,6 +410,12 @@ struct State {
     // worst first) and each reported path's sidetracks, deepest first, at
     // rt_side_off[q] (grown on demand, freed by rt_free)
     RtNodes<R> rt;
+    // per report, from the last propagation: per net driven by a
+    // combinational cell (next net on its worst-input chain, first input in
+    // lv_in order, inputs, worst input pin; all -1 elsewhere), and per input
+    // the slack a sidetrack through it costs
+    int4 *rt_chain = nullptr;
+    R *rt_delta = nullptr;
     int32_t *rt_out = nullptr;
     int64_t *rt_side_off = nullptr;
     int32_t *rt_sides = nullptr;

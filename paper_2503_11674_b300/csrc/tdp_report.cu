@@ -82,16 +82,37 @@ __global__ void k_rt_root_write(Topo t, State<R> s, const int32_t *flag, const i
     stg.key[q] = rt_ord(s.slack[ep]);
 }
 
+// Chain records of this report (one thread per combinational cell; every
+// other net keeps the all -1 record set before): the cell's net gets (net of
+// its worst input, its first input, its inputs, the worst input pin), and
+// each input the cost of a sidetrack through it, Arr(worst input) - Arr(it)
+// (the worst input itself: 0, never used).
+template <typename R>
+__global__ void k_rt_prep(Topo t, State<R> s) {
+    using AC = Acc<R>;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.n_comb) return;
+    const int e = t.lv_onet[k];
+    const int2 pr = s.pred[e];
+    const int a = t.lv_in_ptr[k], b = t.lv_in_ptr[k + 1];
+    s.rt_chain[e] = make_int4(pr.y, a, b - a, pr.x);
+    const typename AC::T aw = s.arr[pr.x];
+    for (int j = a; j < b; ++j) {
+        const int p = t.lv_in_pin[j];
+        s.rt_delta[j] = p == pr.x ? R(0) : AC::diff(aw, s.arr[p]);
+    }
+}
+
 // Children of frontier node lo + f within the bound: count them (WRITE
 // false) or write them at off[f] (WRITE true).  The walk follows the node's
-// last worst-input chain from its head net back to the startpoint and, at
-// each combinational cell on it, visits the inputs other than the worst.
+// last worst-input chain from its head net back to the startpoint through
+// the chain records (one dependent load a cell; the next record is loaded
+// while this cell's inputs are visited) and, at each combinational cell on
+// it, visits the inputs other than the worst.
 template <typename R, bool WRITE>
 __global__ void __launch_bounds__(kRtThreads) k_rt_expand(Topo t, State<R> s, RtNodes<R> acc, int64_t lo,
                                                          int64_t nf, const RtSel *sel, int32_t *cnt,
                                                          const int64_t *off, RtNodes<R> stg) {
-    using AC = Acc<R>;
-    using A = typename AC::T;
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const int64_t x = lo + f;
@@ -107,16 +128,13 @@ __global__ void __launch_bounds__(kRtThreads) k_rt_expand(Topo t, State<R> s, Rt
         int64_t pos = WRITE ? off[f] : 0;
         const int64_t end = WRITE ? off[f + 1] : 0;  // never past this node's range
         int e = t.pin_net[side < 0 ? ep : side];
-        for (;;) {
-            const int2 pr = s.pred[e];
-            if (pr.x < 0) break;
-            const A aw = s.arr[pr.x];
-            const int cell = t.pin_cell[pr.x];
-            const int qa = t.cp_ptr[cell], qb = t.cp_ptr[cell + 1];
-            for (int q = qa; q < qb; ++q) {
-                const int p = t.cp[q];
-                if (p == pr.x || t.pin_kind[p] != PK_COMB_IN) continue;
-                const R cc = cost + AC::diff(aw, s.arr[p]);
+        int4 r = ldg(&s.rt_chain[e]);
+        while (r.w >= 0) {  // e is driven by a combinational cell
+            const int4 rn = ldg(&s.rt_chain[r.x]);
+            for (int j = r.y; j < r.y + r.z; ++j) {
+                const int p = ldg(&t.lv_in_pin[j]);
+                if (p == r.w) continue;
+                const R cc = cost + ldg(&s.rt_delta[j]);
                 const Key k = rt_ord(se + cc);
                 if (k > bound) continue;
                 if (WRITE) {
@@ -124,7 +142,7 @@ __global__ void __launch_bounds__(kRtThreads) k_rt_expand(Topo t, State<R> s, Rt
                     stg.par[pos] = (int32_t)x;
                     stg.side[pos] = p;
                     stg.ep[pos] = ep;
-                    stg.len[pos] = len - s.plen[e] + 2 + s.plen[t.pin_net[p]];
+                    stg.len[pos] = len - s.plen[e] + 2 + s.plen[ldg(&t.lv_in_net[j])];
                     stg.nsd[pos] = nsd;
                     stg.cost[pos] = cc;
                     stg.key[pos] = k;
@@ -133,7 +151,8 @@ __global__ void __launch_bounds__(kRtThreads) k_rt_expand(Topo t, State<R> s, Rt
                     ++c;
                 }
             }
-            e = pr.y;
+            e = r.x;
+            r = rn;
         }
     }
     if (!WRITE) cnt[f] = c;
@@ -461,6 +480,13 @@ tdp_status report_impl(tdp_graph *g, int64_t n, int keep_nonneg) {
     g->rt_nodes = 0;
     TDP_TRY(sort_failing<R>(g));
     if (n == 0 || t.n_ep == 0) return TDP_OK;
+    if (!s.rt_chain) {
+        TDP_TRY(dalloc(g, &s.rt_chain, (size_t)t.n_nets));
+        TDP_TRY(dalloc(g, &s.rt_delta, (size_t)std::max(t.n_in, 1)));
+    }
+    TDP_CUDA(cudaMemsetAsync(s.rt_chain, 0xff, sizeof(int4) * (size_t)t.n_nets, st));
+    ++g->n_launch;
+    if (t.n_comb > 0) k_rt_prep<R><<<div_up(t.n_comb, kRtThreads), kRtThreads, 0, st>>>(t, s);
 
     Grow<RtSel> sel(st);
     Grow<unsigned> hist(st);
