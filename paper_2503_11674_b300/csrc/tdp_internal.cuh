@@ -226,8 +226,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void grid_arrive(const GridSync &gs) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();  // this block's writes before its arrival
-        atomicAdd(gs.count, 1u);
+        // release at GPU scope: this block's writes (ordered before by the
+        // block barrier) become visible before the arrival is counted
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gs.count) : "memory");
     }
 }
 
