@@ -345,8 +345,8 @@ static cudaError_t rt_alloc(T **p, int64_t n, cudaStream_t st) {
     return e;
 }
 
-// A device buffer that grows on demand (its contents are dropped when it
-// grows); `owned` buffers are freed when the object goes away.
+// A temporary device buffer that grows on demand (its contents are dropped
+// when it grows) and is freed when the object goes away.
 template <typename T>
 struct Grow {
     cudaStream_t st;
@@ -409,13 +409,21 @@ static tdp_status grow_nodes(tdp_graph *g, int64_t need, int64_t keep) {
         return TDP_ERR_OOM;
     }
     if (keep > 0) {
-        TDP_CUDA(cudaMemcpyAsync(nw.par, s.rt.par, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.side, s.rt.side, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.ep, s.rt.ep, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.len, s.rt.len, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.nsd, s.rt.nsd, sizeof(int32_t) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.cost, s.rt.cost, sizeof(R) * keep, cudaMemcpyDeviceToDevice, st));
-        TDP_CUDA(cudaMemcpyAsync(nw.key, s.rt.key, sizeof(Key) * keep, cudaMemcpyDeviceToDevice, st));
+        const size_t k = (size_t)keep;
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        const bool copied = cudaMemcpyAsync(nw.par, s.rt.par, sizeof(int32_t) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.side, s.rt.side, sizeof(int32_t) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.ep, s.rt.ep, sizeof(int32_t) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.len, s.rt.len, sizeof(int32_t) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.nsd, s.rt.nsd, sizeof(int32_t) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.cost, s.rt.cost, sizeof(R) * k, d2d, st) == cudaSuccess &&
+                            cudaMemcpyAsync(nw.key, s.rt.key, sizeof(Key) * k, d2d, st) == cudaSuccess;
+        if (!copied) {
+            cudaGetLastError();
+            nodes_free(nw, st);
+            set_error("report_timing: copying the path nodes failed");
+            return TDP_ERR_CUDA;
+        }
     }
     nodes_free(s.rt, st);
     s.rt = nw;
