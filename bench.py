@@ -402,6 +402,9 @@ def run_ours(args):
     stages = None
     if args.stages:
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
+    ktab = kernel_table(G, step, args.warmup + args.steps, nl, info)
+    lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
+    ploop = placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream)
     t1 = table1(G, xs[0], ys[0], T) if not args.no_table1 else None
     fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
 
@@ -443,6 +446,11 @@ def run_ours(args):
             "timing": {"wns_ps": wns, "tns_ps": tns, "T_ps": T, "failing_endpoints": n_viol,
                        "paths_per_step": n_paths, "path_pins_per_step": n_path_pins, "pairs_after": n_pairs},
         }
+        for v in ktab.values():
+            v["frac"] = round(v["gbs"] / hbm, 4)
+        result["kernels"] = ktab
+        result["loss_only"] = lonly
+        result["placement_loop"] = ploop
         if stages:
             result["stages_ms"] = stages
         if t1:
@@ -543,6 +551,83 @@ def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
     G.attraction_set_loss_kind("quadratic")
     out["loss_kinds"] = kinds
     return out
+
+
+KERNEL_TABLE = ["net_rc", "fwd_sweep", "ep_wns", "bwd_sweep", "topk", "pair_walk", "pp_fwd", "pp_bwd_net",
+                "pp_bwd_cell"]
+
+
+def kernel_table(G, step, k0, nl, info, reps=10):
+    """Live duration of every kernel of the iteration in the steady state (CUDA
+    events on the kernel's own stream, one kernel at a time), its algorithmic
+    bytes and the GB/s they make.  The backward sweep runs beside extraction,
+    the pair update and the loss, on its share of the SMs."""
+    import torch
+    out = {}
+    for name in KERNEL_TABLE:
+        G.tdp_profile_kernel(name)
+        for k in range(reps):
+            step(k0 + k)
+        G.sta_join()
+        torch.cuda.synchronize()
+        n, ms = G.tdp_profile_read()
+        G.tdp_profile_kernel(None)
+        if n == 0:
+            continue
+        per = ms / n
+        by = algorithmic_bytes(name, nl, info)
+        out[name] = {"ms": round(per, 4), "algorithmic_bytes": int(by), "gbs": round(by / (per / 1e3) / 1e9, 1)}
+    return out
+
+
+def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100):
+    """Steps of the attraction loss alone (forward + backward) on the current
+    pair set, as a placement step between two timing iterations runs it."""
+    import torch
+    def one(k):
+        x, y = xs[k % len(xs)], ys[k % len(ys)]
+        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
+        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+    for k in range(5):
+        one(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        one(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": round(1000.0 / ms, 1), "unit": "loss fwd+bwd steps/s", "ms_per_step": round(ms, 4)}
+
+
+def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15):
+    """The paper's use of the hot path in placement: the loss forward +
+    backward every step, a timing iteration (STA, extraction, pair update)
+    every `every` steps (m = 15, Section IV)."""
+    import torch
+    def one(k):
+        x, y = xs[k % len(xs)], ys[k % len(ys)]
+        if k % every == 0:
+            G.sta_propagate(x, y, T, sync=False)
+            G.extract_critical_paths(-1, K, False, sync=False)
+            G.attraction_update_pairs(W0, W1, sync=False)
+        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
+        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+    for k in range(every):
+        one(k)
+    G.sta_join()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        one(k)
+    G.sta_join()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": round(1000.0 / ms, 1), "unit": "placement steps/s", "steps": steps, "timing_every": every,
+            "ms_per_step": round(ms, 4)}
 
 
 def table1(G, x, y, T, reps=3):
