@@ -109,12 +109,18 @@ __global__ void k_rt_prep(Topo t, State<R> s) {
 // the chain records (one dependent load a cell; the next record is loaded
 // while this cell's inputs are visited) and, at each combinational cell on
 // it, visits the inputs other than the worst.
+// The frontier holds *nf nodes (read on the device; the grid covers an upper
+// bound); the count pass gives the threads beyond it a count of 0.
 template <typename R, bool WRITE>
 __global__ void __launch_bounds__(kRtThreads) k_rt_expand(Topo t, State<R> s, RtNodes<R> acc, int64_t lo,
-                                                         int64_t nf, const RtSel *sel, int32_t *cnt,
-                                                         const int64_t *off, RtNodes<R> stg) {
+                                                         int64_t n_grid, const int64_t *nf, const RtSel *sel,
+                                                         int32_t *cnt, const int64_t *off, RtNodes<R> stg) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
+    if (f >= n_grid) return;
+    if (f >= *nf) {
+        if (!WRITE) cnt[f] = 0;
+        return;
+    }
     const int64_t x = lo + f;
     const Key bound = sel->bound;
     int c = 0;
@@ -453,6 +459,14 @@ static tdp_status read_i64(const int64_t *d, cudaStream_t st, int64_t *h) {
     return TDP_OK;
 }
 
+// two device counts with one synchronisation
+static tdp_status read_i64x2(const int64_t *d0, const int64_t *d1, cudaStream_t st, int64_t *h0, int64_t *h1) {
+    TDP_CUDA(cudaMemcpyAsync(h0, d0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaMemcpyAsync(h1, d1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TDP_CUDA(cudaStreamSynchronize(st));
+    return TDP_OK;
+}
+
 // theta := the n-th lowest key among k1[0, n1) and k2[0, n2) within the
 // current bound (unchanged when there are fewer than n)
 static void select_bound(tdp_graph *g, RtSel *sel, unsigned *hist, const Key *k1, int64_t n1, const Key *k2,
@@ -499,7 +513,7 @@ tdp_status report_impl(tdp_graph *g, int64_t n, int keep_nonneg) {
     Grow<RtSel> sel(st);
     Grow<unsigned> hist(st);
     Grow<int32_t> flag(st), cnt(st);
-    Grow<int64_t> off(st);
+    Grow<int64_t> off(st), coff(st);
     GrowNodes<R> stg(st);
     RT_NEED(sel, 1);
     RT_NEED(hist, 256);
@@ -542,31 +556,34 @@ tdp_status report_impl(tdp_graph *g, int64_t n, int keep_nonneg) {
         k_rt_flags_le<R><<<div_up(n_stg, kRtThreads), kRtThreads, 0, st>>>(sv.key, n_stg, sel.p, flag.p);
         TDP_TRY(scan_i32_to_i64(g, flag.p, off.p, n_stg, st));
         k_rt_scatter<R><<<div_up(n_stg, kRtThreads), kRtThreads, 0, st>>>(sv, n_stg, sel.p, off.p, s.rt, n_acc);
-        int64_t kept = 0;
-        TDP_TRY(read_i64(off.p + n_stg, st, &kept));
+        // 1-2: count and scan the children within the bound of the new
+        // frontier [n_acc, n_acc + kept), kept = off[n_stg] on the device
+        // (the grid covers n_stg >= kept); then one host read of both sizes
         const int64_t lo = n_acc;
+        const int64_t *kept_dev = off.p + n_stg;
+        RT_NEED(cnt, n_stg);
+        RT_NEED(coff, n_stg + 1);
+        {
+            LaunchScope ls(g, KID_RT_EXPAND);
+            k_rt_expand<R, false><<<div_up(n_stg, kRtThreads), kRtThreads, 0, st>>>(t, s, s.rt, lo, n_stg, kept_dev,
+                                                                                   sel.p, cnt.p, nullptr, sv);
+        }
+        TDP_TRY(scan_i32_to_i64(g, cnt.p, coff.p, n_stg, st));
+        int64_t kept = 0, n_new = 0;
+        TDP_TRY(read_i64x2(kept_dev, coff.p + n_stg, st, &kept, &n_new));
         n_acc += kept;
         if (kept == 0) break;
         ++g->rt_rounds;
-
-        // 1-2: count, scan and write the frontier's children within the bound
-        RT_NEED(cnt, kept);
-        RT_NEED(off, kept + 1);
+        if (n_new == 0) break;
+        const int64_t n_grid = n_stg;
+        RT_NEED(stg, n_new);
         {
             LaunchScope ls(g, KID_RT_EXPAND);
-            k_rt_expand<R, false><<<div_up(kept, kRtThreads), kRtThreads, 0, st>>>(t, s, s.rt, lo, kept, sel.p,
-                                                                                  cnt.p, nullptr, sv);
-        }
-        TDP_TRY(scan_i32_to_i64(g, cnt.p, off.p, kept, st));
-        TDP_TRY(read_i64(off.p + kept, st, &n_stg));
-        if (n_stg == 0) break;
-        RT_NEED(stg, n_stg);
-        {
-            LaunchScope ls(g, KID_RT_EXPAND);
-            k_rt_expand<R, true><<<div_up(kept, kRtThreads), kRtThreads, 0, st>>>(t, s, s.rt, lo, kept, sel.p,
-                                                                                 nullptr, off.p, stg.view());
+            k_rt_expand<R, true><<<div_up(n_grid, kRtThreads), kRtThreads, 0, st>>>(t, s, s.rt, lo, n_grid, kept_dev,
+                                                                                   sel.p, nullptr, coff.p, stg.view());
         }
         TDP_LAUNCH_CHECK();
+        n_stg = n_new;
     }
     g->rt_nodes = n_acc;
     if (n_acc == 0) return TDP_OK;
