@@ -107,6 +107,9 @@ def test_null_handles(lib):
     assert lib.attraction_loss_fwd(None, None, None, 1.0, None) == _abi.TDP_ERR_INVALID
     assert lib.attraction_loss_bwd(None, None, None, 1.0, None, None, None) == _abi.TDP_ERR_INVALID
     assert lib.sta_get_paths(None, None, None, None, None, None) == _abi.TDP_ERR_INVALID
+    assert lib.report_timing(None, 10, 0, None) == _abi.TDP_ERR_INVALID
+    assert lib.sta_join(None) == _abi.TDP_ERR_INVALID
+    assert lib.attraction_set_loss_kind(None, 0) == _abi.TDP_ERR_INVALID
     lib.sta_destroy(None)
     h = C.c_void_p()
     assert lib.sta_build(None, 0, None, C.byref(h)) == _abi.TDP_ERR_INVALID
