@@ -209,8 +209,10 @@ constexpr int kTopkWarps = 4;
 // its frontier one candidate per lane, its paths in shared slots g * KP + r.
 // Reductions, ballots and the tie order stay within a group; the warp loops
 // until every group is done.
+// (at most 32 registers a thread, as the pair walk: four blocks beside a
+// block of the backward sweep)
 template <typename R>
-__global__ void __launch_bounds__(kTopkWarps * 32) k_topk(Topo t, State<R> s, int K, int KP, int G,
+__global__ void __launch_bounds__(kTopkWarps * 32, 16) k_topk(Topo t, State<R> s, int K, int KP, int G,
                                                           int keep_nonneg, int n_cap) {
     __shared__ int sh_par[kTopkWarps][32], sh_side[kTopkWarps][32];
     __shared__ int sh_len[kTopkWarps][32];

@@ -28,8 +28,10 @@ constexpr int kWalkWarps = 4;
 // in the same step are merged (__match_any_sync): the lowest such lane adds
 // the group's summed q and raises the maximum once for all of them (sums and
 // maxima do not depend on how the lanes are grouped).
+// (at most 32 registers a thread: beside a block of the backward sweep an SM
+// then holds four blocks of this kernel instead of three)
 template <typename R>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_pair_walk(Topo t, State<R> s, int K, int KP, int n_cap) {
+__global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State<R> s, int K, int KP, int n_cap) {
     __shared__ long long shQ[kWalkWarps][32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
