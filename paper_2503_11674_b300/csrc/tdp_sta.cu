@@ -12,10 +12,11 @@
 //                TNS over them (FP64, fixed-order reduction); they need the
 //                forward sweep only
 //   k_bwd_sweep  the backward sweep in one cooperative launch: required times
-//                of the nets driven from each level, deepest first (lane per
-//                net of at most 8 sinks, warp per 128 sinks of larger nets,
-//                split nets combined by the last warp to finish), and the
-//                slacks of every other pin.  Nothing later in a timing
+//                of the nets driven from each level, deepest first (a net of
+//                at most 8 sinks on an aligned group of 1, 2 or 4 lanes, a
+//                warp per 64-sink piece of a larger net, the pieces combined
+//                by an atomic min on an order-preserving key), and the slacks
+//                of every other pin.  Nothing later in a timing
 //                iteration reads what it writes, so it runs on a second stream
 //                beside path extraction, the pair update and the loss.
 //
