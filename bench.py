@@ -162,10 +162,10 @@ LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single c
 SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     "fwd_sweep": {"bytes": 477399552, "sources": SWEEP_SOURCES,
-                  "sha256": "60904a8106773c147aeecf6325e856e7166bedd50975670e90ca73b62db23c82",
+                  "sha256": "a1d55675f002ebd28ef4f3bb53292f179ea5548c18feb22bbb4c759133dc4ca1",
                   "profile": "profiles/fwd_sweep_1.2M.md"},
     "bwd_sweep": {"bytes": 434253056, "sources": SWEEP_SOURCES,
-                  "sha256": "60904a8106773c147aeecf6325e856e7166bedd50975670e90ca73b62db23c82",
+                  "sha256": "a1d55675f002ebd28ef4f3bb53292f179ea5548c18feb22bbb4c759133dc4ca1",
                   "profile": "profiles/bwd_sweep_1.2M.md"},
 }
 
