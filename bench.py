@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="1.2M")
+    ap.add_argument("--K", type=int, default=None, help="paths per failing endpoint (default: the config's)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--roofline-kernel", default=ROOFLINE_KERNEL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -141,10 +142,11 @@ class ClockSampler:
 
 def workload_desc(cfg, nl):
     st = nl.stats()
+    K = cfg.K
     return {"workload": f"{cfg.name}: {st['cells']:,} cells ({cfg.n_ff:,} FF, {st['pi']:,} PI, {st['po']:,} PO), "
-                        f"{st['nets']:,} nets, {st['pins']:,} pins, depth {cfg.depth}, K={cfg.K}, "
+                        f"{st['nets']:,} nets, {st['pins']:,} pins, depth {cfg.depth}, K={K}, "
                         f"clock {cfg.t_factor}x max arrival",
-            "cells": st["cells"], "nets": st["nets"], "pins": st["pins"], "depth": cfg.depth, "K": cfg.K,
+            "cells": st["cells"], "nets": st["nets"], "pins": st["pins"], "depth": cfg.depth, "K": K,
             "max_fanout": st["max_fanout"], "t_factor": cfg.t_factor}
 
 
@@ -154,7 +156,7 @@ def workload_desc(cfg, nl):
 # TDP_LEVEL_GRAPHS=1, one CUDA-graph replay of a kernel per level); its
 # "launch" for the roofline is the whole sweep.
 LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single cooperative launch)",
-               "bwd_sweep": "one backward sweep over all logic levels plus WNS/TNS (a single cooperative launch)"}
+               "bwd_sweep": "one backward sweep over all logic levels (a single cooperative launch)"}
 
 # DRAM bytes (read + write) per launch from an ncu capture of the 1.2M-cell
 # workload, with the SHA-256 of the sources the kernel was built from when it
@@ -265,6 +267,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = netgen.CONFIGS[args.config]
+    if args.K:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, K=args.K)
     seed = args.seed + rank                       # independent replica per rank
     nl = netgen.generate(cfg, seed)
     G = TimingGraph(nl, "fp32", device=dev)
@@ -717,6 +722,9 @@ def run_reference(args):
     if rank != 0:
         return None
     cfg = netgen.CONFIGS[args.config]
+    if args.K:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, K=args.K)
     nl = netgen.generate(cfg, args.seed)
     import numpy as np
     import oracle
