@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-table1", action="store_true",
                     help="skip Table I's comparison of report_timing(n) with report_timing_endpoint(n, k)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-on-GPU comparison run")
+    ap.add_argument("--no-incremental", action="store_true",
+                    help="skip the incremental-timing measurements (sta_propagate_incremental)")
     return ap.parse_args()
 
 
@@ -410,6 +412,7 @@ def run_ours(args):
     ktab = kernel_table(G, step, args.warmup + args.steps, nl, info)
     lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
     ploop = placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream)
+    incr = None if args.no_incremental else incremental(G, xs, ys, T, K, mv, stream)
     t1 = table1(G, xs[0], ys[0], T) if not args.no_table1 else None
     fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
 
@@ -456,6 +459,8 @@ def run_ours(args):
         result["kernels"] = ktab
         result["loss_only"] = lonly
         result["placement_loop"] = ploop
+        if incr:
+            result["incremental"] = incr
         if stages:
             result["stages_ms"] = stages
         if t1:
@@ -633,6 +638,83 @@ def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=1
     ms = e0.elapsed_time(e1) / steps
     return {"value": round(1000.0 / ms, 1), "unit": "placement steps/s", "steps": steps, "timing_every": every,
             "ms_per_step": round(ms, 4)}
+
+
+INC_MOVED = (1, 12, 120, 1200, 12000, 120000, None)  # cells moved per call; None: every movable cell
+
+
+def incremental(G, xs, ys, T, K, mv, stream, reps=20):
+    """Incremental timing (sta_propagate_incremental) on this workload.  For
+    each number of moved cells, calls alternate between a placement and the
+    same with that many movable cells moved (seeded Gaussian, sigma as the
+    placements), so that every call sees that many moves.  Per call (median
+    of `reps`, CUDA events on the library stream): the graph's stream until
+    WNS / TNS are ready, the same with the backward sweep joined, and a whole
+    timing iteration (incremental STA, extraction, pair update, loss);
+    beside them the full sta_propagate, and what the library re-evaluated."""
+    import torch
+    dev = xs.device
+    n = xs.shape[1]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(77)
+    movable = torch.nonzero(mv).flatten()
+    x0, y0 = xs[0].clone(), ys[0].clone()
+    buf = torch.zeros((), dtype=torch.float64, device=dev)
+    gx = torch.empty(n, dtype=torch.float32, device=dev)
+    gy = torch.empty(n, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def med(v):
+        return round(sorted(v)[len(v) // 2], 4)
+
+    def measure(prop, pos):
+        for r in range(2):
+            prop(*pos[(r + 1) % 2], T, sync=False)
+        G.sta_join()
+        t_main, t_all, t_it = [], [], []
+        for r in range(2 * reps):
+            x, y = pos[(r + 1) % 2]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            prop(x, y, T, sync=False)
+            ev[1].record(stream)
+            if r < reps:
+                G.sta_join()
+            else:
+                G.extract_critical_paths(-1, K, False, sync=False)
+                G.attraction_update_pairs(W0, W1, sync=False)
+                G.attraction_loss_fwd(x, y, BETA, out=buf)
+                G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+                G.sta_join()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if r < reps:
+                t_main.append(ev[0].elapsed_time(ev[1]))
+                t_all.append(ev[0].elapsed_time(ev[2]))
+            else:
+                t_it.append(ev[0].elapsed_time(ev[2]))
+        return {"propagate_ms": med(t_main), "propagate_with_bwd_ms": med(t_all), "iteration_ms": med(t_it)}
+
+    G.sta_propagate_incremental(x0, y0, T)
+    G.extract_critical_paths(-1, K, False)  # sidetrack lists of the iteration's length
+    rows = []
+    for m in INC_MOVED:
+        if m is None:
+            x1, y1 = xs[1], ys[1]
+        else:
+            idx = movable[torch.randperm(movable.numel(), generator=gen, device=dev)[:m]]
+            x1, y1 = x0.clone(), y0.clone()
+            x1[idx] += SIGMA * torch.randn(m, generator=gen, device=dev)
+            y1[idx] += SIGMA * torch.randn(m, generator=gen, device=dev)
+        row = {"moved_cells": m if m is not None else int(movable.numel())}
+        row.update(measure(G.sta_propagate_incremental, [(x0, y0), (x1, y1)]))
+        st = G.incremental_stats()
+        row.update({"cells_evaluated_selectively": st["cells_evaluated"], "cells_changed": st["cells_changed"],
+                    "levels": [st["first_level"], st["last_level"]],
+                    "every_cell_from_level": st["every_cell_from_level"], "fell_back_to_full": bool(st["full"])})
+        rows.append(row)
+    full = measure(G.sta_propagate, [(x0, y0), (xs[1], ys[1])])
+    return {"unit": "ms per call", "K": K, "rows": rows, "full_sta_propagate": full}
 
 
 def table1(G, x, y, T, reps=3):

@@ -149,6 +149,51 @@ TDP_API tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void *y_
                          double clock_period_ps, double *wns_out, double *tns_out);
 
 /*
+ * Incremental timing: the same results as sta_propagate, bit for bit, for
+ * positions that differ from those of the graph's last propagation in a
+ * few cells only.  Section IV re-times the design every m placement steps;
+ * between two such points few cells may have moved (or, in a loop that
+ * moves cells one at a time, one).  The call compares x_dev / y_dev with the
+ * positions of the last propagation (bit for bit) and re-times:
+ *   - the nets with a pin on a moved cell (Eq. (8): Elmore delays, load,
+ *     delay of the driving cell), each counted as changed;
+ *   - in the forward sweep, only the cells with a changed input or delay,
+ *     over the levels the changes reach; a re-evaluated cell whose arrival,
+ *     worst input, chain length and sidetrack list come out unchanged stops
+ *     the change there.  Once a level's changed cells exceed 1/16 of the
+ *     next level's cells, every later cell is evaluated without checks
+ *     (changes spread through the sidetrack lists to most cells downstream);
+ *   - the endpoints, WNS / TNS and the backward sweep in full (the backward
+ *     sweep runs beside later calls, as in sta_propagate).
+ * Arguments, outputs, stream order and errors as for sta_propagate.  The
+ * first call on a graph, and any call after which the previous state cannot
+ * serve (no earlier propagation, a failed one, per-level launches instead of
+ * a single launch), re-times everything.  From the first call on, the graph
+ * keeps the positions of every propagation (sta_propagate too): 2 * n_cells
+ * floats or doubles, plus 16 bytes per net.
+ */
+TDP_API tdp_status sta_propagate_incremental(tdp_graph *g, const void *x_dev, const void *y_dev,
+                                             double clock_period_ps, double *wns_out, double *tns_out);
+
+/*
+ * What the last propagation re-timed (synchronises the graph's stream).
+ * stats_out: host int64_t[7]:
+ *   [0] 1 if it re-timed everything (sta_propagate, or a first or fallback
+ *       sta_propagate_incremental; then [1]..[5] count every cell and
+ *       level), else 0
+ *   [1] cells that moved
+ *   [2] combinational cells re-evaluated selectively (an input or the
+ *       cell's delay changed) in the forward sweep
+ *   [3] of them, cells whose outputs changed
+ *   [4], [5] first and last level of the forward sweep (0, -1: none)
+ *   [6] level from which the sweep evaluated every cell, without checks
+ *       (0: none): once the changed cells of a level exceed 1/16 of the
+ *       next level's cells, checking costs more than it saves
+ * Errors: TDP_ERR_STATE before the first propagation.
+ */
+TDP_API tdp_status sta_incremental_stats(tdp_graph *g, int64_t *stats_out);
+
+/*
  * Make the graph's stream wait for the backward sweep of the last
  * sta_propagate (queued on the library's second stream).  No-op if nothing
  * is outstanding.  Does not synchronise the host.

@@ -23,7 +23,7 @@ EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_g
            "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
            "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
            "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "attraction_set_loss_kind", "report_timing", "sta_join",
-           "tdp_last_error"]
+           "sta_propagate_incremental", "sta_incremental_stats", "tdp_last_error"]
 
 
 class NetlistDesc(C.Structure):
@@ -77,6 +77,8 @@ def load() -> C.CDLL:
         "attraction_set_loss_kind": [P, C.c_int],
         "report_timing": [P, I32, I32, P],
         "sta_join": [P],
+        "sta_propagate_incremental": [P, P, P, D, P, P],
+        "sta_incremental_stats": [P, P],
         "tdp_last_error": [],
     }
     for name, args in sig.items():

@@ -457,7 +457,8 @@ namespace tdp {
 
 const char *const kKernelNames[KID_COUNT] = {"net_rc",    "fwd_sweep",   "bwd_sweep", "viol_sort",
                                               "topk",      "pair_walk",   "pair_finish", "pp_fwd",
-                                              "pp_bwd_net", "pp_bwd_cell", "rt_expand", "ep_wns"};
+                                              "pp_bwd_net", "pp_bwd_cell", "rt_expand", "ep_wns",
+                                              "inc_moved", "fwd_inc"};
 
 static cudaEvent_t prof_event(tdp_graph *g) {
     if (!g->prof_free.empty()) {
@@ -507,6 +508,7 @@ tdp_status check_sync_status(tdp_graph *g) {
     TDP_CUDA(cudaMemsetAsync(w + 1, 0, sizeof(unsigned), g->stream));
     g->propagated = false;
     g->extracted = false;
+    g->inc_valid = false;
     set_error("a level sweep's grid-wide wait gave up after %.1f s; timing results are not valid",
               kSyncTimeoutNs * 1e-9);
     return TDP_ERR_TIMEOUT;

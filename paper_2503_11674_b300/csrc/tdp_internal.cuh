@@ -61,7 +61,8 @@ constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 // the WNS / TNS reduction.
 enum KernelId {
     KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
-    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_EP_WNS, KID_COUNT
+    KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_EP_WNS,
+    KID_INC_MOVED, KID_FWD_INC, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -338,6 +339,25 @@ struct Topo {
     int4 *bw_lv = nullptr;
 };
 
+// Incremental propagation (sta_propagate_incremental).  Every array is
+// indexed by net; a stamp equal to `cur` (the number of the current
+// incremental call) marks the net for this call only, so nothing is cleared
+// between calls.
+struct Inc {
+    int32_t *stamp = nullptr;   // a cell on the net moved, or its driver's outputs changed
+    int2 *span = nullptr;       // (lo, hi): levels of the cells a change of the net reaches
+                                // (its driving cell when combinational, its sinks' cells)
+    int2 *cspan = nullptr;      // [n_cells] the spans of a cell's nets, combined
+    // [3] levels the changes of this call reach; the level after which they
+    // saturated, plus one (INT_MAX: they did not)
+    int32_t *lohi = nullptr;
+    int32_t *lvchg = nullptr;   // [depth + 2] cells whose outputs changed, per level
+    // [3] moved cells, cells re-evaluated selectively, of them cells with
+    // changed outputs
+    unsigned long long *cnt = nullptr;
+    int cur = 0;
+};
+
 // Host copies of the launch structure of the level sweeps.
 struct Levels {
     std::vector<int32_t> lvl_ptr;   // comb cells of level l: [lvl_ptr[l-1], lvl_ptr[l])
@@ -417,6 +437,8 @@ struct State {
     // the slack a sidetrack through it costs
     int4 *rt_chain = nullptr;
     R *rt_delta = nullptr;
+    // incremental propagation: cell positions of the last propagation
+    R *xprev = nullptr, *yprev = nullptr;
     int32_t *rt_out = nullptr;
     int64_t *rt_side_off = nullptr;
     int32_t *rt_sides = nullptr;
@@ -453,6 +475,11 @@ struct tdp_graph {
     int64_t rt_n_out = 0, rt_n_sides = 0;
     int64_t rt_cap = 0, rt_out_cap = 0, rt_soff_cap = 0, rt_sides_cap = 0;  // buffer capacities
     int rt_rounds = 0;                                     // expansion rounds of the last report
+    // incremental propagation: inc_valid while the state holds the timing of
+    // the positions in xprev / yprev; inc_full when the last incremental call
+    // re-timed everything
+    tdp::Inc inc;
+    bool inc_valid = false, inc_full = true;
     int64_t rt_nodes = 0;                                  // nodes the last report kept
     // level sweeps: one cooperative launch each (single_launch), else CUDA
     // graphs of one kernel per level

@@ -28,6 +28,7 @@
 // barrier are read from L2.  Either way all loads of a group of inputs /
 // sinks are issued before the first store.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "tdp_internal.cuh"
@@ -45,6 +46,12 @@ __device__ __forceinline__ fx2 acc_from_double<float>(double v) {
 }
 
 // ------------------------------------------------------------- net RC ---
+
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_bits(fx2 a, fx2 b) { return same_bits(a.hi, b.hi) && same_bits(a.lo, b.lo); }
 
 template <typename R>
 __device__ __forceinline__ void net_finish(const Topo &t, State<R> &s, int e, int drv, int cd,
@@ -80,14 +87,18 @@ constexpr int kRcThreads = 256;
 
 // Blocks [0, n_small_blocks): one thread per net with at most kBigFanout sinks.
 // Blocks after that: one block per high-fanout net (FP64 load sum, fixed order).
+// inc.cur != 0 (an incremental call): only the nets k_inc_moved stamped are
+// re-timed, by the same code.
 template <typename R>
 __global__ void __launch_bounds__(kRcThreads) k_net_rc(Topo t, State<R> s, const R *__restrict__ x,
                                                        const R *__restrict__ y, double T, R r, R c,
-                                                       R d0, int n_small_blocks) {
+                                                       R d0, int n_small_blocks, Inc inc) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *s.T = T;
+    const bool incr = inc.cur != 0;
     if ((int)blockIdx.x < n_small_blocks) {
         const int e = blockIdx.x * kRcThreads + threadIdx.x;
         if (e >= t.n_nets) return;
+        if (incr && ldg(&inc.stamp[e]) != inc.cur) return;
         const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
         if (b - a - 1 > kBigFanout) return;
         // FP32 sum for nets of at most kBigFanout sinks
@@ -108,6 +119,7 @@ __global__ void __launch_bounds__(kRcThreads) k_net_rc(Topo t, State<R> s, const
     }
     __shared__ double part[kRcThreads / 32];
     const int e = ldg(&t.big_nets[blockIdx.x - n_small_blocks]);
+    if (incr && ldg(&inc.stamp[e]) != inc.cur) return;  // the whole block
     const int a = ldg(&t.net_ptr[e]), b = ldg(&t.net_ptr[e + 1]);
     double load = sinks_rc<R>(t, s, x, y, a, b, a + 1 + threadIdx.x, kRcThreads, r, c);
     for (int o = 16; o > 0; o >>= 1) load += __shfl_xor_sync(0xffffffffu, load, o);
@@ -362,6 +374,33 @@ __device__ __forceinline__ void list_put(BEnt<double> *dst, const LEnt<double> (
     for (int j = 0; j < L; ++j) dst[j] = BEnt<double>{li[j].d, lreg_pin<double>(li[j])};
 }
 
+// whether the stored list at dst holds, bit for bit, what list_put(dst, li)
+// would write
+template <int L>
+__device__ __forceinline__ bool list_same(const BEnt<float> *dst, const uint64_t (&li)[L]) {
+    const float4 *v4 = reinterpret_cast<const float4 *>(dst);
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < list_group(L) / 2; ++q) {
+        const uint64_t x = 2 * q < L ? li[2 * q] : LReg<float>::none();
+        const uint64_t y = 2 * q + 1 < L ? li[2 * q + 1] : LReg<float>::none();
+        const float4 o = __ldcg(&v4[q]);
+        same = same && same_bits(o.x, LReg<float>::cost(x)) && __float_as_int(o.y) == lreg_pin<float>(x) &&
+               same_bits(o.z, LReg<float>::cost(y)) && __float_as_int(o.w) == lreg_pin<float>(y);
+    }
+    return same;
+}
+template <int L>
+__device__ __forceinline__ bool list_same(const BEnt<double> *dst, const LEnt<double> (&li)[L]) {
+    bool same = true;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const BEnt<double> o = ldcg(&dst[j]);
+        same = same && same_bits(o.delta, li[j].d) && o.pin == lreg_pin<double>(li[j]);
+    }
+    return same;
+}
+
 // One cell for one thread: cell k (k < 0: none), its inputs when it has at
 // most kPre, and, once loaded (vals), the values that stay fixed during the
 // sweep (the cell delay, the inputs' Elmore delays) and the arrival and chain
@@ -433,18 +472,20 @@ __device__ __forceinline__ void cell_vals(const State<R> &s, CellPre<R> &c) {
 // Arrival of one cell (Section II-B: max over its inputs of the driver's
 // arrival plus the Elmore delay, plus the cell delay) and, when L > 0, its
 // sidetrack list.  COH: the drivers' values were written by other blocks of
-// the same launch.
+// the same launch.  CMP: returns whether the cell's output arrival, worst
+// input, chain length or list differs, bit for bit, from what was stored
+// before (a cell of more than kPre inputs always counts as changed).
 
-template <typename R, int L, bool COH>
-__device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, const CellPre<R> &c) {
+template <typename R, int L, bool COH, bool CMP = false>
+__device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellPre<R> &c) {
     using AC = Acc<R>;
     using A = typename AC::T;
     using LR = LReg<R>;
-    if (c.k < 0) return;
+    if (c.k < 0) return false;
     const int nin = c.b - c.a;
     if (nin > kPre) {
         fwd_cell_wide<R, L, COH>(t, s, c.k, c.a, c.b);
-        return;
+        return true;
     }
     // every load first, then the arithmetic, then the stores
     const R dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
@@ -481,6 +522,12 @@ __device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, const CellP
             }
         }
     }
+    bool chg = false;
+    if constexpr (CMP) {
+        const int2 op = ldcg(&s.pred[c.e]);
+        chg = !same_bits(ldcg(&s.arr[c.o]), AC::add(best, dcell)) || op.x != bi || op.y != bn ||
+              ldcg(&s.plen[c.e]) != bl + 2;
+    }
 #pragma unroll
     for (int u = 0; u < kPre; ++u)
         if (u < nin) s.arr[c.ip[u]] = av[u];
@@ -504,12 +551,19 @@ __device__ __forceinline__ void fwd_cell(const Topo &t, State<R> &s, const CellP
             const uint32_t key = ((c.ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)c.ip[u];
             list_insert<R, L>(li, own ? LR::make(AC::diff(best, av[u]), key) : LR::none());
         }
+        if constexpr (CMP) {
+            int m = 0;
+#pragma unroll
+            for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
+            chg = chg || ldcg(&s.bcnt[c.e]) != m || !list_same<L>(s.blist + (size_t)c.e * G, li);
+        }
         list_put<L>(s.blist + (size_t)c.e * G, li);
         int m = 0;
 #pragma unroll
         for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
         s.bcnt[c.e] = m;
     }
+    return chg;
 }
 
 // One launch per level (captured in a CUDA graph): a thread per cell.
@@ -548,9 +602,13 @@ constexpr int kBwdThreads = 512;
 // closes level l and the wait, it loads, in one round, the final values of
 // its level l + 1 cell (cell delay, Elmore delays, drivers two or more
 // levels down) and the topology of its level l + 2 cell, so that after the
-// barrier only the values level l wrote are left to load.
+// barrier only the values level l wrote are left to load.  from (if not
+// NULL): the first level to evaluate, in device memory (an incremental
+// propagation hands over the levels after the one where its changes
+// saturated; past the last level: nothing to do); else level 1.
 template <typename R, int L>
-__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s, GridSync gs) {
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s, GridSync gs,
+                                                               const int *from) {
     const int lane = threadIdx.x & 31;
     const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;  // first chunk of this warp
     const int wstride = (blockDim.x >> 5) * gridDim.x;
@@ -559,10 +617,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s
         const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * 32 + lane;
         return k < ldg(&t.lvl_ptr[l]) ? k : -1;
     };
+    const int l0 = from ? max(ldcg(from), 1) : 1;
+    if (l0 > t.depth) return;
     CellPre<R> cur, nxt;
-    cell_topo(t, cell_of(1, w0), cur);
-    cell_topo(t, cell_of(2, w0), nxt);
-    for (int l = 1; l <= t.depth; ++l) {
+    cell_topo(t, cell_of(l0, w0), cur);
+    cell_topo(t, cell_of(l0 + 1, w0), nxt);
+    for (int l = l0; l <= t.depth; ++l) {
         const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), 32);
         if (w0 < nch) {
             fwd_cell<R, L, true>(t, s, cur);
@@ -577,7 +637,229 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s
         cur = nxt;
         cell_vals(s, cur);                // drivers below level l are final
         cell_topo(t, cell_of(l + 2, w0), nxt);
-        if (!grid_wait(gs, (unsigned)l * gridDim.x)) return;
+        if (!grid_wait(gs, (unsigned)(l - l0 + 1) * gridDim.x)) return;
+    }
+}
+
+// ----------------------------------------------------- incremental ---
+//
+// sta_propagate_incremental re-times only what the moved cells reach, with
+// the code of the full propagation, so that its results are bit for bit
+// those of a full one:
+//   k_inc_moved      cells whose position differs (bit for bit) from the
+//                    last propagation: record the new one, stamp their nets
+//                    (their delays may change) and widen the call's level
+//                    span [lo, hi] to the levels those nets reach
+//   k_net_rc         (incremental mode) re-times the stamped nets
+//   k_fwd_sweep_inc  levels lo .. hi: a cell is re-evaluated when its net or
+//                    an input's net is stamped; a re-evaluated cell whose
+//                    outputs changed stamps its net and raises hi to the
+//                    deepest level that net reaches; once the changes of a
+//                    level saturate, it stops and k_fwd_sweep evaluates every
+//                    cell of the levels after
+
+// Level span of each net: the level of its driving cell when that is
+// combinational (its delay depends on the net's load), and the levels of
+// the combinational cells it feeds.  (INT_MAX, 0) when there are none.
+__global__ void k_inc_span(Topo t, int2 *span) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= t.n_nets) return;
+    const int d = ldg(&t.net_level[e]);
+    int lo = d >= 1 ? d : INT_MAX, hi = d;
+    for (int p = ldg(&t.net_ptr[e]) + 1; p < ldg(&t.net_ptr[e + 1]); ++p) {
+        const int on = ldg(&t.sink_onet[p]);
+        if (on < 0) continue;
+        const int l = ldg(&t.net_level[on]);
+        lo = min(lo, l);
+        hi = max(hi, l);
+    }
+    span[e] = make_int2(lo, hi);
+}
+
+// Level span of each cell: the spans of the nets of its pins, combined.
+__global__ void k_inc_cspan(Topo t, const int2 *span, int2 *cspan) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= t.n_cells) return;
+    int lo = INT_MAX, hi = 0;
+    for (int q = ldg(&t.cp_ptr[c]); q < ldg(&t.cp_ptr[c + 1]); ++q) {
+        const int2 sp = ldg(&span[ldg(&t.pin_net[ldg(&t.cp[q])])]);
+        lo = min(lo, sp.x);
+        hi = max(hi, sp.y);
+    }
+    cspan[c] = make_int2(lo, hi);
+}
+
+__global__ void k_inc_reset(Inc inc) {
+    if (threadIdx.x < 3) inc.cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+        inc.lohi[0] = INT_MAX;
+        inc.lohi[1] = 0;
+        inc.lohi[2] = INT_MAX;
+    }
+}
+
+// Widen the call's level span (checked first: the atomics fire only while
+// the span grows).
+__device__ __forceinline__ void inc_widen(const Inc &inc, int lo, int hi) {
+    if (lo < ldcg(&inc.lohi[0])) atomicMin(&inc.lohi[0], lo);
+    if (hi > ldcg(&inc.lohi[1])) atomicMax(&inc.lohi[1], hi);
+}
+
+template <typename R>
+__global__ void k_inc_moved(Topo t, const R *__restrict__ x, const R *__restrict__ y, R *xp, R *yp, Inc inc) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (c < t.n_cells) {
+        const R xv = ldg(&x[c]), yv = ldg(&y[c]);
+        mv = !same_bits(xv, xp[c]) || !same_bits(yv, yp[c]);
+        if (mv) {
+            xp[c] = xv;
+            yp[c] = yv;
+            for (int q = ldg(&t.cp_ptr[c]); q < ldg(&t.cp_ptr[c + 1]); ++q)
+                inc.stamp[ldg(&t.pin_net[ldg(&t.cp[q])])] = inc.cur;
+            const int2 sp = ldg(&inc.cspan[c]);
+            inc_widen(inc, sp.x, sp.y);
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, mv);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&inc.cnt[0], (unsigned long long)__popc(bal));
+}
+
+// Stamps of cell c that are final before the barrier opening its level: its
+// own net (its delay) and the nets of inputs driven two or more levels down.
+// (Bitwise or, not ||: the loads are issued together.)
+template <typename R>
+__device__ __forceinline__ bool inc_dirty_old(const Inc &inc, const CellPre<R> &c) {
+    if (c.k < 0) return false;
+    bool d = ldcg(&inc.stamp[c.e]) == inc.cur;
+    if (c.b - c.a <= kPre) {
+#pragma unroll
+        for (int u = 0; u < kPre; ++u)
+            if (u < c.b - c.a && !((c.fl >> (8 * u)) & kInPrev)) d |= ldcg(&inc.stamp[c.in[u]]) == inc.cur;
+    }
+    return d;
+}
+
+// One cell of the incremental sweep.  After the barrier, in one round: the
+// stamps of the inputs driven by the level below and (whether or not they
+// show a change) those drivers' arrivals and chain lengths, the only values
+// cell_vals left out.  If a stamp is set, the cell's full evaluation, which
+// then loads nothing but the worst input's list.  A wide cell (more than
+// kPre inputs) checks every input's stamp first.
+template <typename R, int L>
+__device__ __forceinline__ void inc_cell(const Topo &t, State<R> &s, const Inc &inc, CellPre<R> &c, bool d,
+                                         int &hi, unsigned &n_eval, unsigned &n_chg) {
+    if (c.k < 0) return;
+    const int nin = c.b - c.a;
+    if (nin > kPre) {
+        for (int p = c.a; p < c.b && !d; ++p) d = ldcg(&inc.stamp[ldg(&t.lv_in_net[p])]) == inc.cur;
+    } else {
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (u < nin && ((c.fl >> (8 * u)) & kInPrev)) {
+                d |= ldcg(&inc.stamp[c.in[u]]) == inc.cur;
+                c.ad[u] = ldcg(&s.arr[c.dv[u]]);
+                c.pl[u] = ldcg(&s.plen[c.in[u]]);
+                c.old |= 1u << u;
+            }
+        }
+    }
+    if (!d) return;
+    ++n_eval;
+    if (fwd_cell<R, L, true, true>(t, s, c)) {
+        inc.stamp[c.e] = inc.cur;
+        hi = max(hi, ldg(&inc.span[c.e]).y);
+        ++n_chg;
+    }
+}
+
+// A level whose changed cells exceed 1/kIncSaturate of the next level's
+// cells ends the selective part of the sweep: k_fwd_sweep, launched after
+// it, evaluates every cell of the following levels, without stamps or
+// comparisons.  The changes of a few moved cells spread through the
+// sidetrack lists to most of the cells downstream, and there the checks only
+// lengthen each level.
+constexpr int kIncSaturate = 16;
+
+// The incremental forward sweep: one cooperative launch over levels lo .. hi
+// of this call (hi grows as changes reach deeper cells), the layout of
+// k_fwd_sweep (a thread per cell, chunk j of a level on block j mod
+// gridDim; in the barrier window, the next level's values and stamps that
+// are already final and the topology of the level after).  When the
+// changes saturate after level l, it records l + 1 in lohi[2] and stops.
+// Every block reads the same lo; a block may read a larger hi than another
+// after a barrier, but only once some block has continued past it, so all
+// blocks leave the loop after the same level.
+template <typename R, int L>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep_inc(Topo t, State<R> s, GridSync gs, Inc inc) {
+    __shared__ int blk_hi;
+    const int lane = threadIdx.x & 31;
+    const int w0 = blockIdx.x + (threadIdx.x >> 5) * gridDim.x;
+    const int wstride = (blockDim.x >> 5) * gridDim.x;
+    auto cell_of = [&](int l, int chunk) {
+        if (l > t.depth) return -1;
+        const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * 32 + lane;
+        return k < ldg(&t.lvl_ptr[l]) ? k : -1;
+    };
+    __shared__ int blk_chg;
+    const int lo = ldcg(&inc.lohi[0]);
+    int hi = min(ldcg(&inc.lohi[1]), t.depth);
+    unsigned n_eval = 0, n_chg = 0, nbar = 0;
+    if (threadIdx.x == 0) blk_hi = blk_chg = 0;
+    __syncthreads();
+    CellPre<R> cur, nxt;
+    bool cur_d = false;
+    if (lo <= hi) {
+        cell_topo(t, cell_of(lo, w0), cur);
+        cell_topo(t, cell_of(lo + 1, w0), nxt);
+        cell_vals(s, cur);
+        cur_d = inc_dirty_old(inc, cur);
+    }
+    for (int l = lo; l <= hi; ++l) {
+        const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), 32);
+        int h = 0;
+        const unsigned c0 = n_chg;
+        if (w0 < nch) {
+            inc_cell<R, L>(t, s, inc, cur, cur_d, h, n_eval, n_chg);
+            for (int ch = w0 + wstride; ch < nch; ch += wstride) {
+                CellPre<R> c;
+                cell_topo(t, cell_of(l, ch), c);
+                cell_vals(s, c);
+                inc_cell<R, L>(t, s, inc, c, inc_dirty_old(inc, c), h, n_eval, n_chg);
+            }
+        }
+        h = __reduce_max_sync(0xffffffffu, h);
+        const unsigned dc = __reduce_add_sync(0xffffffffu, n_chg - c0);
+        if (lane == 0 && h > 0) atomicMax(&blk_hi, h);
+        if (lane == 0 && dc > 0) atomicAdd(&blk_chg, (int)dc);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // before this thread's release arrival below
+            if (blk_hi > 0) atomicMax(&inc.lohi[1], blk_hi);
+            if (blk_chg > 0) atomicAdd(&inc.lvchg[l], blk_chg);
+            blk_hi = blk_chg = 0;
+        }
+        if (l == t.depth) break;
+        grid_arrive(gs);
+        ++nbar;
+        cur = nxt;
+        cell_vals(s, cur);                // values and stamps below level l are final
+        cur_d = inc_dirty_old(inc, cur);
+        cell_topo(t, cell_of(l + 2, w0), nxt);
+        if (!grid_wait(gs, nbar * gridDim.x)) return;
+        // the same counts in every block: level l's are final after the barrier
+        const int next = ldg(&t.lvl_ptr[l + 1]) - ldg(&t.lvl_ptr[l]);
+        if ((long long)ldcg(&inc.lvchg[l]) * kIncSaturate > next) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) inc.lohi[2] = l + 1;
+            break;
+        }
+        hi = min(ldcg(&inc.lohi[1]), t.depth);
+    }
+    n_eval = __reduce_add_sync(0xffffffffu, n_eval);
+    n_chg = __reduce_add_sync(0xffffffffu, n_chg);
+    if (lane == 0 && n_eval) {
+        atomicAdd(&inc.cnt[1], (unsigned long long)n_eval);
+        if (n_chg) atomicAdd(&inc.cnt[2], (unsigned long long)n_chg);
     }
 }
 
@@ -998,6 +1280,31 @@ static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, Grid
     return TDP_OK;
 }
 
+template <typename R>
+static void (*fwd_kernel(int L))(Topo, State<R>, GridSync, const int *) {
+    switch (L) {
+        case 0: return k_fwd_sweep<R, 0>;
+        case 3: return k_fwd_sweep<R, 3>;
+        case 7: return k_fwd_sweep<R, 7>;
+        case 15: return k_fwd_sweep<R, 15>;
+        default: return k_fwd_sweep<R, 31>;
+    }
+}
+
+// The single-launch forward sweep from level *from_dev (NULL: level 1).
+template <typename R>
+static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev) {
+    State<R> &s = state<R>(g);
+    GridSync gs;
+    gs.count = s.gsync;
+    gs.status = s.gsync + 1;
+    gs.timeout_ns = kSyncTimeoutNs;
+    LaunchScope ls(g, KID_FWD_SWEEP, 1, g->stream);
+    TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
+    TDP_CUDA(launch_coop(fwd_kernel<R>(g->list_L), grid, kFwdThreads, g->stream, g->topo, s, gs, from_dev));
+    return TDP_OK;
+}
+
 // Forward sweep, building sidetrack lists of length g->list_L (0: none): one
 // cooperative launch, or one graph replay of the level launches.  Run again,
 // it writes the same arrival times.
@@ -1007,16 +1314,8 @@ tdp_status forward_lists(tdp_graph *g) {
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * kMaxK));
     if (g->single_launch) {
         if (g->topo.depth == 0) return TDP_OK;
-        void (*kernel)(Topo, State<R>, GridSync);
-        switch (g->list_L) {
-            case 0: kernel = k_fwd_sweep<R, 0>; break;
-            case 3: kernel = k_fwd_sweep<R, 3>; break;
-            case 7: kernel = k_fwd_sweep<R, 7>; break;
-            case 15: kernel = k_fwd_sweep<R, 15>; break;
-            default: kernel = k_fwd_sweep<R, 31>; break;
-        }
-        const int grid = coop_grid(g, kernel, kFwdThreads);
-        if (grid > 0) return launch_sweep<R>(g, kernel, grid, kFwdThreads, KID_FWD_SWEEP, g->stream, 0);
+        const int grid = coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads);
+        if (grid > 0) return launch_fwd_sweep<R>(g, grid, nullptr);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
@@ -1079,9 +1378,10 @@ static tdp_status backward(tdp_graph *g) {
     return TDP_OK;
 }
 
+// After the forward sweep: endpoints and WNS / TNS on the graph's stream, the
+// backward sweep beside what follows.
 template <typename R>
-static tdp_status sweep(tdp_graph *g) {
-    TDP_TRY(forward_lists<R>(g));
+static tdp_status sweep_tail(tdp_graph *g) {
     if (g->overlap_bwd) TDP_CUDA(cudaEventRecord(g->ev_fwd, g->stream));
     {
         LaunchScope ls(g, KID_EP_WNS);
@@ -1090,6 +1390,12 @@ static tdp_status sweep(tdp_graph *g) {
     }
     TDP_LAUNCH_CHECK();
     return backward<R>(g);
+}
+
+template <typename R>
+static tdp_status sweep(tdp_graph *g) {
+    TDP_TRY(forward_lists<R>(g));
+    return sweep_tail<R>(g);
 }
 
 template tdp_status forward_lists<float>(tdp_graph *);
@@ -1101,19 +1407,119 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     State<R> &s = state<R>(g);
     const int nsb = div_up(t.n_nets, kRcThreads);
     join_side(g);  // the last backward sweep reads what this propagation rewrites
+    g->inc_valid = false;
     {
         LaunchScope ls(g, KID_NET_RC);
         k_net_rc<R><<<nsb + t.n_big, kRcThreads, 0, g->stream>>>(t, s, x, y, T, (R)g->r, (R)g->c,
-                                                                 (R)g->d0, nsb);
+                                                                 (R)g->d0, nsb, Inc{});
     }
     TDP_LAUNCH_CHECK();
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * kMaxK));
     TDP_TRY(sweep<R>(g));
+    if (s.xprev) {  // incremental propagation is in use: keep these positions
+        TDP_CUDA(cudaMemcpyAsync(s.xprev, x, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
+        TDP_CUDA(cudaMemcpyAsync(s.yprev, y, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
+        g->inc_valid = true;
+    }
+    g->inc_full = true;
     return TDP_OK;
 }
 
 template tdp_status propagate_impl<float>(tdp_graph *, const float *, const float *, double);
 template tdp_status propagate_impl<double>(tdp_graph *, const double *, const double *, double);
+
+// Buffers of incremental propagation, on its first use: the previous
+// positions, the per-net stamps (zero: no call yet) and spans.
+template <typename R>
+static tdp_status inc_alloc(tdp_graph *g) {
+    const Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    Inc &inc = g->inc;
+    const size_t nn = (size_t)std::max(t.n_nets, 1);
+    TDP_TRY(dalloc(g, &inc.stamp, nn));
+    TDP_TRY(dalloc(g, &inc.span, nn));
+    TDP_TRY(dalloc(g, &inc.lohi, 3));
+    TDP_TRY(dalloc(g, &inc.cspan, (size_t)std::max(t.n_cells, 1)));
+    TDP_TRY(dalloc(g, &inc.lvchg, (size_t)t.depth + 2));
+    TDP_TRY(dalloc(g, &inc.cnt, 3));
+    TDP_TRY(dalloc(g, &s.xprev, (size_t)std::max(t.n_cells, 1)));
+    TDP_TRY(dalloc(g, &s.yprev, (size_t)std::max(t.n_cells, 1)));
+    TDP_CUDA(cudaMemsetAsync(inc.stamp, 0, sizeof(int32_t) * nn, g->stream));
+    TDP_CUDA(cudaMemsetAsync(inc.cnt, 0, sizeof(unsigned long long) * 3, g->stream));
+    inc.cur = 0;
+    ++g->n_launch;
+    k_inc_span<<<div_up((int)nn, 256), 256, 0, g->stream>>>(t, inc.span);
+    TDP_LAUNCH_CHECK();
+    ++g->n_launch;
+    k_inc_cspan<<<div_up(std::max(t.n_cells, 1), 256), 256, 0, g->stream>>>(t, inc.span, inc.cspan);
+    TDP_LAUNCH_CHECK();
+    return TDP_OK;
+}
+
+// Incremental propagation: re-times only the nets of moved cells and the
+// cells their changes reach (the same per-net and per-cell code as
+// propagate_impl, so the same bits), then the endpoints and WNS / TNS and
+// the backward sweep in full.  Re-times everything (and keeps the positions)
+// when there is no valid previous propagation to start from.
+template <typename R>
+static tdp_status propagate_incremental_impl(tdp_graph *g, const R *x, const R *y, double T) {
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    if (!s.xprev) TDP_TRY(inc_alloc<R>(g));
+    void (*kernel)(Topo, State<R>, GridSync, Inc);
+    switch (g->list_L) {
+        case 0: kernel = k_fwd_sweep_inc<R, 0>; break;
+        case 3: kernel = k_fwd_sweep_inc<R, 3>; break;
+        case 7: kernel = k_fwd_sweep_inc<R, 7>; break;
+        case 15: kernel = k_fwd_sweep_inc<R, 15>; break;
+        default: kernel = k_fwd_sweep_inc<R, 31>; break;
+    }
+    const int grid = g->single_launch ? coop_grid(g, kernel, kFwdThreads) : 0;
+    const int grid_full = g->single_launch ? coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads) : 0;
+    if (!g->inc_valid || !g->propagated || grid == 0 || grid_full == 0 || g->lists_valid_L != g->list_L ||
+        t.depth == 0)
+        return propagate_impl<R>(g, x, y, T);
+    join_side(g);  // the last backward sweep reads what this propagation rewrites
+    g->inc_valid = false;
+    Inc &inc = g->inc;
+    if (inc.cur == INT_MAX) {  // stamps of earlier calls would alias: start over
+        TDP_CUDA(cudaMemsetAsync(inc.stamp, 0, sizeof(int32_t) * std::max(t.n_nets, 1), g->stream));
+        inc.cur = 0;
+    }
+    ++inc.cur;
+    TDP_CUDA(cudaMemsetAsync(inc.lvchg, 0, sizeof(int32_t) * (t.depth + 2), g->stream));
+    ++g->n_launch;
+    k_inc_reset<<<1, 32, 0, g->stream>>>(inc);
+    TDP_LAUNCH_CHECK();
+    {
+        LaunchScope ls(g, KID_INC_MOVED);
+        k_inc_moved<R><<<div_up(std::max(t.n_cells, 1), 256), 256, 0, g->stream>>>(t, x, y, s.xprev, s.yprev,
+                                                                                  inc);
+    }
+    TDP_LAUNCH_CHECK();
+    const int nsb = div_up(t.n_nets, kRcThreads);
+    {
+        LaunchScope ls(g, KID_NET_RC);
+        k_net_rc<R><<<nsb + t.n_big, kRcThreads, 0, g->stream>>>(t, s, x, y, T, (R)g->r, (R)g->c,
+                                                                 (R)g->d0, nsb, inc);
+    }
+    TDP_LAUNCH_CHECK();
+    {
+        GridSync gs;
+        gs.count = s.gsync;
+        gs.status = s.gsync + 1;
+        gs.timeout_ns = kSyncTimeoutNs;
+        LaunchScope ls(g, KID_FWD_INC, 1, g->stream);
+        TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
+        TDP_CUDA(launch_coop(kernel, grid, kFwdThreads, g->stream, t, s, gs, inc));
+    }
+    // the levels after saturation, if the changes saturated (else it returns at once)
+    TDP_TRY(launch_fwd_sweep<R>(g, grid_full, inc.lohi + 2));
+    TDP_TRY(sweep_tail<R>(g));
+    g->inc_valid = true;
+    g->inc_full = false;
+    return TDP_OK;
+}
 
 template <typename R>
 __global__ void k_acc_to_real(const typename Acc<R>::T *a, R *out, int n) {
@@ -1152,15 +1558,23 @@ static tdp_status get_net_delays_impl(tdp_graph *g, R *tnet, R *cload, R *dcell)
 
 using namespace tdp;
 
-extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void *y_dev,
-                                    double clock_period_ps, double *wns_out, double *tns_out) {
+static tdp_status propagate_common(tdp_graph *g, const void *x_dev, const void *y_dev, double clock_period_ps,
+                                   double *wns_out, double *tns_out, bool incremental) {
     if (!g || !x_dev || !y_dev || !std::isfinite(clock_period_ps)) {
-        set_error("sta_propagate: NULL graph or positions, or non-finite clock period");
+        set_error("%s: NULL graph or positions, or non-finite clock period",
+                  incremental ? "sta_propagate_incremental" : "sta_propagate");
         return TDP_ERR_INVALID;
     }
-    tdp_status st = g->prec == TDP_FP32
-                        ? propagate_impl<float>(g, (const float *)x_dev, (const float *)y_dev, clock_period_ps)
-                        : propagate_impl<double>(g, (const double *)x_dev, (const double *)y_dev, clock_period_ps);
+    tdp_status st;
+    if (g->prec == TDP_FP32) {
+        const float *x = (const float *)x_dev, *y = (const float *)y_dev;
+        st = incremental ? propagate_incremental_impl<float>(g, x, y, clock_period_ps)
+                         : propagate_impl<float>(g, x, y, clock_period_ps);
+    } else {
+        const double *x = (const double *)x_dev, *y = (const double *)y_dev;
+        st = incremental ? propagate_incremental_impl<double>(g, x, y, clock_period_ps)
+                         : propagate_impl<double>(g, x, y, clock_period_ps);
+    }
     if (st != TDP_OK) return st;
     g->propagated = true;
     g->extracted = false;
@@ -1173,6 +1587,46 @@ extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void 
         if (wns_out) *wns_out = h[0];
         if (tns_out) *tns_out = h[1];
     }
+    return TDP_OK;
+}
+
+extern "C" tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void *y_dev,
+                                    double clock_period_ps, double *wns_out, double *tns_out) {
+    return propagate_common(g, x_dev, y_dev, clock_period_ps, wns_out, tns_out, false);
+}
+
+extern "C" tdp_status sta_propagate_incremental(tdp_graph *g, const void *x_dev, const void *y_dev,
+                                                double clock_period_ps, double *wns_out, double *tns_out) {
+    return propagate_common(g, x_dev, y_dev, clock_period_ps, wns_out, tns_out, true);
+}
+
+extern "C" tdp_status sta_incremental_stats(tdp_graph *g, int64_t *stats_out) {
+    if (!g || !stats_out) {
+        set_error("sta_incremental_stats: NULL argument");
+        return TDP_ERR_INVALID;
+    }
+    if (!g->propagated) {
+        set_error("sta_incremental_stats: call sta_propagate_incremental first");
+        return TDP_ERR_STATE;
+    }
+    const Topo &t = g->topo;
+    if (g->inc_full || !g->inc.cnt) {
+        const int64_t all[7] = {1, t.n_cells, t.n_comb, t.n_comb, t.depth > 0 ? 1 : 0, t.depth, 0};
+        for (int i = 0; i < 7; ++i) stats_out[i] = all[i];
+        return TDP_OK;
+    }
+    unsigned long long c[3];
+    int32_t lh[3];
+    TDP_CUDA(cudaMemcpyAsync(c, g->inc.cnt, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+    TDP_CUDA(cudaMemcpyAsync(lh, g->inc.lohi, sizeof(lh), cudaMemcpyDeviceToHost, g->stream));
+    TDP_CUDA(cudaStreamSynchronize(g->stream));
+    stats_out[0] = 0;
+    for (int i = 0; i < 3; ++i) stats_out[1 + i] = (int64_t)c[i];
+    const bool none = lh[0] > lh[1];
+    const bool sat = lh[2] <= t.depth;
+    stats_out[4] = none ? 0 : lh[0];
+    stats_out[5] = none ? -1 : (sat ? t.depth : std::min(lh[1], t.depth));
+    stats_out[6] = sat ? lh[2] : 0;
     return TDP_OK;
 }
 

@@ -85,6 +85,30 @@ class TimingGraph:
                                                            float(clock_period_ps), None, None))
         return None
 
+    def sta_propagate_incremental(self, x: torch.Tensor, y: torch.Tensor, clock_period_ps: float,
+                                  sync: bool = True):
+        """The results of sta_propagate, re-timing only what the cells that moved
+        since the last propagation reach; returns (WNS, TNS) when ``sync``."""
+        x, y = self._pos(x), self._pos(y)
+        name = "sta_propagate_incremental"
+        if sync:
+            wns, tns = C.c_double(), C.c_double()
+            _abi.check(name, self.lib.sta_propagate_incremental(self.handle, _ptr(x), _ptr(y),
+                                                                float(clock_period_ps), C.byref(wns),
+                                                                C.byref(tns)))
+            return wns.value, tns.value
+        _abi.check(name, self.lib.sta_propagate_incremental(self.handle, _ptr(x), _ptr(y),
+                                                            float(clock_period_ps), None, None))
+        return None
+
+    def incremental_stats(self) -> dict:
+        """What the last propagation re-timed (synchronises)."""
+        out = (C.c_int64 * 7)()
+        _abi.check("sta_incremental_stats", self.lib.sta_incremental_stats(self.handle, out))
+        keys = ("full", "moved_cells", "cells_evaluated", "cells_changed", "first_level", "last_level",
+                "every_cell_from_level")
+        return dict(zip(keys, (int(v) for v in out)))
+
     def sta_get_timing(self):
         """(arr, req, slack) per pin, as new device tensors."""
         out = [torch.empty(self.n_pins, dtype=self.dtype, device=self.device) for _ in range(3)]

@@ -109,6 +109,8 @@ def test_null_handles(lib):
     assert lib.sta_get_paths(None, None, None, None, None, None) == _abi.TDP_ERR_INVALID
     assert lib.report_timing(None, 10, 0, None) == _abi.TDP_ERR_INVALID
     assert lib.sta_join(None) == _abi.TDP_ERR_INVALID
+    assert lib.sta_propagate_incremental(None, None, None, 0.0, None, None) == _abi.TDP_ERR_INVALID
+    assert lib.sta_incremental_stats(None, None) == _abi.TDP_ERR_INVALID
     assert lib.attraction_set_loss_kind(None, 0) == _abi.TDP_ERR_INVALID
     lib.sta_destroy(None)
     h = C.c_void_p()
