@@ -166,6 +166,20 @@ int main(void) {
         expect("gy", hgy[c], gy_e[c], 1e-2);
     }
 
+    /* incremental timing at the same placement: the first call re-times
+       everything, the second finds no cell moved; both give WNS = TNS = -10 */
+    double iw = 0.0, it = 0.0;
+    int64_t stats[7];
+    CALL(sta_propagate_incremental(g, x, y, 50.0, &iw, &it));
+    expect("incremental WNS (first call)", iw, -10.0, 1e-4);
+    CALL(sta_propagate_incremental(g, x, y, 50.0, &iw, &it));
+    CALL(sta_incremental_stats(g, stats));
+    expect("incremental WNS", iw, -10.0, 1e-4);
+    expect("incremental TNS", it, -10.0, 1e-4);
+    expect("incremental call re-timed everything", (double)stats[0], 0.0, 0.0);
+    expect("moved cells", (double)stats[1], 0.0, 0.0);
+    expect("cells re-evaluated", (double)stats[2], 0.0, 0.0);
+
     sta_destroy(g);
     cudaFree(x);
     cudaFree(y);
