@@ -130,19 +130,19 @@ TDP_API void sta_destroy(tdp_graph *g);
  * slack; Eqs. (3)-(4) WNS / TNS; Eq. (8) net delay).
  * x_dev, y_dev: [n_cells] cell positions (float or double by precision).
  * Computes Elmore net delays and cell delays, arrival times forward and
- * required times backward over the levels, the slack of every pin, and
+ * required times backward over the levels, the slack of every pin (of the
+ * pins that are not endpoints when sta_get_timing asks for it), and
  * WNS = min slack over violated endpoints, TNS = sum of their slacks (both
  * 0 when no endpoint violates), reduced in FP64.
  * Endpoint slacks, WNS and TNS need the forward sweep only; path extraction,
  * the pair update and the loss read nothing else of the backward sweep.  So
- * the library runs the backward sweep (required times, and the slack of
- * every pin that is not an endpoint) on a second stream of its own, beside
- * whatever the caller queues next.  Calls that read its results
- * (sta_get_timing) or rewrite its inputs (the next sta_propagate) make the
- * graph's stream wait for it first; sta_join does the same on request, e.g.
- * before an event that times a whole iteration.  The environment variable
- * TDP_SERIAL_BWD=1 at sta_build keeps the backward sweep on the graph's
- * stream, in order.
+ * the library runs the backward sweep (required times) on a second stream
+ * of its own, beside whatever the caller queues next.  Calls that read its
+ * results (sta_get_timing) or rewrite its inputs (the next sta_propagate)
+ * make the graph's stream wait for it first; sta_join does the same on
+ * request, e.g. before an event that times a whole iteration.  The
+ * environment variable TDP_SERIAL_BWD=1 at sta_build keeps the backward
+ * sweep on the graph's stream, in order.
  * wns_out / tns_out: host doubles, or NULL to skip the synchronisation.
  */
 TDP_API tdp_status sta_propagate(tdp_graph *g, const void *x_dev, const void *y_dev,

@@ -582,7 +582,7 @@ extern "C" void sta_destroy(tdp_graph *g) {
     for (void *p : g->allocs) cudaFree(p);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->side) cudaStreamDestroy(g->side);
-    if (g->ev_fwd) cudaEventDestroy(g->ev_fwd);
+    if (g->ev_bwd_go) cudaEventDestroy(g->ev_bwd_go);
     if (g->ev_bwd) cudaEventDestroy(g->ev_bwd);
     delete g;
 }
@@ -620,7 +620,7 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
         int prio_lo = 0, prio_hi = 0;
         if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, prio_hi);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fwd, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_bwd_go, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_bwd, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             set_error("sta_build: stream or event creation failed: %s", cudaGetErrorString(e));

@@ -450,10 +450,11 @@ struct tdp_graph {
     tdp_precision prec = TDP_FP32;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // stream used to capture CUDA graphs
-    // the backward sweep runs on `side` after the forward sweep (ev_fwd);
-    // ev_bwd marks its end, bwd_pending until the graph's stream waits for it
+    // the backward sweep runs on `side` once the graph's stream reaches
+    // ev_bwd_go (the end of the forward sweep); ev_bwd marks its end,
+    // bwd_pending until the graph's stream waits for it
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fwd = nullptr, ev_bwd = nullptr;
+    cudaEvent_t ev_bwd_go = nullptr, ev_bwd = nullptr;
     bool overlap_bwd = true, bwd_pending = false;
     tdp::Topo topo;
     tdp::Levels lv;

@@ -15,10 +15,12 @@
 //                of the nets driven from each level, deepest first (a net of
 //                at most 8 sinks on an aligned group of 1, 2 or 4 lanes, a
 //                warp per 64-sink piece of a larger net, the pieces combined
-//                by an atomic min on an order-preserving key), and the slacks
-//                of every other pin.  Nothing later in a timing
-//                iteration reads what it writes, so it runs on a second stream
-//                beside path extraction, the pair update and the loss.
+//                by an atomic min on an order-preserving key).  Required
+//                times need no arrival, and nothing later in a timing
+//                iteration reads them, so it runs on a second stream
+//                beside path extraction, the pair update and the loss
+//   k_pin_slack  slack of every pin that is not an endpoint, on request
+//                (sta_get_timing)
 //
 // Where a cooperative launch cannot be made resident (or TDP_LEVEL_GRAPHS=1),
 // the same per-cell and per-task code runs as one launch per level
@@ -912,7 +914,7 @@ struct SinkPre {
     int p[kBwPerLane], kd[kBwPerLane], sn[kBwPerLane];
     unsigned old;
     R tp[kBwPerLane], dn[kBwPerLane];
-    A ap[kBwPerLane], rq[kBwPerLane];
+    A rq[kBwPerLane];
 };
 
 // topology: one round of loads (task < 0: none)
@@ -950,7 +952,6 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
         c.tp[j] = ldg(&s.tnet[c.p[j]]);
         if ((c.kd[j] & kKindMask) != PK_ENDPOINT) {
             c.dn[j] = ldg(&s.dnet[c.sn[j]]);
-            c.ap[j] = ldg(&s.arr[c.p[j]]);
             if (!(c.kd[j] & kKindPrev)) {
                 c.rq[j] = acc_unkey<R>(ldcg(&s.reqkey[c.sn[j]]));
                 c.old |= 1u << j;
@@ -960,10 +961,11 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
     c.vals = true;
 }
 
-// Required and slack times of the task's sinks, and the net's required time
-// (Section II-B: min over its sinks of the sink's required time minus its
-// Elmore delay) into reqkey (stored, or atomicMin for the pieces of a split
-// net).  PIECE: the warp holds one piece (min over 32 lanes), else small
+// Required times of the task's sinks, and the net's required time (Section
+// II-B: min over its sinks of the sink's required time minus its Elmore
+// delay) into reqkey (stored, or atomicMin for the pieces of a split net).
+// Required times need no arrival: slacks of pins other than endpoints are
+// formed on request (k_pin_slack), those of endpoints by k_ep_wns.  PIECE: the warp holds one piece (min over 32 lanes), else small
 // nets on aligned groups of 1, 2 or 4 lanes (min over the group).  Every lane of the warp
 // calls this.  COH: required times of sink cells were written by other
 // blocks of the same launch.
@@ -973,7 +975,7 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
     using A = typename AC::T;
     A m = AC::pinf();
     if (c.a >= 0) {
-        A rq[kBwPerLane], ap[kBwPerLane];
+        A rq[kBwPerLane];
         R tp[kBwPerLane];
 #pragma unroll
         for (int j = 0; j < kBwPerLane; ++j) {  // loads
@@ -984,16 +986,12 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
             } else {
                 rq[j] = (c.old >> j) & 1u ? c.rq[j] : acc_unkey<R>(ldd<COH>(&s.reqkey[c.sn[j]]));
                 rq[j] = AC::add(rq[j], -(c.vals ? c.dn[j] : ldg(&s.dnet[c.sn[j]])));
-                ap[j] = c.vals ? c.ap[j] : ldg(&s.arr[c.p[j]]);
             }
         }
 #pragma unroll
         for (int j = 0; j < kBwPerLane; ++j) {  // stores
             if (c.p[j] < 0) continue;
-            if ((c.kd[j] & kKindMask) != PK_ENDPOINT) {
-                s.req[c.p[j]] = rq[j];
-                s.slack[c.p[j]] = AC::diff(rq[j], ap[j]);
-            }
+            if ((c.kd[j] & kKindMask) != PK_ENDPOINT) s.req[c.p[j]] = rq[j];
             const A cand = AC::add(rq[j], -tp[j]);
             if (AC::lt(cand, m)) m = cand;
         }
@@ -1011,16 +1009,20 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
     }
 }
 
-// Required time and slack of every net's driver pin, from reqkey.
+// Required time of every net's driver pin, from reqkey.
 template <typename R, bool COH>
 __device__ __forceinline__ void bwd_drivers(const Topo &t, State<R> &s, int i, int stride) {
-    using AC = Acc<R>;
-    for (int e = i; e < t.n_nets; e += stride) {
-        const int a = ldg(&t.net_ptr[e]);
-        const typename AC::T r = acc_unkey<R>(ldd<COH>(&s.reqkey[e]));
-        s.req[a] = r;
-        s.slack[a] = AC::diff(r, ldg(&s.arr[a]));
-    }
+    for (int e = i; e < t.n_nets; e += stride)
+        s.req[ldg(&t.net_ptr[e])] = acc_unkey<R>(ldd<COH>(&s.reqkey[e]));
+}
+
+// Slack = required time - arrival of every pin that is not an endpoint
+// (Eq. (2)), for sta_get_timing; endpoints' slacks are k_ep_wns's.
+template <typename R>
+__global__ void k_pin_slack(Topo t, State<R> s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= t.n_pins || ldg(&t.pin_kind[p]) == PK_ENDPOINT) return;
+    s.slack[p] = Acc<R>::diff(s.req[p], s.arr[p]);
 }
 
 // One launch per level (captured in a CUDA graph): a warp per task.
@@ -1047,7 +1049,7 @@ __global__ void k_bwd_drivers(Topo t, State<R> s) {
 constexpr int kRedThreads = 256;
 constexpr int kRedFinal = 1024;  // chunk partials the last block combines at once (a power of 2)
 constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
-constexpr int kBwdOverlapNum = 10;     // overlapped backward sweep: 10/16 of the resident grid
+constexpr int kBwdOverlapNum = 9;      // overlapped backward sweep: 9/16 of the resident grid
 
 // Endpoints (FF D and PO pins): arrival = the driver's arrival + the pin's
 // Elmore delay, required time = T, slack = T - arrival; then WNS = min over
@@ -1154,7 +1156,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
 // its first task of the next two levels: between its arrival at the barrier
 // that closes level l and the wait, it loads the final values of its level
 // l - 1 task and the topology of its level l - 2 task.  After the last
-// level, the driver pins' required times and slacks.
+// level, the driver pins' required times.
 template <typename R>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
     const int lane = threadIdx.x & 31;
@@ -1338,21 +1340,26 @@ __global__ void k_bwd_reset(unsigned long long *reqkey, int n, unsigned *count) 
     if (i == 0) *count = 0u;
 }
 
-// Backward sweep: one cooperative launch, or one graph replay, on the graph's
-// second stream after the forward sweep (or on its stream when the two are
-// serialised); sta_join and every call that needs its results wait for it.
+// Backward sweep: one cooperative launch, or one graph replay.  Nothing
+// later in a timing iteration reads what it writes, so with the overlap on
+// it runs on the graph's second stream from the end of the forward sweep
+// (ev_bwd_go), beside the endpoints, extraction, the pair update and the
+// loss, on kBwdOverlapNum / 16 of its resident grid; serialised, on the
+// graph's stream after the endpoints.  sta_join and every call that needs
+// its results wait for it.
 template <typename R>
 static tdp_status backward(tdp_graph *g) {
     cudaStream_t st = g->stream;
-    if (g->overlap_bwd) {  // ev_fwd: recorded after the forward sweep
-        TDP_CUDA(cudaStreamWaitEvent(g->side, g->ev_fwd, 0));
+    if (g->overlap_bwd) {
+        TDP_CUDA(cudaStreamWaitEvent(g->side, g->ev_bwd_go, 0));
         st = g->side;
     }
     bool done = false;
     if (g->single_launch) {
         // beside extraction, the pair update and the loss, the sweep leaves
-        // SMs to them: kBwdOverlapNum / 16 of the resident grid (the best
-        // split measured at 1.2M cells on 148 SMs: 80 to 100 blocks)
+        // SMs to them: kBwdOverlapNum / 16 of the resident grid (83 of 148
+        // blocks; measured at 1.2M cells, a step took 1.189, 1.157, 1.111,
+        // 1.135, 1.171 and 1.270 ms for 7/16 to 12/16)
         int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
         if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * kBwdOverlapNum / 16);
         if (grid > 0) {
@@ -1378,11 +1385,11 @@ static tdp_status backward(tdp_graph *g) {
     return TDP_OK;
 }
 
-// After the forward sweep: endpoints and WNS / TNS on the graph's stream, the
-// backward sweep beside what follows.
+// After the forward sweep: the endpoints and WNS / TNS, and the backward
+// sweep (which reads no arrival and starts at once on the second stream).
 template <typename R>
-static tdp_status sweep_tail(tdp_graph *g) {
-    if (g->overlap_bwd) TDP_CUDA(cudaEventRecord(g->ev_fwd, g->stream));
+static tdp_status finish_sweeps(tdp_graph *g) {
+    if (g->overlap_bwd) TDP_CUDA(cudaEventRecord(g->ev_bwd_go, g->stream));
     {
         LaunchScope ls(g, KID_EP_WNS);
         const int chunks = div_up(std::max(g->topo.n_ep, 1), kRedChunk);
@@ -1390,12 +1397,6 @@ static tdp_status sweep_tail(tdp_graph *g) {
     }
     TDP_LAUNCH_CHECK();
     return backward<R>(g);
-}
-
-template <typename R>
-static tdp_status sweep(tdp_graph *g) {
-    TDP_TRY(forward_lists<R>(g));
-    return sweep_tail<R>(g);
 }
 
 template tdp_status forward_lists<float>(tdp_graph *);
@@ -1415,7 +1416,8 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     }
     TDP_LAUNCH_CHECK();
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * kMaxK));
-    TDP_TRY(sweep<R>(g));
+    TDP_TRY(forward_lists<R>(g));
+    TDP_TRY(finish_sweeps<R>(g));
     if (s.xprev) {  // incremental propagation is in use: keep these positions
         TDP_CUDA(cudaMemcpyAsync(s.xprev, x, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
         TDP_CUDA(cudaMemcpyAsync(s.yprev, y, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
@@ -1515,7 +1517,7 @@ static tdp_status propagate_incremental_impl(tdp_graph *g, const R *x, const R *
     }
     // the levels after saturation, if the changes saturated (else it returns at once)
     TDP_TRY(launch_fwd_sweep<R>(g, grid_full, inc.lohi + 2));
-    TDP_TRY(sweep_tail<R>(g));
+    TDP_TRY(finish_sweeps<R>(g));
     g->inc_valid = true;
     g->inc_full = false;
     return TDP_OK;
@@ -1532,9 +1534,10 @@ static tdp_status get_timing_impl(tdp_graph *g, R *arr, R *req, R *slack) {
     State<R> &s = state<R>(g);
     int n = g->topo.n_pins;
     join_side(g);
-    g->n_launch += (arr ? 1 : 0) + (req ? 1 : 0);
+    g->n_launch += (arr ? 1 : 0) + (req ? 1 : 0) + (slack ? 1 : 0);
     if (arr) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.arr, arr, n);
     if (req) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.req, req, n);
+    if (slack) k_pin_slack<R><<<div_up(std::max(n, 1), 256), 256, 0, g->stream>>>(g->topo, s);
     TDP_LAUNCH_CHECK();
     if (slack)
         TDP_CUDA(cudaMemcpyAsync(slack, s.slack, sizeof(R) * n, cudaMemcpyDeviceToDevice, g->stream));
