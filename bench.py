@@ -165,11 +165,11 @@ LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single c
 # was taken; the figure is reported only while those sources are unchanged.
 SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
-    "fwd_sweep": {"bytes": 477330176, "sources": SWEEP_SOURCES,
-                  "sha256": "2d9d480cd74141f4e8bbb46dd2baa7eb3c38dc49aaf949b2c47f2351fd58f357",
+    "fwd_sweep": {"bytes": 456485632, "sources": SWEEP_SOURCES,
+                  "sha256": "9e1b1fdef23029b9cc5d53b3cccdea9f56d31f0b6127191af68b10331fb926b8",
                   "profile": "profiles/fwd_sweep_1.2M.md"},
-    "bwd_sweep": {"bytes": 192587008, "sources": SWEEP_SOURCES,
-                  "sha256": "2d9d480cd74141f4e8bbb46dd2baa7eb3c38dc49aaf949b2c47f2351fd58f357",
+    "bwd_sweep": {"bytes": 192797696, "sources": SWEEP_SOURCES,
+                  "sha256": "9e1b1fdef23029b9cc5d53b3cccdea9f56d31f0b6127191af68b10331fb926b8",
                   "profile": "profiles/bwd_sweep_1.2M.md"},
 }
 
@@ -213,10 +213,10 @@ def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
         # delay (4), arrival of the output (8), worst input / chain length (12);
         # sidetrack list: write L entries and read the inherited L (8 B each)
         # and both counts (8); per input: pin, net, driver, driver kind (13),
-        # Elmore delay (4), arrival written (8); per driving net: its arrival
-        # (8) and chain length (4), each read once
+        # Elmore delay (4) (its arrival is formed on request, not stored);
+        # per driving net: its arrival (8) and chain length (4), each read once
         L = g_info["list_L"]
-        return n_comb * (12 + 4 + 8 + 12 + 16 * L + 8) + n_in * (13 + 4 + 8) + N * (8 + 4)
+        return n_comb * (12 + 4 + 8 + 12 + 16 * L + 8) + n_in * (13 + 4) + N * (8 + 4)
     if kernel == "bwd_sweep":
         # per sink: kind, cell output, its net (9), Elmore delay (4); comb
         # inputs write their required time (8); endpoints (required time T)

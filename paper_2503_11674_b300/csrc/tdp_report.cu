@@ -96,10 +96,15 @@ __global__ void k_rt_prep(Topo t, State<R> s) {
     const int2 pr = s.pred[e];
     const int a = t.lv_in_ptr[k], b = t.lv_in_ptr[k + 1];
     s.rt_chain[e] = make_int4(pr.y, a, b - a, pr.x);
-    const typename AC::T aw = s.arr[pr.x];
+    // input arrivals: the driver's arrival plus the Elmore delay, as the
+    // forward sweep forms them
+    auto in_arr = [&](int j) { return AC::add(s.arr[t.lv_in_drv[j]], s.tnet[t.lv_in_pin[j]]); };
+    typename AC::T aw = AC::ninf();
+    for (int j = a; j < b; ++j)
+        if (t.lv_in_pin[j] == pr.x) aw = in_arr(j);
     for (int j = a; j < b; ++j) {
         const int p = t.lv_in_pin[j];
-        s.rt_delta[j] = p == pr.x ? R(0) : AC::diff(aw, s.arr[p]);
+        s.rt_delta[j] = p == pr.x ? R(0) : AC::diff(aw, in_arr(j));
     }
 }
 

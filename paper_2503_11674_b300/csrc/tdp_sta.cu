@@ -233,7 +233,6 @@ __device__ __noinline__ void fwd_cell_wide(const Topo &t, State<R> &s, int k, in
         for (int u = 0; u < kPre; ++u) {
             if (p0 + u < b) {
                 av[u] = AC::add(av[u], tv[u]);
-                s.arr[ip[u]] = av[u];
                 // largest arrival, lowest pin on ties (the group order below)
                 if (bi < 0 || AC::gt(av[u], best) || (!AC::gt(best, av[u]) && ip[u] < bi)) {
                     best = av[u];
@@ -258,7 +257,7 @@ __device__ __noinline__ void fwd_cell_wide(const Topo &t, State<R> &s, int k, in
         for (int p = a; p < b; ++p) {
             const int ip = ldg(&t.lv_in_pin[p]);
             if (ip == bi) continue;
-            const A av = ldcg(&s.arr[ip]);  // stored above by this thread
+            const A av = AC::add(ldd<COH>(&s.arr[ldg(&t.lv_in_drv[p])]), ldg(&s.tnet[ip]));
             const LEnt<R> x{AC::diff(best, av), ((ip < bi ? 0u : 2u) << 29) | (uint32_t)ip};
             int j = 0;
             for (; j < L; ++j) {
@@ -473,7 +472,9 @@ __device__ __forceinline__ void cell_vals(const State<R> &s, CellPre<R> &c) {
 
 // Arrival of one cell (Section II-B: max over its inputs of the driver's
 // arrival plus the Elmore delay, plus the cell delay) and, when L > 0, its
-// sidetrack list.  COH: the drivers' values were written by other blocks of
+// sidetrack list.  The input pins' arrivals are not stored: nothing in a
+// timing iteration reads them, and k_in_arr forms them, with the same
+// addition, when sta_get_timing asks.  COH: the drivers' values were written by other blocks of
 // the same launch.  CMP: returns whether the cell's output arrival, worst
 // input, chain length or list differs, bit for bit, from what was stored
 // before (a cell of more than kPre inputs always counts as changed).
@@ -530,9 +531,6 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
         chg = !same_bits(ldcg(&s.arr[c.o]), AC::add(best, dcell)) || op.x != bi || op.y != bn ||
               ldcg(&s.plen[c.e]) != bl + 2;
     }
-#pragma unroll
-    for (int u = 0; u < kPre; ++u)
-        if (u < nin) s.arr[c.ip[u]] = av[u];
     s.arr[c.o] = AC::add(best, dcell);
     s.pred[c.e] = make_int2(bi, bn);
     s.plen[c.e] = bl + 2;
@@ -1014,6 +1012,16 @@ template <typename R, bool COH>
 __device__ __forceinline__ void bwd_drivers(const Topo &t, State<R> &s, int i, int stride) {
     for (int e = i; e < t.n_nets; e += stride)
         s.req[ldg(&t.net_ptr[e])] = acc_unkey<R>(ldd<COH>(&s.reqkey[e]));
+}
+
+// Arrival of every combinational input pin: its driver's arrival plus its
+// Elmore delay (the addition of fwd_cell), for sta_get_timing.
+template <typename R>
+__global__ void k_in_arr(Topo t, State<R> s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= t.n_in) return;
+    const int p = ldg(&t.lv_in_pin[j]);
+    s.arr[p] = Acc<R>::add(s.arr[ldg(&t.lv_in_drv[j])], ldg(&s.tnet[p]));
 }
 
 // Slack = required time - arrival of every pin that is not an endpoint
@@ -1534,7 +1542,9 @@ static tdp_status get_timing_impl(tdp_graph *g, R *arr, R *req, R *slack) {
     State<R> &s = state<R>(g);
     int n = g->topo.n_pins;
     join_side(g);
-    g->n_launch += (arr ? 1 : 0) + (req ? 1 : 0) + (slack ? 1 : 0);
+    g->n_launch += (arr || slack ? 1 : 0) + (arr ? 1 : 0) + (req ? 1 : 0) + (slack ? 1 : 0);
+    if ((arr || slack) && g->topo.n_in > 0)
+        k_in_arr<R><<<div_up(g->topo.n_in, 256), 256, 0, g->stream>>>(g->topo, s);
     if (arr) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.arr, arr, n);
     if (req) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.req, req, n);
     if (slack) k_pin_slack<R><<<div_up(std::max(n, 1), 256), 256, 0, g->stream>>>(g->topo, s);
