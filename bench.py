@@ -165,11 +165,11 @@ LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single c
 # was taken; the figure is reported only while those sources are unchanged.
 SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
-    "fwd_sweep": {"bytes": 456485632, "sources": SWEEP_SOURCES,
-                  "sha256": "9e1b1fdef23029b9cc5d53b3cccdea9f56d31f0b6127191af68b10331fb926b8",
+    "fwd_sweep": {"bytes": 456201984, "sources": SWEEP_SOURCES,
+                  "sha256": "282bed6810eed92ec3ce39034e079f3d6745c454f0df8e35a0457531fbc178a4",
                   "profile": "profiles/fwd_sweep_1.2M.md"},
-    "bwd_sweep": {"bytes": 192797696, "sources": SWEEP_SOURCES,
-                  "sha256": "9e1b1fdef23029b9cc5d53b3cccdea9f56d31f0b6127191af68b10331fb926b8",
+    "bwd_sweep": {"bytes": 127325440, "sources": SWEEP_SOURCES,
+                  "sha256": "282bed6810eed92ec3ce39034e079f3d6745c454f0df8e35a0457531fbc178a4",
                   "profile": "profiles/bwd_sweep_1.2M.md"},
 }
 
@@ -218,13 +218,12 @@ def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
         L = g_info["list_L"]
         return n_comb * (12 + 4 + 8 + 12 + 16 * L + 8) + n_in * (13 + 4) + N * (8 + 4)
     if kernel == "bwd_sweep":
-        # per sink: kind, cell output, its net (9), Elmore delay (4); comb
-        # inputs write their required time (8); endpoints (required time T)
-        # are written by ep_wns; per net: pin range (8), driver required time
-        # written (8), driving-cell delay (4); per comb output its required
-        # time read once (8).  No arrival: slacks other than the endpoints'
-        # are formed on request
-        return S * (9 + 4) + n_in * 8 + N * (8 + 8 + 4) + n_comb * 8
+        # per sink: kind, cell output, its net (9), Elmore delay (4); per net:
+        # its required time written (8) and the driving cell's delay (4); per
+        # comb output its required time read once (8).  Only nets' required
+        # times are stored: pins' required times and slacks (other than the
+        # endpoints', from ep_wns) are formed on request
+        return S * (9 + 4) + N * (8 + 4) + n_comb * 8
     if kernel == "ep_wns":
         # per endpoint: (pin, driver pin) (8), driver arrival (8), Elmore delay
         # (4), arrival, required time and slack written (20)

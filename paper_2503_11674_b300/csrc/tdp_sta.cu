@@ -19,8 +19,9 @@
 //                times need no arrival, and nothing later in a timing
 //                iteration reads them, so it runs on a second stream
 //                beside path extraction, the pair update and the loss
-//   k_pin_slack  slack of every pin that is not an endpoint, on request
-//                (sta_get_timing)
+//   k_pin_req, k_in_arr, k_pin_slack
+//                required time, input-pin arrival and slack of every pin
+//                that is not an endpoint, on request (sta_get_timing)
 //
 // Where a cooperative launch cannot be made resident (or TDP_LEVEL_GRAPHS=1),
 // the same per-cell and per-task code runs as one launch per level
@@ -959,11 +960,13 @@ __device__ __forceinline__ void sink_vals(const State<R> &s, SinkPre<R> &c) {
     c.vals = true;
 }
 
-// Required times of the task's sinks, and the net's required time (Section
-// II-B: min over its sinks of the sink's required time minus its Elmore
-// delay) into reqkey (stored, or atomicMin for the pieces of a split net).
-// Required times need no arrival: slacks of pins other than endpoints are
-// formed on request (k_pin_slack), those of endpoints by k_ep_wns.  PIECE: the warp holds one piece (min over 32 lanes), else small
+// The net's required time (Section II-B: min over its sinks of the sink's
+// required time minus its Elmore delay; a sink's required time is its
+// cell's output required time minus the cell delay, or T at an endpoint)
+// into reqkey (stored, or atomicMin for the pieces of a split net).  Only
+// the nets' required times are stored: those of pins, and slacks, are
+// formed on request (k_pin_req, k_pin_slack), the endpoints' by k_ep_wns.
+// Required times need no arrival.  PIECE: the warp holds one piece (min over 32 lanes), else small
 // nets on aligned groups of 1, 2 or 4 lanes (min over the group).  Every lane of the warp
 // calls this.  COH: required times of sink cells were written by other
 // blocks of the same launch.
@@ -987,9 +990,8 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
             }
         }
 #pragma unroll
-        for (int j = 0; j < kBwPerLane; ++j) {  // stores
+        for (int j = 0; j < kBwPerLane; ++j) {
             if (c.p[j] < 0) continue;
-            if ((c.kd[j] & kKindMask) != PK_ENDPOINT) s.req[c.p[j]] = rq[j];
             const A cand = AC::add(rq[j], -tp[j]);
             if (AC::lt(cand, m)) m = cand;
         }
@@ -1007,11 +1009,22 @@ __device__ __forceinline__ void bwd_net(State<R> &s, const SinkPre<R> &c, int la
     }
 }
 
-// Required time of every net's driver pin, from reqkey.
-template <typename R, bool COH>
-__device__ __forceinline__ void bwd_drivers(const Topo &t, State<R> &s, int i, int stride) {
-    for (int e = i; e < t.n_nets; e += stride)
-        s.req[ldg(&t.net_ptr[e])] = acc_unkey<R>(ldd<COH>(&s.reqkey[e]));
+// Required time of every pin that is not an endpoint, for sta_get_timing:
+// a driver pin takes its net's required time, a combinational input its
+// cell's output required time minus the cell delay (the addition of
+// bwd_net).
+template <typename R>
+__global__ void k_pin_req(Topo t, State<R> s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= t.n_pins) return;
+    const int kind = ldg(&t.pin_kind[p]);
+    if (kind == PK_ENDPOINT) return;
+    if (kind == PK_COMB_IN) {
+        const int sn = ldg(&t.sink_onet[p]);
+        s.req[p] = Acc<R>::add(acc_unkey<R>(s.reqkey[sn]), -ldg(&s.dnet[sn]));
+    } else {
+        s.req[p] = acc_unkey<R>(s.reqkey[ldg(&t.pin_net[p])]);
+    }
 }
 
 // Arrival of every combinational input pin: its driver's arrival plus its
@@ -1046,11 +1059,6 @@ __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, in
     bwd_net<R, false>(s, c, threadIdx.x & 31, w >= n_small);
 }
 
-template <typename R>
-__global__ void k_bwd_drivers(Topo t, State<R> s) {
-    pdl_wait();
-    bwd_drivers<R, false>(t, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
 
 // ---------------------------------------------------------- WNS / TNS ---
 
@@ -1163,8 +1171,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
 // block j mod gridDim, a grid-wide barrier after each level.  A warp carries
 // its first task of the next two levels: between its arrival at the barrier
 // that closes level l and the wait, it loads the final values of its level
-// l - 1 task and the topology of its level l - 2 task.  After the last
-// level, the driver pins' required times.
+// l - 1 task and the topology of its level l - 2 task.
 template <typename R>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s, GridSync gs) {
     const int lane = threadIdx.x & 31;
@@ -1199,7 +1206,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_sweep(Topo t, State<R> s
         }
         if (!grid_wait(gs, (++n) * gridDim.x)) return;
     }
-    bwd_drivers<R, true>(t, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------ launch ---
@@ -1229,11 +1235,6 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
                        g->lv.bw_s_lo[l], ns, nb);
             ++nk;
         }
-        ok = cudaGetLastError() == cudaSuccess;
-    }
-    if (bwd && ok) {
-        launch_pdl(k_bwd_drivers<R>, 4 * 148, 256, cs, t, s);
-        nk += 1;
         ok = cudaGetLastError() == cudaSuccess;
     }
     cudaGraph_t graph = nullptr;
@@ -1542,9 +1543,10 @@ static tdp_status get_timing_impl(tdp_graph *g, R *arr, R *req, R *slack) {
     State<R> &s = state<R>(g);
     int n = g->topo.n_pins;
     join_side(g);
-    g->n_launch += (arr || slack ? 1 : 0) + (arr ? 1 : 0) + (req ? 1 : 0) + (slack ? 1 : 0);
+    g->n_launch += (arr || slack ? 1 : 0) + (req || slack ? 1 : 0) + (arr ? 1 : 0) + (req ? 1 : 0) + (slack ? 1 : 0);
     if ((arr || slack) && g->topo.n_in > 0)
         k_in_arr<R><<<div_up(g->topo.n_in, 256), 256, 0, g->stream>>>(g->topo, s);
+    if (req || slack) k_pin_req<R><<<div_up(std::max(n, 1), 256), 256, 0, g->stream>>>(g->topo, s);
     if (arr) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.arr, arr, n);
     if (req) k_acc_to_real<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.req, req, n);
     if (slack) k_pin_slack<R><<<div_up(std::max(n, 1), 256), 256, 0, g->stream>>>(g->topo, s);
