@@ -1,0 +1,50 @@
+"""bench.py's CPU paths, on a small netlist: the reference arm (the oracle as
+it stands, one full timing iteration a step) and the CPU baseline."""
+import numpy as np
+
+import bench
+import netgen
+import oracle
+
+
+class _Args:
+    config, seed, steps, warmup, K = "tiny", 1, 3, 2, None
+
+
+def _single_rank(monkeypatch):
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+
+
+def test_reference_arm_line(monkeypatch):
+    _single_rank(monkeypatch)
+    r = bench.run_reference(_Args())
+    assert r["impl"] == "reference" and r["metric"] == bench.METRIC and r["unit"] == bench.UNIT
+    assert r["higher_is_better"] is True and r["value"] > 0
+    assert (r["steps"], r["steps_timed"], r["warmup"], r["warmup_run"]) == (3, 3, 2, 1)
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == r["value"]
+    assert r["ms_per_step"] == round(1000.0 / r["value"], 1)
+
+
+def test_reference_arm_stops_its_timed_steps_at_the_budget(monkeypatch):
+    _single_rank(monkeypatch)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 0.0)
+
+    class Args(_Args):
+        steps = 50
+
+    r = bench.run_reference(Args())
+    assert r["steps"] == 50 and r["steps_timed"] == 2  # at least two, then the budget ends them
+
+
+def test_cpu_baseline_times_full_iterations():
+    cfg = netgen.CONFIGS["tiny"]
+    nl = netgen.generate(cfg, 1)
+    T = oracle.clock_period(nl, cfg.t_factor)
+    x2, y2 = netgen.perturb(nl.x, nl.y, nl.cell_fixed, 2.0, np.random.default_rng(0))
+    cb = bench.cpu_baseline(nl, cfg, T, [(nl.x, nl.y), (x2, y2)])
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert cb["sample"].startswith("2 full timing iterations")
+    assert abs(cb["seconds_per_iteration"] - 1.0 / cb["value"]) < 1e-3
