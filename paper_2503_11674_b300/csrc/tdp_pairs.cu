@@ -72,6 +72,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
         }
         int e = on ? t.pin_net[ep] : 0;
         int j = ns - 1;  // sides[] holds the deepest sidetrack first
+        // the next sidetrack to take, in registers: its pin, the net where
+        // it is taken (-2: none) and the net it leads to; refreshed only
+        // when it is taken, so that a step's only dependent load is pred
+        int nside = -1, nat = -2, nto = -1;
+        auto next_side = [&]() {
+            if (j >= 0) {
+                nside = sides[j];
+                nat = t.sink_onet[nside];
+                nto = t.pin_net[nside];
+            } else {
+                nat = -2;
+            }
+        };
+        next_side();
         bool walking = on;
         unsigned last_mask = 0;
         long long last_sum = 0, last_max = 0;
@@ -84,9 +98,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
                     walking = false;
                 } else {
                     int nx;
-                    if (j >= 0 && t.sink_onet[sides[j]] == e) {
-                        pi = sides[j--];
-                        nx = t.pin_net[pi];
+                    if (nat == e) {
+                        pi = nside;
+                        nx = nto;
+                        --j;
+                        next_side();
                     } else {
                         nx = pr.y;
                     }
