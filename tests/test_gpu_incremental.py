@@ -184,3 +184,32 @@ def test_level_launch_fallback_re_times_everything(monkeypatch):
     assert A.sta_propagate_incremental(x2, y, T) == B.sta_propagate(x2, y, T)
     assert A.incremental_stats()["full"] == 1
     _assert_same_state(A, B)
+
+
+def test_incremental_matches_full_propagation_at_1_2m_cells():
+    """The benchmark's workload (1.2M cells, K = 16 lists): 1, 120 and 12,000
+    moved cells, each call checked bit for bit against a full propagation,
+    timing and paths (the selective sweep, and its hand-over to the full
+    sweep once the changes saturate)."""
+    cfg = netgen.CONFIGS["1.2M"]
+    nl = netgen.generate(cfg, 1)
+    T = oracle.clock_period(nl, cfg.t_factor)
+    A, B = _graph(nl, "fp32"), _graph(nl, "fp32")
+    x, y = nl.x.copy(), nl.y.copy()
+    A.sta_propagate_incremental(_t(x, A.dtype), _t(y, A.dtype), T)
+    A.extract_critical_paths(-1, cfg.K)  # lists of the iteration's length from here on
+    rng = np.random.default_rng(11)
+    movable = np.nonzero(nl.cell_fixed == 0)[0]
+    seen = []
+    for m in (1, 120, 12000):
+        idx = rng.choice(movable, m, replace=False)
+        x[idx] += rng.normal(0.0, 2.0, m).astype(np.float32)
+        y[idx] += rng.normal(0.0, 2.0, m).astype(np.float32)
+        xa, ya = _t(x, A.dtype), _t(y, A.dtype)
+        assert A.sta_propagate_incremental(xa, ya, T) == B.sta_propagate(xa, ya, T), m
+        st = A.incremental_stats()
+        assert st["full"] == 0 and st["moved_cells"] == m, st
+        seen.append(st["every_cell_from_level"])
+        _assert_same_state(A, B)
+        _assert_same_paths(A, B, cfg.K)
+    assert seen[-1] > 0  # 12,000 moved cells saturate: the full sweep finished the call
