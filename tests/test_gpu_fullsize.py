@@ -1,4 +1,5 @@
-"""Parity at the full 1.2M-cell workload, in the benchmark's launch configuration.
+"""Parity at the full 1.2M-cell workload, in the benchmark's launch configuration
+(FP32, and the same STA on an FP64 graph).
 
 The FP64 oracle computes every pin's timing at this size in seconds, so STA is
 checked on every pin.  Path sets are checked against the oracle on a sample of
@@ -109,3 +110,23 @@ def test_loss_and_gradient(run):
     g = np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]).astype(np.float64)
     gr = np.concatenate([gx_r, gy_r])
     assert np.linalg.norm(g - gr) / np.linalg.norm(gr) <= 1e-5
+
+
+def test_fp64_graph_every_pin_and_fp32_agreement(run):
+    """The same workload on an FP64 graph: every pin's net delays, arrival,
+    required time and slack against the FP64 oracle within the FP64-on-GPU
+    tolerance (same arithmetic, another order and fused multiply-adds), and
+    WNS / TNS of the FP32 graph within the FP32 tolerances of it."""
+    from paper_2503_11674_b300 import TimingGraph
+    from parity_util import TOL64
+    nl, T, tm = run["nl"], run["T"], run["tm"]
+    G = TimingGraph(nl, "fp64")
+    x = torch.tensor(nl.x, dtype=torch.float64, device="cuda")
+    y = torch.tensor(nl.y, dtype=torch.float64, device="cuda")
+    wns, tns = G.sta_propagate(x, y, T)
+    check_sta(G, tm, T, TOL64)
+    assert tns == pytest.approx(tm["tns"], rel=1e-9)
+    assert wns == pytest.approx(tm["wns"], rel=1e-9)
+    assert run["tns"] == pytest.approx(tns, rel=1e-6)
+    assert run["wns"] == pytest.approx(wns, rel=1e-6)
+    G.close()
