@@ -6,11 +6,13 @@
 // Euclidean distance in place of the quadratic term (the ablation of
 // Section IV).
 // with (x_d, y_d) the driver pin of s's net; pin coordinates are the cell
-// position plus the pin offset.  Both passes walk only the nets that hold a
-// sink of P (the compacted list pnets, thread per net, for nets of at most
+// position plus the pin offset.  The forward pass takes the sinks of P from
+// the compacted list ppins, a thread per pair, so that no thread scans the
+// other sinks of a net.  The backward pass walks the nets that hold a sink
+// of P (the compacted list pnets, thread per net, for nets of at most
 // kBigFanout sinks; a warp per net of the static list of larger nets, which
-// skips nets without one), so a net's sinks are read contiguously and a
-// driver's gradient is summed in one place, in FP64, in a fixed order.
+// skips nets without one), so that a driver's gradient is summed in one
+// place, in FP64, in a fixed order.
 //
 //   k_pp_fwd       terms in the working precision, FP64 total; fixed grid and
 //                  fixed-order block / grid reduction (deterministic)
@@ -51,30 +53,18 @@ __device__ __forceinline__ void pair_grad(R dx, R dy, int kind, R &gx, R &gy) {
     }
 }
 
+// Pair term of sink pin p, with a the driver pin of its net.
 template <typename R>
-__device__ __forceinline__ double net_pp(const Topo &t, const State<R> &s, const R *x, const R *y,
-                                         int a, int b, int first, int step, int kind) {
-    double acc = 0.0;
-    bool have = false;
-    R xd = 0, yd = 0;
-    for (int p = a + 1 + first; p < b; p += step) {
-        if (!s.in_p[p]) continue;
-        if (!have) {
-            const int cd = t.pin_cell[a];
-            xd = x[cd] + s.pin_dx[a];
-            yd = y[cd] + s.pin_dy[a];
-            have = true;
-        }
-        const int cs = t.pin_cell[p];
-        const R dx = x[cs] + s.pin_dx[p] - xd;
-        const R dy = y[cs] + s.pin_dy[p] - yd;
-        acc += (double)(s.w[p] * pair_term(dx, dy, kind));
-    }
-    return acc;
+__device__ __forceinline__ R pin_pp(const Topo &t, const State<R> &s, const R *x, const R *y, int p, int a,
+                                    int kind) {
+    const int cd = t.pin_cell[a];
+    const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
+    const int cs = t.pin_cell[p];
+    const R dx = x[cs] + s.pin_dx[p] - xd;
+    const R dy = y[cs] + s.pin_dy[p] - yd;
+    return s.w[p] * pair_term(dx, dy, kind);
 }
 
-// warp tasks of both loss passes: warps [0, nsw) take 32 consecutive entries
-// of pnets (a lane per net), warps [nsw, nsw + n_big) one larger net each
 template <typename R>
 __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
                                                          const R *__restrict__ y, double beta,
@@ -82,22 +72,11 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int np = s.pcnt[0];
-    const int nsw = (np + 31) >> 5;
-    const int tasks = nsw + t.n_big;
-    const int nwarps = gridDim.x * (kLossThreads / 32);
+    const int np = s.pcnt[2];
     double acc = 0.0;
-    for (int task = blockIdx.x * (kLossThreads / 32) + wib; task < tasks; task += nwarps) {
-        if (task < nsw) {
-            const int i = task * 32 + lane;
-            if (i < np) {
-                const int e = s.pnets[i];
-                acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], 0, 1, kind);
-            }
-        } else {
-            const int e = t.big_nets[task - nsw];
-            if (s.net_pf[e]) acc += net_pp(t, s, x, y, t.net_ptr[e], t.net_ptr[e + 1], lane, 32, kind);
-        }
+    for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
+        const int p = s.ppins[i];
+        acc += (double)pin_pp(t, s, x, y, p, t.net_ptr[t.pin_net[p]], kind);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) sh[wib] = acc;
