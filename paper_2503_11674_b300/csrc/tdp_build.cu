@@ -93,14 +93,13 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     // loss
     TDP_TRY(dalloc(g, &s.net_pf, (size_t)t.n_nets + 32));
     TDP_TRY(dalloc(g, &s.cell_pf, (size_t)t.n_cells + 32));
-    TDP_TRY(dalloc(g, &s.pnets, t.n_nets));
     TDP_TRY(dalloc(g, &s.pcells, t.n_cells));
     TDP_TRY(dalloc(g, &s.ppins, std::max(t.n_pins, 1)));
-    TDP_TRY(dalloc(g, &s.pcnt, 3));
+    TDP_TRY(dalloc(g, &s.pcnt, 2));
     TDP_TRY(dalloc(g, &s.cmp_blk, std::max(t.n_pins, std::max(t.n_nets, t.n_cells)) / kCompactItems + 2));
     TDP_CUDA(cudaMemset(s.net_pf, 0, (size_t)t.n_nets + 32));
     TDP_CUDA(cudaMemset(s.cell_pf, 0, (size_t)t.n_cells + 32));
-    TDP_CUDA(cudaMemset(s.pcnt, 0, 3 * sizeof(int32_t)));
+    TDP_CUDA(cudaMemset(s.pcnt, 0, 2 * sizeof(int32_t)));
     TDP_TRY(dalloc(g, &s.gslot, 2 * (size_t)t.n_pins));
     TDP_CUDA(cudaMemset(s.gslot, 0, 2 * sizeof(R) * (size_t)t.n_pins));
     TDP_TRY(dalloc(g, &s.loss_part, 1024));

@@ -413,16 +413,15 @@ struct State {
     uint8_t *touch = nullptr, *in_p = nullptr;   // [n_pins]
     R *w = nullptr;                               // [n_pins]
     long long *n_pairs = nullptr;
-    // pairs, compacted for the loss: nets holding a sink of P, cells with a
-    // pin in such a net's pair (sink in P or the net's driver), the sink pins
-    // of P; the lists are ascending, counts in pcnt[0] (nets of at most
-    // kBigFanout sinks), pcnt[1] (cells) and pcnt[2] (pins)
+    // pairs, compacted for the loss: the sink pins of P, and the cells with
+    // a pin in a pair (its sink or the driver of its net); the lists are
+    // ascending, counts in pcnt[0] (pins) and pcnt[1] (cells).  net_pf marks
+    // the nets holding a sink of P (for the larger nets' warps)
     uint8_t *net_pf = nullptr;    // [n_nets] 0, kPfSmall or kPfLarge
     uint8_t *cell_pf = nullptr;   // [n_cells]
-    int32_t *pnets = nullptr;     // [n_nets]
-    int32_t *pcells = nullptr;    // [n_cells]
     int32_t *ppins = nullptr;     // [n_pins]
-    int32_t *pcnt = nullptr;      // [3]
+    int32_t *pcells = nullptr;    // [n_cells]
+    int32_t *pcnt = nullptr;      // [2]
     int32_t *cmp_blk = nullptr;   // per-block counts of the compaction
     // loss
     R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y); zero outside P
@@ -599,7 +598,7 @@ tdp_status check_sync_status(tdp_graph *g);
 void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
                 int32_t *count);
 
-// rebuild the compacted pair lists (pnets, pcells, ppins, pcnt) from net_pf / cell_pf / in_p
+// rebuild the compacted pair lists (ppins, pcells, pcnt) from in_p / cell_pf
 template <typename R>
 tdp_status compact_pairs(tdp_graph *g);
 

@@ -6,19 +6,19 @@
 // Euclidean distance in place of the quadratic term (the ablation of
 // Section IV).
 // with (x_d, y_d) the driver pin of s's net; pin coordinates are the cell
-// position plus the pin offset.  The forward pass takes the sinks of P from
-// the compacted list ppins, a thread per pair, so that no thread scans the
-// other sinks of a net.  The backward pass walks the nets that hold a sink
-// of P (the compacted list pnets, thread per net, for nets of at most
-// kBigFanout sinks; a warp per net of the static list of larger nets, which
-// skips nets without one), so that a driver's gradient is summed in one
-// place, in FP64, in a fixed order.
+// position plus the pin offset.  Both passes take the sinks of P from the
+// compacted, ascending list ppins, a thread per pair, so that no thread
+// scans the other sinks of a net; the pairs of one net are consecutive
+// there.  In the backward pass the first pair of a net of at most
+// kBigFanout sinks sums its net's pin gradients for the driver, in FP64, in
+// pin order; a larger net is a warp's (the static list of larger nets,
+// skipped without a pair), which walks its sinks and sums in a fixed order.
 //
 //   k_pp_fwd       terms in the working precision, FP64 total; fixed grid and
 //                  fixed-order block / grid reduction (deterministic)
-//   k_pp_bwd_net   pin gradients 2 beta w (p_s - p_d) of the net's sinks in
-//                  P, minus their sum on the driver, into the pins' slots in
-//                  the cell -> pins order (slots outside P stay zero)
+//   k_pp_bwd_net   pin gradients 2 beta w (p_s - p_d) of the sinks in P,
+//                  minus their sum on each net's driver, into the pins' slots
+//                  in the cell -> pins order (slots outside P stay zero)
 //   k_pp_bwd_cell  per cell of the compacted list pcells, the FP64 sum of its
 //                  pins' slots times the incoming gradient scale (fixed cells
 //                  0); every other cell's gradient is 0
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int np = s.pcnt[2];
+    const int np = s.pcnt[0];
     double acc = 0.0;
     for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
         const int p = s.ppins[i];
@@ -126,37 +126,75 @@ __device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x,
     }
 }
 
+// Gradient of the pair term of sink pin p (driver pin a) with respect to the
+// sink's position, times beta w (the arithmetic of net_grad).
+template <typename R>
+__device__ __forceinline__ void pin_grad(const Topo &t, const State<R> &s, const R *x, const R *y, int p, int a,
+                                         double beta, int kind, R &gx, R &gy) {
+    const int cd = t.pin_cell[a];
+    const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
+    const int cs = t.pin_cell[p];
+    const R k = (R)beta * s.w[p];
+    R ux, uy;
+    pair_grad(x[cs] + s.pin_dx[p] - xd, y[cs] + s.pin_dy[p] - yd, kind, ux, uy);
+    gx = k * ux;
+    gy = k * uy;
+}
+
+// warp tasks: warps [0, npw) take 32 consecutive pairs of ppins (a lane per
+// pair; pairs of larger nets are left to their net's warp), warps
+// [npw, npw + n_big) one larger net each
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
                                                     const R *__restrict__ y, double beta, int kind) {
     const int lane = threadIdx.x & 31;
     const int np = s.pcnt[0];
-    const int nsw = (np + 31) >> 5;
-    const int tasks = nsw + t.n_big;
+    const int npw = (np + 31) >> 5;
+    const int tasks = npw + t.n_big;
     const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
     for (int task = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); task < tasks; task += nwarps) {
-        double sx = 0.0, sy = 0.0;
-        int a;
-        if (task < nsw) {
+        if (task < npw) {
             const int i = task * 32 + lane;
             if (i >= np) continue;
-            const int e = s.pnets[i];
-            a = t.net_ptr[e];
-            net_grad(t, s, x, y, a, t.net_ptr[e + 1], 0, 1, beta, kind, sx, sy);
+            const int p = s.ppins[i];
+            const int e = t.pin_net[p];
+            const int a = t.net_ptr[e];
+            if (t.net_ptr[e + 1] - a - 1 > kBigFanout) continue;  // its net's warp
+            R gx, gy;
+            pin_grad(t, s, x, y, p, a, beta, kind, gx, gy);
+            const int slot = t.slot_of_pin[p];
+            s.gslot[2 * slot] = gx;
+            s.gslot[2 * slot + 1] = gy;
+            if (i > 0 && t.pin_net[s.ppins[i - 1]] == e) continue;
+            // the net's first pair: the driver's gradient, minus the sum of
+            // the net's pin gradients in pin order (at most kBigFanout)
+            double sx = (double)gx, sy = (double)gy;
+            for (int j = i + 1; j < np; ++j) {
+                const int q = s.ppins[j];
+                if (t.pin_net[q] != e) break;
+                R qx, qy;
+                pin_grad(t, s, x, y, q, a, beta, kind, qx, qy);
+                sx += (double)qx;
+                sy += (double)qy;
+            }
+            const int ds = t.slot_of_pin[a];
+            s.gslot[2 * ds] = (R)(-sx);
+            s.gslot[2 * ds + 1] = (R)(-sy);
         } else {
-            const int e = t.big_nets[task - nsw];
+            const int e = t.big_nets[task - npw];
             if (!s.net_pf[e]) continue;  // warp-uniform
-            a = t.net_ptr[e];
+            const int a = t.net_ptr[e];
+            double sx = 0.0, sy = 0.0;
             net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, beta, kind, sx, sy);
             for (int o = 16; o > 0; o >>= 1) {
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane != 0) continue;
+            const int ds = t.slot_of_pin[a];
+            s.gslot[2 * ds] = (R)(-sx);
+            s.gslot[2 * ds + 1] = (R)(-sy);
         }
-        const int slot = t.slot_of_pin[a];
-        s.gslot[2 * slot] = (R)(-sx);
-        s.gslot[2 * slot + 1] = (R)(-sy);
     }
 }
 

@@ -256,10 +256,9 @@ template <typename R>
 tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    compact_u8(g, s.net_pf, kPfSmall, t.n_nets, nullptr, s.pnets, s.pcnt);
+    compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt);
     compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1);
-    compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt + 2);
-    g->n_launch += 9;
+    g->n_launch += 6;
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
@@ -397,7 +396,7 @@ static tdp_status reset_pairs_impl(tdp_graph *g) {
     TDP_CUDA(cudaMemsetAsync(s.n_pairs, 0, sizeof(long long), g->stream));
     TDP_CUDA(cudaMemsetAsync(s.net_pf, 0, g->topo.n_nets, g->stream));
     TDP_CUDA(cudaMemsetAsync(s.cell_pf, 0, g->topo.n_cells, g->stream));
-    TDP_CUDA(cudaMemsetAsync(s.pcnt, 0, 3 * sizeof(int32_t), g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.pcnt, 0, 2 * sizeof(int32_t), g->stream));
     TDP_CUDA(cudaMemsetAsync(s.gslot, 0, 2 * sizeof(R) * (size_t)np, g->stream));
     return TDP_OK;
 }
