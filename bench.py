@@ -239,11 +239,16 @@ def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
         # endpoint, slack, cost, count and parent / sidetrack records (24)
         return occ * 41.0 + paths * 24.0
     if kernel == "pp_fwd":
+        # per pair: its list entry (4), its net and the net's driver (8), the
+        # two pins' cells (8), offsets (16) and the weight (4), the two cells'
+        # positions (16)
         nP = g_info["pairs"]
-        return 4 * (N + 1) + S + 16 * nP + 12 * N + 8 * C
+        return 56 * nP
     if kernel == "pp_bwd_net":
+        # per pair as the forward pass (56) and its gradient slot (4 + 8
+        # written); per pair net the driver's slot (4 + 8 written)
         nP = g_info["pairs"]
-        return 4 * (N + 1) + S + 16 * nP + 12 * N + 8 * C + 12 * P
+        return 68 * nP + 12 * min(nP, N)
     if kernel == "pp_bwd_cell":
         return 4 * (C + 1) + 8 * P + C + 8 * C
     if kernel == "topk":
