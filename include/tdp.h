@@ -348,7 +348,12 @@ TDP_API tdp_status attraction_set_loss_kind(tdp_graph *g, tdp_loss_kind kind);
  * counter) is a static device array of the library, 128 KiB + 4 bytes held
  * on every GPU that loads the library until the process exits.
  *   n_nets        nets; at most 4,194,304 (more: TDP_ERR_INVALID)
- *   net_ptr_dev   int32[n_nets+1] pins of each net, driver first (as sta_build)
+ *   net_ptr_dev   int32[n_nets+1] pins of each net, driver first (as sta_build):
+ *                 non-decreasing, net_ptr[0] = 0; every net should hold its
+ *                 driver pin and at least one sink (sta_build rejects other
+ *                 nets; here an empty net adds nothing and reads no pin).
+ *                 This call does not validate the arrays: they are not
+ *                 read on the host
  *   pin_cell_dev  int32[n_pins], pin_dx_dev / pin_dy_dev float[n_pins] (um)
  *   w_dev         float[n_pins] weight of the pair (driver, pin) of every sink
  *                 pin; 0 for pins not in P (and ignored on drivers)
@@ -397,6 +402,31 @@ TDP_API tdp_status tdp_profile_read(tdp_graph *g, int64_t *launches_out, double 
  * (0, 1000]), TDP_ERR_CUDA.
  */
 TDP_API tdp_status tdp_selftest_grid_wait(double timeout_ms, int32_t *gave_up_out);
+
+/*
+ * Test hooks of the host-side failure paths (no counterpart in the paper).
+ * They make a failure on the host; none of them faults, traps or stalls a
+ * GPU.
+ * tdp_debug_fail_alloc: the n-th next device allocation the library makes
+ * (process-wide, any graph; cudaMalloc of graph state or cudaMallocAsync of
+ * a temporary) fails as if the device were out of memory, without calling
+ * CUDA; the call that made it returns TDP_ERR_OOM and frees what it had
+ * allocated.  n = 0 cancels a pending failure.  Errors: TDP_ERR_INVALID
+ * (n < 0).
+ * tdp_debug_pending_alloc_failure: *n_out = the countdown left (0: none
+ * pending, i.e. the injected failure has happened or was cancelled).
+ * tdp_debug_set_sync_status: writes `status` into the graph's sticky status
+ * word of the level sweeps' grid-wide waits (the word a wait that gave up
+ * sets), on the graph's stream, and synchronises.  A non-zero status makes
+ * the next host-synchronising call that checks the word (sta_propagate with
+ * wns_out or tns_out, extract_critical_paths with n_paths_out,
+ * report_timing) return TDP_ERR_TIMEOUT, clear the word and mark the timing
+ * results invalid, as after a real timeout.  Errors: TDP_ERR_INVALID (NULL
+ * graph), TDP_ERR_CUDA.
+ */
+TDP_API tdp_status tdp_debug_fail_alloc(int64_t n);
+TDP_API tdp_status tdp_debug_pending_alloc_failure(int64_t *n_out);
+TDP_API tdp_status tdp_debug_set_sync_status(tdp_graph *g, uint32_t status);
 
 /* Message for the last non-OK status returned on this host thread. */
 TDP_API const char *tdp_last_error(void);

@@ -2,6 +2,7 @@
 // cells (the timing graph of Section II-B is a DAG once flip-flops cut it),
 // and lay the level-ordered CSR arrays out in device memory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -658,5 +659,52 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
         return st;
     }
     *out = g;
+    return TDP_OK;
+}
+
+// ------------------------------------------------------------ test hooks ---
+
+namespace tdp {
+namespace {
+std::atomic<int64_t> g_fail_alloc{0};  // n > 0: the n-th next allocation fails
+}  // namespace
+
+bool alloc_fail_injected() {
+    int64_t c = g_fail_alloc.load();
+    while (c > 0) {
+        if (g_fail_alloc.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+}  // namespace tdp
+
+extern "C" tdp_status tdp_debug_fail_alloc(int64_t n) {
+    if (n < 0) {
+        set_error("tdp_debug_fail_alloc: n < 0");
+        return TDP_ERR_INVALID;
+    }
+    g_fail_alloc.store(n);
+    return TDP_OK;
+}
+
+extern "C" tdp_status tdp_debug_pending_alloc_failure(int64_t *n_out) {
+    if (!n_out) {
+        set_error("tdp_debug_pending_alloc_failure: n_out is NULL");
+        return TDP_ERR_INVALID;
+    }
+    *n_out = g_fail_alloc.load();
+    return TDP_OK;
+}
+
+extern "C" tdp_status tdp_debug_set_sync_status(tdp_graph *g, uint32_t status) {
+    if (!g) {
+        set_error("tdp_debug_set_sync_status: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    join_side(g);
+    unsigned *w = g->prec == TDP_FP32 ? g->s32.gsync : g->s64.gsync;
+    const unsigned h = status;
+    TDP_CUDA(cudaMemcpyAsync(w + 1, &h, sizeof(h), cudaMemcpyHostToDevice, g->stream));
+    TDP_CUDA(cudaStreamSynchronize(g->stream));
     return TDP_OK;
 }

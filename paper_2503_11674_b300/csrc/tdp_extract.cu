@@ -339,13 +339,13 @@ template <typename R>
 static tdp_status ensure_path_buffers(tdp_graph *g, int K) {
     State<R> &s = state<R>(g);
     const Topo &t = g->topo;
-    if (!s.p_parent) {  // sized for the largest K once
-        size_t slots = (size_t)std::max(t.n_ep, 1) * kMaxK;
-        TDP_TRY(dalloc(g, &s.p_parent, slots));
-        TDP_TRY(dalloc(g, &s.p_side, slots));
-        TDP_TRY(dalloc(g, &s.p_len, slots));
-        TDP_TRY(dalloc(g, &s.p_cost, slots));
-    }
+    // sized for the largest K, each buffer once (a call that failed part way
+    // keeps what it got)
+    const size_t slots = (size_t)std::max(t.n_ep, 1) * kMaxK;
+    if (!s.p_parent) TDP_TRY(dalloc(g, &s.p_parent, slots));
+    if (!s.p_side) TDP_TRY(dalloc(g, &s.p_side, slots));
+    if (!s.p_len) TDP_TRY(dalloc(g, &s.p_len, slots));
+    if (!s.p_cost) TDP_TRY(dalloc(g, &s.p_cost, slots));
     return TDP_OK;
 }
 
@@ -372,12 +372,12 @@ static tdp_status sort_viol(tdp_graph *g) {
     SortItem *b = reinterpret_cast<SortItem *>(s.sort_b);
     int32_t *viol = nullptr, *cnt = nullptr, *par = nullptr, *side = nullptr, *len = nullptr;
     R *cost = nullptr;
-    bool ok = cudaMallocAsync(&viol, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
-              cudaMallocAsync(&cnt, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
-              cudaMallocAsync(&par, sizeof(int32_t) * slots, st) == cudaSuccess &&
-              cudaMallocAsync(&side, sizeof(int32_t) * slots, st) == cudaSuccess &&
-              cudaMallocAsync(&len, sizeof(int32_t) * slots, st) == cudaSuccess &&
-              cudaMallocAsync(&cost, sizeof(R) * slots, st) == cudaSuccess;
+    bool ok = dmalloc_async(&viol, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
+              dmalloc_async(&cnt, sizeof(int32_t) * std::max(t.n_ep, 1), st) == cudaSuccess &&
+              dmalloc_async(&par, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              dmalloc_async(&side, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              dmalloc_async(&len, sizeof(int32_t) * slots, st) == cudaSuccess &&
+              dmalloc_async(&cost, sizeof(R) * slots, st) == cudaSuccess;
     tdp_status rc = TDP_OK;
     if (!ok) {
         set_error("sta_get_paths: temporary allocation failed");
@@ -546,9 +546,9 @@ tdp_status get_paths_impl(tdp_graph *g, int32_t *viol, int32_t *ep, R *slack, in
     }
     int64_t *base = nullptr, *pin_off = nullptr;
     int32_t *lens = nullptr;
-    cudaError_t e1 = cudaMallocAsync(&base, sizeof(int64_t) * (n_use + 1), st);
-    cudaError_t e2 = cudaMallocAsync(&pin_off, sizeof(int64_t) * (np + 1), st);
-    cudaError_t e3 = cudaMallocAsync(&lens, sizeof(int32_t) * np, st);
+    cudaError_t e1 = dmalloc_async(&base, sizeof(int64_t) * (n_use + 1), st);
+    cudaError_t e2 = dmalloc_async(&pin_off, sizeof(int64_t) * (np + 1), st);
+    cudaError_t e3 = dmalloc_async(&lens, sizeof(int32_t) * np, st);
     tdp_status rc = TDP_OK;
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         set_error("sta_get_paths: temporary allocation failed");

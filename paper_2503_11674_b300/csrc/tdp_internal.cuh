@@ -498,12 +498,27 @@ struct tdp_graph {
 };
 
 namespace tdp {
+// Every device allocation of the library goes through dalloc (cudaMalloc,
+// owned by the graph) or dmalloc_async (cudaMallocAsync, temporaries).  The
+// test hook tdp_debug_fail_alloc can make one of them fail on the host
+// without calling CUDA, so that the out-of-memory paths are tested without
+// exhausting a GPU.
+bool alloc_fail_injected();
+template <typename T>
+cudaError_t dmalloc_async(T **p, size_t bytes, cudaStream_t st) {
+    if (alloc_fail_injected()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
 template <typename T>
 tdp_status dalloc(tdp_graph *g, T **p, size_t n) {
     void *q = nullptr;
     size_t bytes = n * sizeof(T);
     if (bytes == 0) bytes = sizeof(T);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = alloc_fail_injected() ? cudaErrorMemoryAllocation : cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));

@@ -328,7 +328,7 @@ tdp_status scan_i32_to_i64(tdp_graph *g, const int32_t *in, int64_t *out, int64_
     g->n_launch += 3;
     const int nt = div_up(std::max<int64_t>(n, 1), kScanTile);
     long long *tile = nullptr;
-    if (cudaMallocAsync(&tile, sizeof(long long) * nt, st) != cudaSuccess) {
+    if (dmalloc_async(&tile, sizeof(long long) * nt, st) != cudaSuccess) {
         set_error("scan: temporary allocation failed");
         return TDP_ERR_OOM;
     }

@@ -48,8 +48,8 @@ k_pp_fwd_noalloc(int n_nets, const int32_t *__restrict__ net_ptr, const int32_t 
     __shared__ bool last;
     const int e = blockIdx.x * kNaThreads + threadIdx.x;
     double acc = 0.0;
-    if (e < n_nets) {
-        const int a = net_ptr[e], b = net_ptr[e + 1];
+    const int a = e < n_nets ? net_ptr[e] : 0, b = e < n_nets ? net_ptr[e + 1] : 0;
+    if (b > a) {  // an empty net (a caller error) adds nothing and reads no pin
         const int cd = pin_cell[a];
         const float xd = x[cd] + dx[a], yd = y[cd] + dy[a];
         for (int p = a + 1; p < b; ++p) {

@@ -315,8 +315,8 @@ static tdp_status get_pairs_impl(tdp_graph *g, int32_t *pins, R *w, int64_t *n_o
     cudaStream_t st = g->stream;
     int32_t *flags = nullptr;
     int64_t *off = nullptr;
-    if (cudaMallocAsync(&flags, sizeof(int32_t) * n, st) != cudaSuccess ||
-        cudaMallocAsync(&off, sizeof(int64_t) * (n + 1), st) != cudaSuccess) {
+    if (dmalloc_async(&flags, sizeof(int32_t) * n, st) != cudaSuccess ||
+        dmalloc_async(&off, sizeof(int64_t) * (n + 1), st) != cudaSuccess) {
         if (flags) cudaFreeAsync(flags, st);
         set_error("attraction_get_pairs: temporary allocation failed");
         return TDP_ERR_OOM;

@@ -348,7 +348,7 @@ __global__ void k_rt_pair_walk(Topo t, State<R> s, RtNodes<R> acc, const int32_t
 template <typename T>
 static cudaError_t rt_alloc(T **p, int64_t n, cudaStream_t st) {
     *p = nullptr;
-    const cudaError_t e = cudaMallocAsync(p, sizeof(T) * (size_t)std::max<int64_t>(n, 1), st);
+    const cudaError_t e = dmalloc_async(p, sizeof(T) * (size_t)std::max<int64_t>(n, 1), st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -507,10 +507,8 @@ tdp_status report_impl(tdp_graph *g, int64_t n, int keep_nonneg) {
     g->rt_nodes = 0;
     TDP_TRY(sort_failing<R>(g));
     if (n == 0 || t.n_ep == 0) return TDP_OK;
-    if (!s.rt_chain) {
-        TDP_TRY(dalloc(g, &s.rt_chain, (size_t)t.n_nets));
-        TDP_TRY(dalloc(g, &s.rt_delta, (size_t)std::max(t.n_in, 1)));
-    }
+    if (!s.rt_chain) TDP_TRY(dalloc(g, &s.rt_chain, (size_t)t.n_nets));
+    if (!s.rt_delta) TDP_TRY(dalloc(g, &s.rt_delta, (size_t)std::max(t.n_in, 1)));
     TDP_CUDA(cudaMemsetAsync(s.rt_chain, 0xff, sizeof(int4) * (size_t)t.n_nets, st));
     ++g->n_launch;
     if (t.n_comb > 0) k_rt_prep<R><<<div_up(t.n_comb, kRtThreads), kRtThreads, 0, st>>>(t, s);

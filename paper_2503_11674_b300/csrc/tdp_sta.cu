@@ -1427,7 +1427,7 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * kMaxK));
     TDP_TRY(forward_lists<R>(g));
     TDP_TRY(finish_sweeps<R>(g));
-    if (s.xprev) {  // incremental propagation is in use: keep these positions
+    if (s.yprev) {  // incremental propagation is in use: keep these positions
         TDP_CUDA(cudaMemcpyAsync(s.xprev, x, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
         TDP_CUDA(cudaMemcpyAsync(s.yprev, y, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
         g->inc_valid = true;
@@ -1447,13 +1447,15 @@ static tdp_status inc_alloc(tdp_graph *g) {
     State<R> &s = state<R>(g);
     Inc &inc = g->inc;
     const size_t nn = (size_t)std::max(t.n_nets, 1);
-    TDP_TRY(dalloc(g, &inc.stamp, nn));
-    TDP_TRY(dalloc(g, &inc.span, nn));
-    TDP_TRY(dalloc(g, &inc.lohi, 3));
-    TDP_TRY(dalloc(g, &inc.cspan, (size_t)std::max(t.n_cells, 1)));
-    TDP_TRY(dalloc(g, &inc.lvchg, (size_t)t.depth + 2));
-    TDP_TRY(dalloc(g, &inc.cnt, 3));
-    TDP_TRY(dalloc(g, &s.xprev, (size_t)std::max(t.n_cells, 1)));
+    // each buffer once (a call that failed part way keeps what it got);
+    // yprev last: its presence means the whole set is allocated
+    if (!inc.stamp) TDP_TRY(dalloc(g, &inc.stamp, nn));
+    if (!inc.span) TDP_TRY(dalloc(g, &inc.span, nn));
+    if (!inc.lohi) TDP_TRY(dalloc(g, &inc.lohi, 3));
+    if (!inc.cspan) TDP_TRY(dalloc(g, &inc.cspan, (size_t)std::max(t.n_cells, 1)));
+    if (!inc.lvchg) TDP_TRY(dalloc(g, &inc.lvchg, (size_t)t.depth + 2));
+    if (!inc.cnt) TDP_TRY(dalloc(g, &inc.cnt, 3));
+    if (!s.xprev) TDP_TRY(dalloc(g, &s.xprev, (size_t)std::max(t.n_cells, 1)));
     TDP_TRY(dalloc(g, &s.yprev, (size_t)std::max(t.n_cells, 1)));
     TDP_CUDA(cudaMemsetAsync(inc.stamp, 0, sizeof(int32_t) * nn, g->stream));
     TDP_CUDA(cudaMemsetAsync(inc.cnt, 0, sizeof(unsigned long long) * 3, g->stream));
@@ -1476,7 +1478,7 @@ template <typename R>
 static tdp_status propagate_incremental_impl(tdp_graph *g, const R *x, const R *y, double T) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    if (!s.xprev) TDP_TRY(inc_alloc<R>(g));
+    if (!s.yprev) TDP_TRY(inc_alloc<R>(g));
     void (*kernel)(Topo, State<R>, GridSync, Inc);
     switch (g->list_L) {
         case 0: kernel = k_fwd_sweep_inc<R, 0>; break;
@@ -1590,7 +1592,12 @@ static tdp_status propagate_common(tdp_graph *g, const void *x_dev, const void *
         st = incremental ? propagate_incremental_impl<double>(g, x, y, clock_period_ps)
                          : propagate_impl<double>(g, x, y, clock_period_ps);
     }
-    if (st != TDP_OK) return st;
+    if (st != TDP_OK) {  // a propagation that failed part way leaves no valid timing
+        g->propagated = false;
+        g->extracted = false;
+        g->inc_valid = false;
+        return st;
+    }
     g->propagated = true;
     g->extracted = false;
     g->lists_valid_L = g->list_L;

@@ -115,3 +115,15 @@ def test_null_handles(lib):
     lib.sta_destroy(None)
     h = C.c_void_p()
     assert lib.sta_build(None, 0, None, C.byref(h)) == _abi.TDP_ERR_INVALID
+
+
+def test_debug_hooks_check_their_arguments_on_the_host(lib):
+    """The failure-injection hooks reject bad arguments without touching a device."""
+    n = C.c_int64(-7)
+    assert lib.tdp_debug_fail_alloc(-1) == _abi.TDP_ERR_INVALID
+    assert lib.tdp_debug_fail_alloc(3) == _abi.TDP_OK
+    assert lib.tdp_debug_pending_alloc_failure(C.byref(n)) == _abi.TDP_OK and n.value == 3
+    assert lib.tdp_debug_fail_alloc(0) == _abi.TDP_OK
+    assert lib.tdp_debug_pending_alloc_failure(C.byref(n)) == _abi.TDP_OK and n.value == 0
+    assert lib.tdp_debug_pending_alloc_failure(None) == _abi.TDP_ERR_INVALID
+    assert lib.tdp_debug_set_sync_status(None, 1) == _abi.TDP_ERR_INVALID

@@ -3,11 +3,11 @@
 
 * STA on every pin and WNS / TNS against the FP64 oracle.
 * The extraction of all failing endpoints with K = 32 (the call of a timing
-  iteration) is checked by its totals against the oracle's failing endpoints,
-  and repeated for determinism; its paths are too many to materialise here
-  (~2.6M paths, ~600M pins), so
-* the K = 32 path sets of the 400 most critical endpoints are extracted and
-  compared with the oracle's pin sequences under the margin rule.
+  iteration; ~61,000 endpoints, ~1.9M paths, ~440M path pins) is compared
+  with the oracle on every failing endpoint: bit-exact pin sequences on every
+  endpoint whose top-K set is decided by more than the slack tolerance, the
+  unique part and the validity of every path on the others.  A second
+  extraction gives the same bits.
 * The pair update runs on the full path set; the loss and its gradient are
   checked with a seeded pair set.
 """
@@ -17,7 +17,7 @@ import torch
 
 import netgen
 import oracle
-from parity_util import TOL32, check_sta, compare_paths, gpu_paths
+from parity_util import TOL32, check_sta, compare_paths
 
 pytestmark = pytest.mark.gpu
 
@@ -41,13 +41,23 @@ def run():
     wns, tns = G.sta_propagate(x, y, T)
     n1 = G.extract_critical_paths(-1, cfg.K, False)
     tot1 = G.sta_get_paths_size()
+    Pd = G.sta_get_paths()
     n2 = G.extract_critical_paths(-1, cfg.K, False)
     tot2 = G.sta_get_paths_size()
+    Pd2 = G.sta_get_paths()
+    same = all(torch.equal(Pd[k], Pd2[k]) for k in Pd)
+    del Pd2
+    P = {k: v.cpu().numpy() for k, v in Pd.items()}
+    del Pd
     n_pairs = G.attraction_update_pairs(10.0, 0.2)
-    G.extract_critical_paths(400, cfg.K, False)
-    P = gpu_paths(G)
     return dict(nl=nl, T=T, tm=tm, G=G, x=x, y=y, wns=wns, tns=tns, K=cfg.K, n1=n1, n2=n2, tot1=tot1,
-                tot2=tot2, n_pairs=n_pairs, P=P)
+                tot2=tot2, same=same, n_pairs=n_pairs, P=P)
+
+
+def _failing_endpoints(nl, tm):
+    ct = nl.cell_type[nl.pin_cell]
+    ep = np.nonzero((nl.pin_dir == 0) & ((ct == netgen.FF) | (ct == netgen.PO)))[0]
+    return ep[tm["slack"][ep] < 0.0]
 
 
 def test_sta_every_pin(run):
@@ -59,24 +69,29 @@ def test_sta_every_pin(run):
 def test_all_endpoint_extraction_totals(run):
     nl, tm, K = run["nl"], run["tm"], run["K"]
     n_viol, n_paths, n_pins = run["tot1"]
-    ref_viol = oracle.topk(nl, tm, -1, 1)["viol"]
+    ref_viol = _failing_endpoints(nl, tm)
     assert abs(n_viol - len(ref_viol)) <= 2, (n_viol, len(ref_viol))
     assert n_viol <= n_paths <= K * n_viol
     assert n_pins > 2 * n_paths
     assert run["n1"] == n_paths
-    assert (run["n2"], run["tot2"]) == (run["n1"], run["tot1"])  # deterministic
+    assert (run["n2"], run["tot2"]) == (run["n1"], run["tot1"])
+    assert run["same"]  # the second extraction wrote the same bits
     assert run["n_pairs"] > 0
 
 
-def test_most_critical_endpoint_paths(run):
+def test_paths_on_every_failing_endpoint(run):
     P, nl, tm = run["P"], run["nl"], run["tm"]
-    assert len(P["viol"]) >= 400 and len(np.unique(P["ep"])) == 400
-    checked, amb = compare_paths(nl, tm, run["T"], run["K"], False, P, TOL32, endpoints=P["viol"][:400])
-    # every endpoint whose set is decided by more than the slack tolerance
-    # (1e-3 ps + 1e-6 x ~3.7 us here, ~3.7 ps) matches exactly; with K = 32
-    # the 32nd and 33rd paths of a critical endpoint are often closer than
-    # that, so a share of the endpoints is ambiguous by the margin rule
-    assert checked >= 300, (checked, amb)
+    d = compare_paths(nl, tm, run["T"], run["K"], False, P, TOL32, extra=1, detail=True)
+    # every decided endpoint matched exactly inside compare_paths; with K = 32
+    # the 32nd and 33rd paths of an endpoint are more often closer than the
+    # slack tolerance (1e-3 ps + 1e-6 x ~4 us here, ~4 ps), so a few percent
+    # of the endpoints are ambiguous and pass the validity checks instead
+    assert d["checked"] + d["ambiguous"] >= len(_failing_endpoints(nl, tm))
+    assert d["ambiguous"] <= 0.1 * (d["checked"] + d["ambiguous"]), d["ambiguous"]
+    assert d["paths"] == len(P["ep"])
+    print(f"\nstress path sets: {d['checked']} decided endpoints identical, {d['ambiguous']} ambiguous "
+          f"({len(d['differ'])} of them with another set), {d['paths']} paths, "
+          f"max |slack - oracle| {d['max_slack_err']:.3g} ps")
 
 
 def test_loss_and_gradient(run):
