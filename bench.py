@@ -166,11 +166,9 @@ LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single c
 SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     "fwd_sweep": {"bytes": 455568128, "sources": SWEEP_SOURCES,
-                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a",
-                  "profile": "profiles/fwd_sweep_1.2M.md"},
+                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a"},
     "bwd_sweep": {"bytes": 127864576, "sources": SWEEP_SOURCES,
-                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a",
-                  "profile": "profiles/bwd_sweep_1.2M.md"},
+                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a"},
 }
 
 
@@ -193,12 +191,70 @@ def list_length(K: int) -> int:
     return next(b for b in (0, 3, 7, 15, 31) if b >= K - 1)
 
 
-def algorithmic_bytes(kernel: str, nl, g_info: dict) -> float:
-    """Compulsory DRAM bytes of one launch of `kernel` (FP32 graph, 4-byte indices).
+def netlist_counts(nl) -> dict:
+    """Element counts the byte models are stated in."""
+    import numpy as np
+    C, P, N = nl.n_cells, nl.n_pins, nl.n_nets
+    S = P - N
+    sink_cell_type = nl.cell_type[nl.pin_cell[nl.pin_dir == 0]]
+    n_in = int((sink_cell_type == 0).sum())          # inputs of combinational cells
+    return {"cells": C, "pins": P, "nets": N, "sinks": S, "comb_inputs": n_in, "endpoints": int(S - n_in),
+            "comb": int((nl.cell_type == 0).sum())}
 
-    Each array element a kernel must read or write is counted once; gathers
-    of shared data (cell positions, driver arrival) are counted once per
-    element of the gathered array.
+
+# The method's own traffic model: the compulsory bytes of each step of the
+# timing iteration, each array element touched once, FP32 values and 4-byte
+# indices, per element (the step names follow the hot-path table):
+#   a1+a2 net RC       read 28 B per sink and 28 B per net, write 4 B per sink and 4 B per net
+#   a3+a4 forward      read 16 B per cell input pin and 8 B per cell, write 4 B per pin and 8 B per cell
+#   a5 backward        12 B per pin
+#   a6 slack, WNS/TNS  12 B per pin (here: per endpoint; other pins' slacks are formed on request)
+#   a7-a10 extraction and pair update
+#                      20 B per pair occurrence (a net arc on an extracted path) for the
+#                      search and 32 B per occurrence for the pair update (4 radix passes x 8 B)
+#   a11 loss           40 B per pair; the backward pass also 8 B per pin and 8 B per cell
+# The sidetrack lists of the forward sweep are not part of a3+a4: they are
+# the top-K search's data (a9), moved into the sweep by this design, and are
+# reported on their own.
+MODEL_STEPS = {
+    "net_rc": "a1+a2", "fwd_sweep": "a3+a4", "bwd_sweep": "a5", "ep_wns": "a6 (endpoints)",
+    "topk+pair_walk": "a7-a10", "pp_fwd": "a11 forward", "pp_bwd": "a11 backward",
+}
+
+
+def model_bytes(step: str, nl, g_info: dict) -> float:
+    """Bytes of one launch of `step` by the method's traffic model above."""
+    c = netlist_counts(nl)
+    if step == "net_rc":
+        return 32 * c["sinks"] + 32 * c["nets"]
+    if step == "fwd_sweep":
+        return 16 * c["comb_inputs"] + 8 * c["comb"] + 4 * c["pins"] + 8 * c["comb"]
+    if step == "bwd_sweep":
+        return 12 * c["pins"]
+    if step == "ep_wns":
+        return 12 * c["endpoints"]
+    if step == "topk+pair_walk":
+        return (20 + 32) * g_info["path_pins"] / 2.0
+    if step == "pp_fwd":
+        return 40 * g_info["pairs"]
+    if step == "pp_bwd":
+        return 40 * g_info["pairs"] + 8 * c["pins"] + 8 * c["cells"]
+    raise ValueError(step)
+
+
+def list_bytes(nl, g_info: dict) -> float:
+    """Sidetrack-list bytes of one forward sweep: per combinational cell the
+    inherited list read and its own list written, L entries of 8 B each."""
+    return netlist_counts(nl)["comb"] * 16 * g_info["list_L"]
+
+
+def own_bytes(kernel: str, nl, g_info: dict) -> float:
+    """This design's compulsory DRAM bytes of one launch of `kernel` (FP32
+    graph, 4-byte indices): every array element the kernel as built must read
+    or write, counted once; gathers of shared data (cell positions, driver
+    arrival) are counted once per element of the gathered array.  Unlike the
+    method's model above this includes the design's own data (sidetrack
+    lists, padded records, compacted pair lists).
     """
     import numpy as np
     C, P, N = nl.n_cells, nl.n_pins, nl.n_nets
@@ -415,7 +471,8 @@ def run_ours(args):
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
     ktab = kernel_table(G, step, args.warmup + args.steps, nl, info)
     lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
-    ploop = placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream)
+    ploop = {"every_10_of_500": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=500, every=10),
+             "every_15_of_150": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15)}
     incr = None if args.no_incremental else incremental(G, xs, ys, T, K, mv, stream)
     t1 = table1(G, xs[0], ys[0], T) if not args.no_table1 else None
     fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
@@ -435,16 +492,32 @@ def run_ours(args):
         roof = None
         if prof_n > 0:
             per_launch_ms = prof_ms / prof_n
-            bytes_ = algorithmic_bytes(args.roofline_kernel, nl, info)
+            kern = args.roofline_kernel
+            in_model = kern in MODEL_STEPS
+            bytes_ = model_bytes(kern, nl, info) if in_model else own_bytes(kern, nl, info)
             achieved = bytes_ / (per_launch_ms / 1000.0) / 1e9
-            roof = {"kernel": args.roofline_kernel, "bound": "hbm", "achieved": round(achieved, 1),
+            roof = {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                    "peak_source": peak_src, "traffic": profiled_traffic(args.roofline_kernel),
+                    "peak_source": peak_src, "traffic": profiled_traffic(kern),
                     "algorithmic_bytes_per_launch": int(bytes_),
+                    "bytes_basis": (f"the method's traffic model, step {MODEL_STEPS[kern]} (per-element "
+                                    "figures in bench.model_bytes)") if in_model else "this design's own count",
                     "launch_ms": round(per_launch_ms, 4), "launches": prof_n,
-                    "launch_unit": LAUNCH_UNIT.get(args.roofline_kernel, "one kernel launch")}
+                    "launch_unit": LAUNCH_UNIT.get(kern, "one kernel launch")}
+            if kern == "fwd_sweep":
+                lb = list_bytes(nl, info)
+                ob = own_bytes(kern, nl, info)
+                roof["sidetrack_lists"] = {
+                    "bytes_per_launch": int(lb), "gbs": round(lb / (per_launch_ms / 1000.0) / 1e9, 1),
+                    "note": "top-K search data (a9) built inside the sweep; not counted in achieved"}
+                roof["own_bytes_per_launch"] = int(ob)
+                roof["own_gbs"] = round(ob / (per_launch_ms / 1000.0) / 1e9, 1)
         cfgd = workload_desc(cfg, nl)
         cfgd.update({"seed": args.seed, "placements": f"{N_POS_SETS} seeded Gaussian moves (sigma {SIGMA} um), cycled",
+                     "formed_on_request": "not in the timed iteration, which consumes none of them: required times "
+                                          "and slacks of pins other than endpoints, input pins' arrivals "
+                                          "(sta_get_timing), the (slack, pin) order of the failing endpoints and "
+                                          "the paths' pin lists (sta_get_paths)",
                      "l2": "no flush: per-step working set (netlist + timing state, ~0.5 GB) exceeds the 126 MB L2",
                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                      "w0": W0, "w1": W1, "beta": BETA})
@@ -459,8 +532,9 @@ def run_ours(args):
                        "paths_per_step": n_paths, "path_pins_per_step": n_path_pins, "pairs_after": n_pairs},
         }
         for v in ktab.values():
-            v["frac"] = round(v["gbs"] / hbm, 4)
+            v["own_frac"] = round(v["own_gbs"] / hbm, 4)
         result["kernels"] = ktab
+        result["roofline_per_kernel"] = roofline_per_kernel(ktab, nl, info, hbm)
         result["loss_only"] = lonly
         result["placement_loop"] = ploop
         if incr:
@@ -472,8 +546,10 @@ def run_ours(args):
         if fp64:
             result["fp64_gpu"] = fp64
         if world == 1 and not args.no_cpu_baseline:
-            placements = [(xs[k].cpu().numpy(), ys[k].cpu().numpy()) for k in range(2)]
-            result["cpu_baseline"] = cpu_baseline(nl, cfg, T, placements)
+            placements = [(xs[k].double().cpu().numpy(), ys[k].double().cpu().numpy()) for k in range(2)]
+            ref = {}
+            result["cpu_baseline"] = cpu_baseline(nl, cfg, T, placements, keep=ref)
+            result["errors_vs_oracle"] = errors_vs_oracle(G, nl, K, T, xs[0], ys[0], ref)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -589,9 +665,32 @@ def kernel_table(G, step, k0, nl, info, reps=10):
         if n == 0:
             continue
         per = ms / n
-        by = algorithmic_bytes(name, nl, info)
-        out[name] = {"ms": round(per, 4), "algorithmic_bytes": int(by), "gbs": round(by / (per / 1e3) / 1e9, 1)}
+        by = own_bytes(name, nl, info)
+        out[name] = {"ms": round(per, 4), "own_bytes": int(by), "own_gbs": round(by / (per / 1e3) / 1e9, 1)}
     return out
+
+
+def roofline_per_kernel(ktab, nl, info, hbm):
+    """Each propagation, extraction and loss kernel against the measured HBM
+    peak, by the method's traffic model (model_bytes) and its live duration
+    from kernel_table.  The search and the pair walk together do a7-a10; the
+    two backward loss kernels together a11's backward pass."""
+    rows = {}
+
+    def add(step, ms, kernels):
+        b = model_bytes(step, nl, info)
+        g = b / (ms / 1e3) / 1e9
+        rows[step] = {"step": MODEL_STEPS[step], "kernels": kernels, "ms": round(ms, 4), "model_bytes": int(b),
+                      "gbs": round(g, 1), "frac": round(g / hbm, 4)}
+
+    for k in ("net_rc", "fwd_sweep", "bwd_sweep", "ep_wns", "pp_fwd"):
+        if k in ktab:
+            add(k, ktab[k]["ms"], [k])
+    if "topk" in ktab and "pair_walk" in ktab:
+        add("topk+pair_walk", ktab["topk"]["ms"] + ktab["pair_walk"]["ms"], ["topk", "pair_walk"])
+    if "pp_bwd_net" in ktab and "pp_bwd_cell" in ktab:
+        add("pp_bwd", ktab["pp_bwd_net"]["ms"] + ktab["pp_bwd_cell"]["ms"], ["pp_bwd_net", "pp_bwd_cell"])
+    return rows
 
 
 def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100):
@@ -616,9 +715,11 @@ def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100):
 
 
 def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15):
-    """The paper's use of the hot path in placement: the loss forward +
-    backward every step, a timing iteration (STA, extraction, pair update)
-    every `every` steps (m = 15, Section IV)."""
+    """The hot path as placement uses it: the loss forward + backward every
+    step, a timing iteration (STA, extraction, pair update) every `every`
+    steps.  The 1.2M-cell workload is configured as one timing iteration
+    every 10 steps of a 500-step loop; the paper re-times every m = 15 steps
+    (Section IV)."""
     import torch
     def one(k):
         x, y = xs[k % len(xs)], ys[k % len(ys)]
@@ -764,11 +865,13 @@ def table1(G, x, y, T, reps=3):
 
 # ------------------------------------------------------------ CPU oracle --
 
-def oracle_iteration(nl, cfg, T, pos, state=None):
+def oracle_iteration(nl, cfg, T, pos, state=None, keep=None):
     """One full timing iteration of the FP64 oracle at placement `pos`: STA of
     the whole netlist, report_timing_endpoint(all failing endpoints, K) in
     one call, the Eq. (w_ij) pair update (the pair set `state` carried from
-    the last iteration) and the loss.  Returns its seconds and the new state."""
+    the last iteration) and the loss.  Returns its seconds, the new state and
+    the number of failing endpoints; with `keep` (a dict) it also leaves the
+    timing, the paths and the new pair set there."""
     import oracle
     x, y = pos
     t0 = time.perf_counter()
@@ -777,24 +880,115 @@ def oracle_iteration(nl, cfg, T, pos, state=None):
     in_p, w = oracle.update_pairs(nl, P, tm["wns"], W0, W1,
                                   None if state is None else state[0], None if state is None else state[1])
     oracle.loss(nl, in_p, w, BETA, x, y)
-    return time.perf_counter() - t0, (in_p, w), len(P["viol"])
+    sec = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(tm=tm, paths=P, in_p=in_p, w=w)
+    return sec, (in_p, w), len(P["viol"])
 
 
-def cpu_baseline(nl, cfg, T, placements):
+def host_cpu() -> dict:
+    """The host's CPU: logical cores (nproc), those this process may use, and the model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "usable": len(os.sched_getaffinity(0)), "model": model}
+
+
+def cpu_baseline(nl, cfg, T, placements, keep=None):
     """The oracle as it stands on one host core: full timing iterations (every
     failing endpoint, nothing scaled) at consecutive placements, the pair set
-    carried from one to the next as in the placement loop."""
+    carried from one to the next as in the placement loop.  `keep` receives
+    the first iteration's results (for the error report)."""
     state, total, nvs = None, 0.0, []
-    for pos in placements:
-        sec, state, nv = oracle_iteration(nl, cfg, T, pos, state)
+    for i, pos in enumerate(placements):
+        sec, state, nv = oracle_iteration(nl, cfg, T, pos, state, keep if i == 0 else None)
         total += sec
         nvs.append(nv)
     n = len(placements)
     return {"value": round(n / total, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"{n} full timing iterations of the same workload at consecutive placements: FP64 STA, "
                       f"top-{cfg.K} extraction on every failing endpoint ({', '.join(str(v) for v in nvs)}), "
                       f"pair update and loss; {total:.1f} s of single-threaded CPU work",
             "seconds_per_iteration": round(total / n, 3)}
+
+
+def errors_vs_oracle(G, nl, K, T, xd, yd, ref):
+    """The FP32 GPU results at one placement against the FP64 oracle's at the
+    same placement (the first CPU-baseline iteration, `ref`), per result:
+    arrival, required time and slack of every pin (max |d| in ps, max |d| /
+    value scale, and max |d| over the stated tolerance 1e-3 ps + 1e-6 x
+    scale: at most 1 is within it); WNS / TNS relative; the path sets of every
+    failing endpoint under the margin rule (decided endpoints must match
+    exactly); the pair set after one update from an empty set; the loss and
+    the gradient on the GPU's pair set (relative, relative L2)."""
+    import numpy as np
+    tests_dir = os.path.join(ROOT, "tests")
+    if tests_dir not in sys.path:
+        sys.path.insert(0, tests_dir)
+    import oracle
+    from parity_util import TOL32, compare_paths, sta_scales
+    tm = ref["tm"]
+    a, r = TOL32
+    out = {"tolerance": "|d| <= 1e-3 ps + 1e-6 x scale; scale: |arr|, max(|req|, T - req), "
+                        "max(|arr|, |req|, T - slack)"}
+    wns, tns = G.sta_propagate(xd, yd, T)
+    got = [t.double().cpu().numpy() for t in G.sta_get_timing()]
+    for name, g, sc in zip(("arr", "req", "slack"), got, sta_scales(tm, T)):
+        d = np.abs(g - tm[name])
+        out[name] = {"max_abs_ps": float(d.max()),
+                     "max_rel": float((d / np.maximum(np.abs(sc), 1e-30)).max()),
+                     "max_over_tol": float((d / (a + r * np.abs(sc))).max())}
+    out["wns_rel"] = abs(wns - tm["wns"]) / max(abs(tm["wns"]), 1e-30)
+    out["tns_rel"] = abs(tns - tm["tns"]) / max(abs(tm["tns"]), 1e-30)
+    G.extract_critical_paths(-1, K, False)
+    P = {k: v.cpu().numpy() for k, v in G.sta_get_paths().items()}
+    try:
+        d = compare_paths(nl, tm, T, K, False, P, TOL32, detail=True)
+        out["paths"] = {"decided_endpoints": d["checked"], "decided_mismatching": 0,
+                        "ambiguous_endpoints": d["ambiguous"], "ambiguous_with_another_set": len(d["differ"]),
+                        "paths": d["paths"], "max_slack_abs_ps": float(d["max_slack_err"])}
+    except AssertionError as e:
+        out["paths"] = {"decided_mismatching": "at least 1", "first_failure": str(e)[:300]}
+    G.attraction_reset_pairs()
+    G.attraction_update_pairs(W0, W1)
+    pins, w = G.attraction_get_pairs()
+    pins, w = pins.cpu().numpy().astype(np.int64), w.double().cpu().numpy()
+    in_ref, w_ref = oracle.update_pairs(nl, ref["paths"], tm["wns"], W0, W1)
+    ref_pins = np.nonzero(in_ref)[0]
+    common = np.intersect1d(pins, ref_pins)
+    wg = np.zeros(nl.n_pins)
+    wg[pins] = w
+    out["pairs"] = {"gpu": int(len(pins)), "oracle": int(len(ref_pins)),
+                    "symmetric_difference": int(len(np.setxor1d(pins, ref_pins))),
+                    "max_rel_weight_diff": float((np.abs(wg[common] - w_ref[common]) /
+                                                  np.abs(w_ref[common])).max()) if len(common) else 0.0}
+    in_p = np.zeros(nl.n_pins, np.uint8)
+    in_p[pins] = 1
+    x0, y0 = xd.double().cpu().numpy(), yd.double().cpu().numpy()
+    pp, gx_r, gy_r = oracle.loss(nl, in_p, wg, BETA, x0, y0)
+    lg = G.attraction_loss_fwd(xd, yd, BETA).item()
+    gx, gy = G.attraction_loss_bwd(xd, yd, BETA)
+    g = np.concatenate([gx.double().cpu().numpy(), gy.double().cpu().numpy()])
+    gr = np.concatenate([gx_r, gy_r])
+    out["loss_rel"] = abs(lg - pp) / max(abs(pp), 1e-30)
+    out["grad_rel_l2"] = float(np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-30))
+    return out
 
 
 REF_BUDGET_S = 150.0  # timed oracle work of the reference arm at most (its run ends within minutes)

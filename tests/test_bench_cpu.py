@@ -48,3 +48,30 @@ def test_cpu_baseline_times_full_iterations():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
     assert cb["sample"].startswith("2 full timing iterations")
     assert abs(cb["seconds_per_iteration"] - 1.0 / cb["value"]) < 1e-3
+
+
+def test_cpu_baseline_keeps_the_first_iteration_and_names_the_host():
+    cfg = netgen.CONFIGS["tiny"]
+    nl = netgen.generate(cfg, 1)
+    T = oracle.clock_period(nl, cfg.t_factor)
+    keep = {}
+    cb = bench.cpu_baseline(nl, cfg, T, [(nl.x, nl.y)], keep=keep)
+    assert set(keep) == {"tm", "paths", "in_p", "w"}
+    assert keep["tm"]["T"] == T and len(keep["paths"]["viol"]) > 0
+    assert cb["host"]["nproc"] >= 1 and 1 <= cb["host"]["usable"] <= cb["host"]["nproc"]
+
+
+def test_model_bytes_follow_the_per_element_figures():
+    nl = netgen.generate("tiny", 1)
+    c = bench.netlist_counts(nl)
+    assert c["sinks"] == nl.n_pins - nl.n_nets
+    assert c["comb_inputs"] + c["endpoints"] == c["sinks"]
+    info = {"path_pins": 1000, "pairs": 50, "list_L": 15}
+    assert bench.model_bytes("fwd_sweep", nl, info) == 16 * c["comb_inputs"] + 16 * c["comb"] + 4 * nl.n_pins
+    assert bench.model_bytes("net_rc", nl, info) == 32 * (c["sinks"] + nl.n_nets)
+    assert bench.model_bytes("bwd_sweep", nl, info) == 12 * nl.n_pins
+    assert bench.model_bytes("topk+pair_walk", nl, info) == 52 * 500
+    assert bench.model_bytes("pp_bwd", nl, info) == 40 * 50 + 8 * nl.n_pins + 8 * nl.n_cells
+    assert bench.list_bytes(nl, info) == c["comb"] * 16 * 15
+    assert set(bench.MODEL_STEPS) == {"net_rc", "fwd_sweep", "bwd_sweep", "ep_wns", "topk+pair_walk", "pp_fwd",
+                                      "pp_bwd"}
