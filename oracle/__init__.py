@@ -64,6 +64,8 @@ def _load():
         lib.or_loss.restype = C.c_double
         lib.or_loss.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P,
                                 C.c_double, C.c_int, P, P]
+        lib.or_net_weights.restype = C.c_int
+        lib.or_net_weights.argtypes = [C.c_int, P, P, C.c_double, C.c_double, C.c_double, P]
         lib.or_loss_kind.restype = C.c_double
         lib.or_loss_kind.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P,
                                      C.c_double, C.c_int, C.c_int, P, P]
@@ -228,3 +230,17 @@ def loss(nl, in_p, w, beta: float = 1.0, x=None, y=None, drop_fixed: bool = True
                           _p(np.ascontiguousarray(in_p, dtype=np.uint8)), _p(_f64(w)), float(beta),
                           int(bool(drop_fixed)), LOSS_KINDS[kind], _p(gx), _p(gy))
     return float(pp), gx, gy
+
+
+def net_weights(nl, timing: dict, alpha: float, gamma: float, w=None):
+    """Net weights from pin slacks with momentum: the net-weighting baseline
+    of Section II-C and of the "w/o Path Extraction" ablation (Section IV),
+    under this reading (the paper gives no formula): s_e = worst pin slack of
+    net e, c_e = min(1, max(0, -s_e) / |WNS|) (0 if WNS = 0),
+    w_e <- alpha w_e + (1 - alpha)(1 + gamma c_e), w starting at 1.
+    Returns (new weights, number of nets with s_e < 0)."""
+    lib = _load()
+    w = np.ones(nl.n_nets) if w is None else _f64(w).copy()
+    n = lib.or_net_weights(nl.n_nets, _p(_i32(nl.net_ptr)), _p(_f64(timing["slack"])), float(timing["wns"]),
+                           float(alpha), float(gamma), _p(w))
+    return w, int(n)

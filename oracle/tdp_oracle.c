@@ -22,6 +22,10 @@
  *                   of Section III-D, with its analytic gradient;
  *                   or_loss_kind also the HPWL and linear Euclidean pair
  *                   distances of the ablation (Section IV).
+ *   or_net_weights  the net-weighting baseline (Section II-C; the "w/o Path
+ *                   Extraction" ablation of Section IV): net weights from
+ *                   the worst pin slack on each net, with momentum (a stated
+ *                   reading: the paper gives no formula).
  *
  * Where the paper is silent (delay model, ties, endpoints) this file reads
  * it as follows: single corner, late only, ideal clock
@@ -576,4 +580,41 @@ double or_loss(int n_cells, int n_pins, int n_nets, const int32_t *pin_cell,
                const double *w, double beta, int drop_fixed, double *gx, double *gy) {
     return or_loss_kind(n_cells, n_pins, n_nets, pin_cell, net_ptr, pin_dx, pin_dy, cell_fixed, x, y,
                         in_p, w, beta, drop_fixed, 0, gx, gy);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Net weighting from pin slacks (the baseline of Section II-C and of the   */
+/* "w/o Path Extraction" ablation, Section IV)                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The net-weighting scheme the paper compares against (DREAMPlace 4.0's):
+ * the placement objective weights each net's wirelength by w_e (Section
+ * II-C), a net's weight follows the worst pin slack within the net (the
+ * three-pin-net example of Section III-A), and the weights are updated with
+ * momentum (Section IV).  The paper gives no constants or formula, so this
+ * is a stated reading:
+ *   s_e     worst slack over the pins of net e (slack[] from or_sta);
+ *   c_e     criticality min(1, max(0, -s_e) / |WNS|), 0 when WNS = 0;
+ *   w_e  <- alpha * w_e + (1 - alpha) * (1 + gamma * c_e).
+ * w is updated in place; returns the number of nets with s_e < 0.
+ */
+int or_net_weights(int n_nets, const int32_t *net_ptr, const double *slack, double wns, double alpha,
+                   double gamma, double *w) {
+    int n_crit = 0;
+    for (int e = 0; e < n_nets; ++e) {
+        double s = slack[net_ptr[e]];
+        for (int p = net_ptr[e] + 1; p < net_ptr[e + 1]; ++p)
+            if (slack[p] < s) s = slack[p];
+        double c = 0.0;
+        if (s < 0.0) {
+            ++n_crit;
+            if (wns < 0.0) {
+                c = -s / -wns;
+                if (c > 1.0) c = 1.0;
+            }
+        }
+        w[e] = alpha * w[e] + (1.0 - alpha) * (1.0 + gamma * c);
+    }
+    return n_crit;
 }
