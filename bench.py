@@ -473,6 +473,7 @@ def run_ours(args):
     lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
     ploop = {"every_10_of_500": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=500, every=10),
              "every_15_of_150": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15)}
+    netw = net_weighting(G, xs, ys, T, stream)
     incr = None if args.no_incremental else incremental(G, xs, ys, T, K, mv, stream)
     t1 = table1(G, xs[0], ys[0], T) if not args.no_table1 else None
     fp64 = None if args.no_fp64 else fp64_run(nl, xs, ys, T, K, dev, stream, wns, tns)
@@ -537,6 +538,7 @@ def run_ours(args):
         result["roofline_per_kernel"] = roofline_per_kernel(ktab, nl, info, hbm)
         result["loss_only"] = lonly
         result["placement_loop"] = ploop
+        result["net_weighting"] = netw
         if incr:
             result["incremental"] = incr
         if stages:
@@ -743,6 +745,43 @@ def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=1
     ms = e0.elapsed_time(e1) / steps
     return {"value": round(1000.0 / ms, 1), "unit": "placement steps/s", "steps": steps, "timing_every": every,
             "ms_per_step": round(ms, 4)}
+
+
+def net_weighting(G, xs, ys, T, stream, alpha=0.5, gamma=4.0, steps=20):
+    """The net-weighting baseline's timing iteration on this workload (the
+    "w/o Path Extraction" scheme): a full STA, whose backward sweep's
+    required times the weights need, and one momentum update of every net's
+    weight from its worst pin slack (net_weights_update).  Also the update
+    kernel alone: 28 B per net (net pointer, required-time key, driver
+    arrival, weight read and written)."""
+    import torch
+    G.net_weights_reset()
+
+    def one(k):
+        G.sta_propagate(xs[k % len(xs)], ys[k % len(ys)], T, sync=False)
+        G.net_weights_update(alpha, gamma, sync=False)
+
+    for k in range(3):
+        one(k)
+    G.sta_join()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    G.tdp_profile_kernel("net_weights")
+    e0.record(stream)
+    for k in range(steps):
+        one(3 + k)
+    G.sta_join()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    n, kms = G.tdp_profile_read()
+    G.tdp_profile_kernel(None)
+    ms = e0.elapsed_time(e1) / steps
+    n_crit = G.net_weights_update(alpha, gamma)
+    by = 28.0 * G.n_nets
+    per = kms / max(n, 1)
+    return {"value": round(1000.0 / ms, 1), "unit": "iter/s", "ms_per_step": round(ms, 4), "steps": steps,
+            "alpha": alpha, "gamma": gamma, "critical_nets": n_crit,
+            "update_kernel": {"ms": round(per, 4), "bytes": int(by), "gbs": round(by / (per / 1e3) / 1e9, 1)}}
 
 
 INC_MOVED = (1, 12, 120, 1200, 12000, 120000, None)  # cells moved per call; None: every movable cell

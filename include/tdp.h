@@ -338,6 +338,34 @@ TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const vo
 TDP_API tdp_status attraction_set_loss_kind(tdp_graph *g, tdp_loss_kind kind);
 
 /*
+ * Net weighting from pin slacks, with momentum: the net-weighting scheme the
+ * paper compares its pin-pair attraction against (Section II-C, the weighted
+ * wirelength objective sum_e w_e WL_e; the "w/o Path Extraction" column of
+ * the ablation, Section IV, DREAMPlace 4.0's pin-level scheme).  The paper
+ * names the scheme without its formula; this library reads it as
+ *   s_e  = the worst slack over the pins of net e (equal to its driver
+ *          pin's slack, as sta_get_timing reports it),
+ *   c_e  = min(1, max(0, -s_e) / |WNS|)  (0 when WNS = 0),
+ *   w_e <- alpha * w_e + (1 - alpha) * (1 + gamma * c_e),
+ * with every w_e starting at 1 (sta_build, net_weights_reset).  The weights
+ * are for the caller's weighted wirelength; this library computes no
+ * wirelength.
+ * net_weights_update: one update from the last sta_propagate (waits for its
+ *   backward sweep).  alpha in [0, 1] (momentum), gamma >= 0 (weight gain).
+ *   n_critical_out: host int64, the number of nets with s_e < 0 (the call
+ *   then synchronises), or NULL.  Stream-ordered otherwise.
+ * net_weights_get: copies the weights (float or double [n_nets], the graph's
+ *   precision) to w_dev; stream-ordered.
+ * net_weights_reset: every weight back to 1.
+ * Errors: TDP_ERR_INVALID (NULL graph or output, alpha or gamma out of
+ * range), TDP_ERR_STATE (update before sta_propagate), TDP_ERR_OOM,
+ * TDP_ERR_CUDA, TDP_ERR_TIMEOUT (as sta_propagate).
+ */
+TDP_API tdp_status net_weights_update(tdp_graph *g, double alpha, double gamma, int64_t *n_critical_out);
+TDP_API tdp_status net_weights_get(tdp_graph *g, void *w_dev);
+TDP_API tdp_status net_weights_reset(tdp_graph *g);
+
+/*
  * attraction_loss_fwd for callers that cannot allocate device memory (no
  * counterpart in the paper): code working inside a device-memory budget fixed
  * in advance, code whose allocator owns all device memory, or code that must
@@ -382,7 +410,8 @@ TDP_API tdp_status attraction_loss_fwd_noalloc(int32_t n_nets, const int32_t *ne
  * of CUDA events on the graph's stream: "net_rc", "fwd_sweep" (one replay of
  * the forward level kernels), "bwd_sweep" (the backward level kernels and
  * WNS / TNS), "viol_sort" (the whole endpoint sort), "topk", "pair_walk",
- * "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell"; NULL or "" stops.
+ * "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell", "rt_expand",
+ * "ep_wns", "inc_moved", "fwd_inc", "net_weights"; NULL or "" stops.
  * tdp_profile_read: synchronise the stream, return the number of timed
  * launches and their summed device time in ms, and reset both.
  */

@@ -23,7 +23,8 @@ EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_g
            "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
            "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
            "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "attraction_set_loss_kind", "report_timing", "sta_join",
-           "sta_propagate_incremental", "sta_incremental_stats", "tdp_debug_fail_alloc",
+           "sta_propagate_incremental", "sta_incremental_stats", "net_weights_update",
+           "net_weights_get", "net_weights_reset", "tdp_debug_fail_alloc",
            "tdp_debug_pending_alloc_failure", "tdp_debug_set_sync_status", "tdp_last_error"]
 
 
@@ -80,6 +81,9 @@ def load() -> C.CDLL:
         "sta_join": [P],
         "sta_propagate_incremental": [P, P, P, D, P, P],
         "sta_incremental_stats": [P, P],
+        "net_weights_update": [P, D, D, P],
+        "net_weights_get": [P, P],
+        "net_weights_reset": [P],
         "tdp_debug_fail_alloc": [I64],
         "tdp_debug_pending_alloc_failure": [P],
         "tdp_debug_set_sync_status": [P, C.c_uint32],

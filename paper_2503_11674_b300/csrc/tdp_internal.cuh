@@ -62,7 +62,7 @@ constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 enum KernelId {
     KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
     KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_EP_WNS,
-    KID_INC_MOVED, KID_FWD_INC, KID_COUNT
+    KID_INC_MOVED, KID_FWD_INC, KID_NET_WEIGHTS, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -439,6 +439,10 @@ struct State {
     R *rt_delta = nullptr;
     // incremental propagation: cell positions of the last propagation
     R *xprev = nullptr, *yprev = nullptr;
+    // net weighting (net_weights_update): a weight per net, and the count of
+    // nets with negative slack of the last update
+    R *net_w = nullptr;
+    int32_t *n_crit = nullptr;
     int32_t *rt_out = nullptr;
     int64_t *rt_side_off = nullptr;
     int32_t *rt_sides = nullptr;
@@ -463,6 +467,7 @@ struct tdp_graph {
     double r = 0, c = 0, d0 = 0;
     int K = 0, keep_nonneg = 0, n_endpoints = -1;
     int loss_kind = 0;  // tdp_loss_kind of the attraction loss
+    bool net_w_init = false;  // net weights allocated and set to 1
     bool propagated = false, extracted = false;
     // failing endpoints: sorted by (slack, pin), or (extraction of all of
     // them) by pin until sta_get_paths sorts them and their path records

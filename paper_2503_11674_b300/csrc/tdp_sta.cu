@@ -1046,6 +1046,41 @@ __global__ void k_pin_slack(Topo t, State<R> s) {
     s.slack[p] = Acc<R>::diff(s.req[p], s.arr[p]);
 }
 
+// Net weights from pin slacks, with momentum: the net-weighting scheme the
+// paper compares against (Section II-C; the "w/o Path Extraction" ablation
+// of Section IV).  The paper gives no formula; the reading: a net's
+// criticality follows the worst slack over its pins, which is its driver
+// pin's slack (a sink's slack is its required time minus the driver's
+// arrival minus its Elmore delay, and the driver's required time is the
+// least over its sinks of required time minus Elmore delay), formed here as
+// k_pin_req and k_pin_slack form it; c = min(1, max(0, -slack) / |WNS|), 0
+// when WNS = 0, and w <- alpha w + (1 - alpha)(1 + gamma c).  A thread per
+// net; the nets of negative slack are counted with one integer atomic per
+// block.
+template <typename R>
+__global__ void k_net_weights(Topo t, State<R> s, R alpha, R gamma) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int crit = 0;
+    if (e < t.n_nets) {
+        const double wns = s.wns_tns[0];
+        const R sl = Acc<R>::diff(acc_unkey<R>(s.reqkey[e]), s.arr[ldg(&t.net_ptr[e])]);
+        R c = R(0);
+        if (sl < R(0)) {
+            crit = 1;
+            if (wns < 0.0) c = min(R(1), -sl / (R)(-wns));
+        }
+        s.net_w[e] = alpha * s.net_w[e] + (R(1) - alpha) * (R(1) + gamma * c);
+    }
+    crit = __syncthreads_count(crit);
+    if (threadIdx.x == 0 && crit > 0) atomicAdd(s.n_crit, crit);
+}
+
+template <typename R>
+__global__ void k_fill(R *p, int n, R v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
 // One launch per level (captured in a CUDA graph): a warp per task.
 template <typename R>
 __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, int first, int n_small,
@@ -1688,6 +1723,86 @@ extern "C" tdp_status sta_get_net_delays(tdp_graph *g, void *tnet_dev, void *clo
     return g->prec == TDP_FP32
                ? get_net_delays_impl<float>(g, (float *)tnet_dev, (float *)cload_dev, (float *)dcell_dev)
                : get_net_delays_impl<double>(g, (double *)tnet_dev, (double *)cload_dev, (double *)dcell_dev);
+}
+
+namespace tdp {
+
+// the net weights, allocated and set to 1 on first use (each buffer once:
+// a call that failed part way keeps what it got)
+template <typename R>
+static tdp_status net_weights_ready(tdp_graph *g) {
+    State<R> &s = state<R>(g);
+    const int n = std::max(g->topo.n_nets, 1);
+    if (!s.net_w) TDP_TRY(dalloc(g, &s.net_w, (size_t)n));
+    if (!s.n_crit) TDP_TRY(dalloc(g, &s.n_crit, 1));
+    if (!g->net_w_init) {
+        ++g->n_launch;
+        k_fill<R><<<div_up(n, 256), 256, 0, g->stream>>>(s.net_w, n, R(1));
+        TDP_LAUNCH_CHECK();
+        g->net_w_init = true;
+    }
+    return TDP_OK;
+}
+
+template <typename R>
+static tdp_status net_weights_impl(tdp_graph *g, double alpha, double gamma, int64_t *n_crit_out) {
+    State<R> &s = state<R>(g);
+    const Topo &t = g->topo;
+    TDP_TRY(net_weights_ready<R>(g));
+    join_side(g);  // the nets' required times are the backward sweep's
+    TDP_CUDA(cudaMemsetAsync(s.n_crit, 0, sizeof(int32_t), g->stream));
+    if (t.n_nets > 0) {
+        LaunchScope ls(g, KID_NET_WEIGHTS);
+        k_net_weights<R><<<div_up(t.n_nets, 256), 256, 0, g->stream>>>(t, s, (R)alpha, (R)gamma);
+    }
+    TDP_LAUNCH_CHECK();
+    if (n_crit_out) {
+        int32_t h = 0;
+        TDP_CUDA(cudaMemcpyAsync(&h, s.n_crit, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        TDP_TRY(check_sync_status(g));  // synchronises the stream
+        *n_crit_out = h;
+    }
+    return TDP_OK;
+}
+
+}  // namespace tdp
+
+extern "C" tdp_status net_weights_update(tdp_graph *g, double alpha, double gamma, int64_t *n_critical_out) {
+    if (!g || !(alpha >= 0.0 && alpha <= 1.0) || !(gamma >= 0.0) || !std::isfinite(gamma)) {
+        set_error("net_weights_update: NULL graph, alpha outside [0, 1] or gamma negative or not finite");
+        return TDP_ERR_INVALID;
+    }
+    if (!g->propagated) {
+        set_error("net_weights_update: call sta_propagate first");
+        return TDP_ERR_STATE;
+    }
+    return g->prec == TDP_FP32 ? net_weights_impl<float>(g, alpha, gamma, n_critical_out)
+                               : net_weights_impl<double>(g, alpha, gamma, n_critical_out);
+}
+
+extern "C" tdp_status net_weights_get(tdp_graph *g, void *w_dev) {
+    if (!g || !w_dev) {
+        set_error("net_weights_get: NULL graph or output");
+        return TDP_ERR_INVALID;
+    }
+    const size_t n = (size_t)g->topo.n_nets;
+    if (g->prec == TDP_FP32) {
+        TDP_TRY(net_weights_ready<float>(g));
+        TDP_CUDA(cudaMemcpyAsync(w_dev, g->s32.net_w, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
+    } else {
+        TDP_TRY(net_weights_ready<double>(g));
+        TDP_CUDA(cudaMemcpyAsync(w_dev, g->s64.net_w, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    return TDP_OK;
+}
+
+extern "C" tdp_status net_weights_reset(tdp_graph *g) {
+    if (!g) {
+        set_error("net_weights_reset: NULL graph");
+        return TDP_ERR_INVALID;
+    }
+    g->net_w_init = false;
+    return g->prec == TDP_FP32 ? net_weights_ready<float>(g) : net_weights_ready<double>(g);
 }
 
 namespace tdp {

@@ -235,6 +235,27 @@ class TimingGraph:
                                                 _ptr(grad_scale), _ptr(gx), _ptr(gy)))
         return gx, gy
 
+    # ------------------------------------------------------ net weighting --
+    def net_weights_update(self, alpha: float = 0.5, gamma: float = 4.0, sync: bool = True):
+        """One momentum update of the per-net weights from the last propagation's
+        pin slacks (the net-weighting baseline); returns the number of nets
+        with negative slack when ``sync``."""
+        if sync:
+            n = C.c_int64()
+            _abi.check("net_weights_update",
+                       self.lib.net_weights_update(self.handle, float(alpha), float(gamma), C.byref(n)))
+            return n.value
+        _abi.check("net_weights_update", self.lib.net_weights_update(self.handle, float(alpha), float(gamma), None))
+        return None
+
+    def net_weights_get(self) -> torch.Tensor:
+        w = torch.empty(self.n_nets, dtype=self.dtype, device=self.device)
+        _abi.check("net_weights_get", self.lib.net_weights_get(self.handle, _ptr(w)))
+        return w
+
+    def net_weights_reset(self):
+        _abi.check("net_weights_reset", self.lib.net_weights_reset(self.handle))
+
     # ---------------------------------------------------- instrumentation --
     def tdp_get_launch_count(self) -> int:
         n = C.c_int64()

@@ -61,6 +61,26 @@ def check_sta(G, tm, T, tol):
     return arr, req, slack
 
 
+def check_net_weights(nl, tm, T, w_gpu, w_ref, n_gpu, n_ref, tol, eps, k, gamma):
+    """Net weights after k updates against the oracle's (bound derived in
+    tests/test_gpu_net_weights.py): |dw| <= gamma (tol_s + tol_WNS) / |WNS|
+    + k x 4 rounding units x (1 + gamma); the counts of critical nets differ
+    by at most the nets whose slack is within tol_s of zero."""
+    a, r = tol
+    drv = np.asarray(nl.net_ptr)[:-1]
+    sc = sta_scales(tm, T)[2]
+    tol_s = a + r * sc[drv]
+    ct = nl.cell_type[nl.pin_cell]
+    ep = np.nonzero((nl.pin_dir == 0) & ((ct == 1) | (ct == 3)))[0]
+    tol_wns = a + r * sc[ep].max()
+    dc = (tol_s + tol_wns) / max(abs(tm["wns"]), 1e-30)
+    bound = gamma * dc + k * 4 * eps * (1 + gamma)
+    err = np.abs(w_gpu - w_ref)
+    assert (err <= bound).all(), (err.max(), int(np.argmax(err - bound)))
+    near0 = int((np.abs(tm["slack"][drv]) <= tol_s).sum())
+    assert abs(n_gpu - n_ref) <= near0, (n_gpu, n_ref, near0)
+
+
 def paths_by_endpoint(P):
     """{endpoint: [(slack, pins tuple), ...] in rank order}."""
     out = {}

@@ -118,6 +118,18 @@ def test_loss_and_gradient(run):
     assert np.linalg.norm(g - gr) / np.linalg.norm(gr) <= 1e-5
 
 
+def test_net_weights_at_full_size(run):
+    """The net-weighting baseline on the same propagation: one update from
+    weights of 1, against the oracle's, every net."""
+    from parity_util import check_net_weights
+    nl, G, tm, T = run["nl"], run["G"], run["tm"], run["T"]
+    G.net_weights_reset()
+    n_gpu = G.net_weights_update(0.5, 4.0)
+    w_ref, n_ref = oracle.net_weights(nl, tm, 0.5, 4.0)
+    w_gpu = G.net_weights_get().double().cpu().numpy()
+    check_net_weights(nl, tm, T, w_gpu, w_ref, n_gpu, n_ref, TOL32, 2.0 ** -23, 1, 4.0)
+
+
 def test_fp64_graph_every_pin_and_fp32_agreement(run):
     """The same workload on an FP64 graph: every pin's net delays, arrival,
     required time and slack against the FP64 oracle within the FP64-on-GPU
