@@ -289,3 +289,52 @@ def from_lists(cells: list, nets: list, r_per_um=0.004, c_per_um=0.2, d0_ps=5.0)
         y=np.array([c["y"] for c in cells], dtype=np.float32),
         r_per_um=r_per_um, c_per_um=c_per_um, d0_ps=d0_ps,
     )
+
+
+def random_dag(n_comb: int, n_ff: int, depth: int, wide_frac: float, seed: int = 1,
+               max_inputs: int = 10) -> Netlist:
+    """A small seeded levelized netlist whose combinational cells include
+    wide ones: a fraction ``wide_frac`` of them has 5 to ``max_inputs``
+    inputs, the rest 1 to 4.  Input 0 of a level-l cell comes from level
+    l - 1 (flip-flop Q for level 1), the others from a uniform lower level;
+    every flip-flop D pin from a uniform combinational cell; a net left
+    without a sink gets a primary-output port.  Positions uniform on the die,
+    R_drv ~ U[0.5, 2] kOhm, pin capacitance ~ U[1, 3] fF, zero pin offsets."""
+    rng = np.random.default_rng(seed)
+    cells = [{"type": "FF", "x": rng.uniform(0, DIE_UM), "y": rng.uniform(0, DIE_UM),
+              "rdrv": rng.uniform(0.5, 2.0)} for _ in range(n_ff)]
+    by_level = [list(range(n_ff))]
+    inputs = {}
+    for l in range(1, depth + 1):
+        n_l = n_comb // depth + (1 if l <= n_comb % depth else 0)
+        lvl = []
+        for _ in range(n_l):
+            c = len(cells)
+            cells.append({"type": "COMB", "x": rng.uniform(0, DIE_UM), "y": rng.uniform(0, DIE_UM),
+                          "rdrv": rng.uniform(0.5, 2.0)})
+            k = int(rng.integers(5, max_inputs + 1)) if rng.random() < wide_frac else int(rng.integers(1, 5))
+            drv = [by_level[l - 1][int(rng.integers(len(by_level[l - 1])))]]
+            for _ in range(k - 1):
+                ll = int(rng.integers(0, l))
+                drv.append(by_level[ll][int(rng.integers(len(by_level[ll])))])
+            inputs[c] = drv
+            lvl.append(c)
+        by_level.append(lvl)
+    comb = [c for lvl in by_level[1:] for c in lvl]
+    for f in range(n_ff):
+        inputs[f] = [comb[int(rng.integers(len(comb)))]]
+    sinks = {c: [] for c in range(len(cells))}
+    for c, drv in inputs.items():
+        for d in drv:
+            sinks[d].append(c)
+    n_driving = len(cells)
+    for d in range(n_driving):
+        if not sinks[d]:
+            cells.append({"type": "PO", "x": rng.uniform(0, DIE_UM), "y": rng.uniform(0, DIE_UM), "rdrv": 0.0})
+            sinks[d].append(len(cells) - 1)
+    nets = []
+    for d in range(n_driving):
+        order = rng.permutation(len(sinks[d]))
+        nets.append([(d, float(rng.uniform(1.0, 3.0)))] +
+                    [(sinks[d][i], float(rng.uniform(1.0, 3.0))) for i in order])
+    return from_lists(cells, nets)

@@ -349,11 +349,11 @@ def test_autograd_finite_differences(prec):
                 assert abs(fd - gref[c]) <= bound, (c, fd, gref[c], bound)
 
 
-def _pipeline(nl, T, prec):
+def _pipeline(nl, T, prec, K=16):
     G = _graph(nl, prec)
     x, y = _pos(nl, G.dtype)
     r = [G.sta_propagate(x, y, T)]
-    G.extract_critical_paths(-1, 16, False)
+    G.extract_critical_paths(-1, K, False)
     P = gpu_paths(G)
     G.attraction_update_pairs(10.0, 0.2)
     pins, w = G.attraction_get_pairs()
@@ -391,6 +391,30 @@ def test_level_launches_match_single_launch_sweeps(prec, monkeypatch):
     monkeypatch.setenv("TDP_LEVEL_GRAPHS", "1")
     lv = _pipeline(nl, T, prec)
     _assert_same(one, lv)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_wide_cells(prec, monkeypatch):
+    """Cells of more than four inputs (15% of them, 5 to 10 inputs) take the
+    one-input-at-a-time path of the forward sweep: STA on every pin and the
+    paths of every failing endpoint against the oracle, and the single-launch
+    sweeps bit-identical to the per-level launches."""
+    nl = netgen.random_dag(3000, 300, 20, 0.15, 4)
+    assert (np.bincount(nl.pin_cell[nl.pin_dir == 0], minlength=nl.n_cells) > 4).sum() > 300
+    T = oracle.clock_period(nl, 0.9)
+    tm = oracle.sta(nl, T=T)
+    G = _graph(nl, prec)
+    x, y = _pos(nl, G.dtype)
+    tol = tol_of(G.dtype)
+    G.sta_propagate(x, y, T)
+    check_sta(G, tm, T, tol)
+    G.extract_critical_paths(-1, 8, False)
+    checked, amb = compare_paths(nl, tm, T, 8, False, gpu_paths(G), tol)
+    assert checked > 0 and amb <= max(2, 0.05 * (checked + amb)), (checked, amb)
+    G.close()
+    one = _pipeline(nl, T, prec, 8)
+    monkeypatch.setenv("TDP_LEVEL_GRAPHS", "1")
+    _assert_same(one, _pipeline(nl, T, prec, 8))
 
 
 def _pipeline_async(nl, T, prec):
