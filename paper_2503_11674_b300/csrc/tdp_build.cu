@@ -94,8 +94,18 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     // loss
     TDP_TRY(dalloc(g, &s.net_pf, (size_t)t.n_nets + 32));
     TDP_TRY(dalloc(g, &s.cell_pf, (size_t)t.n_cells + 32));
-    TDP_TRY(dalloc(g, &s.pcells, t.n_cells));
     TDP_TRY(dalloc(g, &s.ppins, std::max(t.n_pins, 1)));
+    TDP_TRY(dalloc(g, &s.pcells, t.n_cells));
+    {
+        const size_t ns = (size_t)std::max(t.n_pins - t.n_nets, 1);
+        TDP_TRY(dalloc(g, &s.pr_a, ns));
+        TDP_TRY(dalloc(g, &s.pr_o, 4 * ns));
+        TDP_TRY(dalloc(g, &s.pr_w, ns));
+        TDP_TRY(dalloc(g, &s.pr_n, ns));
+        TDP_TRY(dalloc(g, &s.pr_big, (size_t)std::max(t.n_big, 1)));
+        TDP_TRY(dalloc(g, &s.pr_nbig, 1));
+        TDP_CUDA(cudaMemset(s.pr_nbig, 0, sizeof(int32_t)));
+    }
     TDP_TRY(dalloc(g, &s.pcnt, 2));
     TDP_TRY(dalloc(g, &s.cmp_blk, std::max(t.n_pins, std::max(t.n_nets, t.n_cells)) / kCompactItems + 2));
     TDP_CUDA(cudaMemset(s.net_pf, 0, (size_t)t.n_nets + 32));

@@ -415,14 +415,27 @@ struct State {
     long long *n_pairs = nullptr;
     // pairs, compacted for the loss: the sink pins of P, and the cells with
     // a pin in a pair (its sink or the driver of its net); the lists are
-    // ascending, counts in pcnt[0] (pins) and pcnt[1] (cells).  net_pf marks
-    // the nets holding a sink of P (for the larger nets' warps)
+    // ascending, counts in pcnt[0] (pins) and pcnt[1] (cells).  cell_pf
+    // flags those cells, net_pf the nets holding a sink of P
     uint8_t *net_pf = nullptr;    // [n_nets] 0, kPfSmall or kPfLarge
     uint8_t *cell_pf = nullptr;   // [n_cells]
     int32_t *ppins = nullptr;     // [n_pins]
     int32_t *pcells = nullptr;    // [n_cells]
     int32_t *pcnt = nullptr;      // [2]
     int32_t *cmp_blk = nullptr;   // per-block counts of the compaction
+    // pair records, one per sink of P in the order of ppins, rebuilt after
+    // every change of P: (sink's cell, driver's cell, sink's gradient slot,
+    // driver's gradient slot for the first pair of a net of at most
+    // kBigFanout sinks, else -1); pin offsets (sink x, y, driver x, y); the
+    // weight; for a net's first pair, the net's pairs.  pr_big lists the
+    // nets of more than kBigFanout sinks holding a pair: (first record,
+    // pairs, driver's gradient slot, 0), pr_nbig of them
+    int4 *pr_a = nullptr;         // [n_sinks]
+    R *pr_o = nullptr;            // [4 * n_sinks]
+    R *pr_w = nullptr;            // [n_sinks]
+    int32_t *pr_n = nullptr;      // [n_sinks]
+    int4 *pr_big = nullptr;       // [n_big]
+    int32_t *pr_nbig = nullptr;
     // loss
     R *gslot = nullptr;           // [2*n_pins] pin gradients in cell-slot order (x, y); zero outside P
     double *loss_part = nullptr;

@@ -4,24 +4,24 @@
 //
 // or, as set by attraction_set_loss_kind, with the pair's HPWL or linear
 // Euclidean distance in place of the quadratic term (the ablation of
-// Section IV).
-// with (x_d, y_d) the driver pin of s's net; pin coordinates are the cell
-// position plus the pin offset.  Both passes take the sinks of P from the
-// compacted, ascending list ppins, a thread per pair, so that no thread
-// scans the other sinks of a net; the pairs of one net are consecutive
-// there.  In the backward pass the first pair of a net of at most
-// kBigFanout sinks sums its net's pin gradients for the driver, in FP64, in
-// pin order; a larger net is a warp's (the static list of larger nets,
-// skipped without a pair), which walks its sinks and sums in a fixed order.
+// Section IV), with (x_d, y_d) the driver pin of s's net; pin coordinates
+// are the cell position plus the pin offset.  Both passes read the pair
+// records (State::pr_*, rebuilt after each change of P, in the ascending
+// order of the sinks of P, so that the pairs of one net are consecutive):
+// a record, then the two cells' positions, a thread per pair.
 //
 //   k_pp_fwd       terms in the working precision, FP64 total; fixed grid and
 //                  fixed-order block / grid reduction (deterministic)
-//   k_pp_bwd_net   pin gradients 2 beta w (p_s - p_d) of the sinks in P,
-//                  minus their sum on each net's driver, into the pins' slots
-//                  in the cell -> pins order (slots outside P stay zero)
+//   k_pp_bwd_net   pin gradients beta w dQ/dp_s of the sinks in P into their
+//                  slots in the cell -> pins order, and minus their sum, in
+//                  FP64, on each net's driver: the first pair of a net of at
+//                  most kBigFanout sinks sums its net's pairs in pin order; a
+//                  larger net holding a pair is a warp's (lanes strided over
+//                  its pairs, then a butterfly), in a fixed order either way.
+//                  Slots outside P stay zero
 //   k_pp_bwd_cell  per cell of the compacted list pcells, the FP64 sum of its
 //                  pins' slots times the incoming gradient scale (fixed cells
-//                  0); every other cell's gradient is 0
+//                  0); in the same launch, 0 for every other cell
 #include "tdp_internal.cuh"
 
 namespace tdp {
@@ -53,16 +53,33 @@ __device__ __forceinline__ void pair_grad(R dx, R dy, int kind, R &gx, R &gy) {
     }
 }
 
-// Pair term of sink pin p, with a the driver pin of its net.
+// the four offsets of pair record i (sink x, y, driver x, y)
+__device__ __forceinline__ void pair_offsets(const float *o, int i, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(o) + i);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void pair_offsets(const double *o, int i, double (&v)[4]) {
+    const double2 q0 = __ldg(reinterpret_cast<const double2 *>(o) + 2 * i);
+    const double2 q1 = __ldg(reinterpret_cast<const double2 *>(o) + 2 * i + 1);
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+}
+
+// The sink-minus-driver pin vector of pair record i (record r): the pin
+// coordinates are the cell position plus the pin offset.
 template <typename R>
-__device__ __forceinline__ R pin_pp(const Topo &t, const State<R> &s, const R *x, const R *y, int p, int a,
-                                    int kind) {
-    const int cd = t.pin_cell[a];
-    const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
-    const int cs = t.pin_cell[p];
-    const R dx = x[cs] + s.pin_dx[p] - xd;
-    const R dy = y[cs] + s.pin_dy[p] - yd;
-    return s.w[p] * pair_term(dx, dy, kind);
+__device__ __forceinline__ void pair_vec(const State<R> &s, const R *x, const R *y, int i, const int4 &r, R &dx,
+                                         R &dy) {
+    R o[4];
+    pair_offsets(s.pr_o, i, o);
+    const R xd = x[r.y] + o[2], yd = y[r.y] + o[3];
+    dx = x[r.x] + o[0] - xd;
+    dy = y[r.x] + o[1] - yd;
 }
 
 template <typename R>
@@ -75,8 +92,10 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     const int np = s.pcnt[0];
     double acc = 0.0;
     for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
-        const int p = s.ppins[i];
-        acc += (double)pin_pp(t, s, x, y, p, t.net_ptr[t.pin_net[p]], kind);
+        const int4 r = __ldg(&s.pr_a[i]);
+        R dx, dy;
+        pair_vec(s, x, y, i, r, dx, dy);
+        acc += (double)(__ldg(&s.pr_w[i]) * pair_term(dx, dy, kind));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) sh[wib] = acc;
@@ -102,120 +121,113 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     }
 }
 
-// Pin gradients of one net.  Lanes [first, first+step) share the net when it
-// is large; the driver's sum is returned to the caller (partial per lane).
+// Gradient of pair record i's term with respect to the sink's position,
+// beta w dQ/dp_s.
 template <typename R>
-__device__ __forceinline__ void net_grad(const Topo &t, State<R> &s, const R *x, const R *y,
-                                         int a, int b, int first, int step, double beta, int kind,
-                                         double &sx, double &sy) {
-    const int cd = t.pin_cell[a];
-    const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
-    for (int p = a + 1 + first; p < b; p += step) {
-        if (!s.in_p[p]) continue;
-        const int cs = t.pin_cell[p];
-        const R k = (R)beta * s.w[p];
-        R ux, uy;
-        pair_grad(x[cs] + s.pin_dx[p] - xd, y[cs] + s.pin_dy[p] - yd, kind, ux, uy);
-        const R gx = k * ux;
-        const R gy = k * uy;
-        sx += (double)gx;
-        sy += (double)gy;
-        const int slot = t.slot_of_pin[p];
-        s.gslot[2 * slot] = gx;
-        s.gslot[2 * slot + 1] = gy;
-    }
-}
-
-// Gradient of the pair term of sink pin p (driver pin a) with respect to the
-// sink's position, times beta w (the arithmetic of net_grad).
-template <typename R>
-__device__ __forceinline__ void pin_grad(const Topo &t, const State<R> &s, const R *x, const R *y, int p, int a,
+__device__ __forceinline__ void rec_grad(const State<R> &s, const R *x, const R *y, int i, const int4 &r,
                                          double beta, int kind, R &gx, R &gy) {
-    const int cd = t.pin_cell[a];
-    const R xd = x[cd] + s.pin_dx[a], yd = y[cd] + s.pin_dy[a];
-    const int cs = t.pin_cell[p];
-    const R k = (R)beta * s.w[p];
-    R ux, uy;
-    pair_grad(x[cs] + s.pin_dx[p] - xd, y[cs] + s.pin_dy[p] - yd, kind, ux, uy);
+    R dx, dy, ux, uy;
+    pair_vec(s, x, y, i, r, dx, dy);
+    const R k = (R)beta * __ldg(&s.pr_w[i]);
+    pair_grad(dx, dy, kind, ux, uy);
     gx = k * ux;
     gy = k * uy;
 }
 
-// warp tasks: warps [0, npw) take 32 consecutive pairs of ppins (a lane per
-// pair; pairs of larger nets are left to their net's warp), warps
-// [npw, npw + n_big) one larger net each
+// warp tasks: warps [0, npw) take 32 consecutive pair records (a lane per
+// pair), warps [npw, npw + pr_nbig) one larger net each
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
                                                     const R *__restrict__ y, double beta, int kind) {
     const int lane = threadIdx.x & 31;
     const int np = s.pcnt[0];
     const int npw = (np + 31) >> 5;
-    const int tasks = npw + t.n_big;
+    const int tasks = npw + *s.pr_nbig;
     const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
     for (int task = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); task < tasks; task += nwarps) {
         if (task < npw) {
             const int i = task * 32 + lane;
             if (i >= np) continue;
-            const int p = s.ppins[i];
-            const int e = t.pin_net[p];
-            const int a = t.net_ptr[e];
-            if (t.net_ptr[e + 1] - a - 1 > kBigFanout) continue;  // its net's warp
+            const int4 r = __ldg(&s.pr_a[i]);
             R gx, gy;
-            pin_grad(t, s, x, y, p, a, beta, kind, gx, gy);
-            const int slot = t.slot_of_pin[p];
-            s.gslot[2 * slot] = gx;
-            s.gslot[2 * slot + 1] = gy;
-            if (i > 0 && t.pin_net[s.ppins[i - 1]] == e) continue;
-            // the net's first pair: the driver's gradient, minus the sum of
-            // the net's pin gradients in pin order (at most kBigFanout)
+            rec_grad(s, x, y, i, r, beta, kind, gx, gy);
+            s.gslot[2 * r.z] = gx;
+            s.gslot[2 * r.z + 1] = gy;
+            if (r.w < 0) continue;
+            // the first pair of a net of at most kBigFanout sinks: the driver's
+            // gradient, minus the sum of the net's pin gradients in pin order
             double sx = (double)gx, sy = (double)gy;
-            for (int j = i + 1; j < np; ++j) {
-                const int q = s.ppins[j];
-                if (t.pin_net[q] != e) break;
+            const int n = __ldg(&s.pr_n[i]);
+            for (int j = i + 1; j < i + n; ++j) {
+                const int4 q = __ldg(&s.pr_a[j]);
                 R qx, qy;
-                pin_grad(t, s, x, y, q, a, beta, kind, qx, qy);
+                rec_grad(s, x, y, j, q, beta, kind, qx, qy);
                 sx += (double)qx;
                 sy += (double)qy;
             }
-            const int ds = t.slot_of_pin[a];
-            s.gslot[2 * ds] = (R)(-sx);
-            s.gslot[2 * ds + 1] = (R)(-sy);
+            s.gslot[2 * r.w] = (R)(-sx);
+            s.gslot[2 * r.w + 1] = (R)(-sy);
         } else {
-            const int e = t.big_nets[task - npw];
-            if (!s.net_pf[e]) continue;  // warp-uniform
-            const int a = t.net_ptr[e];
+            const int4 big = __ldg(&s.pr_big[task - npw]);  // (first record, pairs, driver slot)
             double sx = 0.0, sy = 0.0;
-            net_grad(t, s, x, y, a, t.net_ptr[e + 1], lane, 32, beta, kind, sx, sy);
+            for (int j = big.x + lane; j < big.x + big.y; j += 32) {
+                const int4 q = __ldg(&s.pr_a[j]);
+                R qx, qy;
+                rec_grad(s, x, y, j, q, beta, kind, qx, qy);
+                sx += (double)qx;
+                sy += (double)qy;
+            }
             for (int o = 16; o > 0; o >>= 1) {
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane != 0) continue;
-            const int ds = t.slot_of_pin[a];
-            s.gslot[2 * ds] = (R)(-sx);
-            s.gslot[2 * ds + 1] = (R)(-sy);
+            s.gslot[2 * big.z] = (R)(-sx);
+            s.gslot[2 * big.z + 1] = (R)(-sy);
         }
     }
 }
 
+// Two roles in one launch, on disjoint cells: blocks [0, kCellBlocks) take
+// the compacted list pcells (the cells with a pin in a pair) densely, so that
+// the FP64 sums run on full warps; the other blocks write zero gradients to
+// every cell without a pin in a pair, eight cells a thread.
+constexpr int kCellBlocks = 148 * 4;
+constexpr int kZeroCells = 8;
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const double *gscale,
                                                      R *__restrict__ gx, R *__restrict__ gy) {
-    const int nc = s.pcnt[1];
-    const double g = gscale ? *gscale : 1.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        const int c = s.pcells[i];
-        double ax = 0.0, ay = 0.0;
-        if (!t.cell_fixed[c]) {
-            for (int k = t.cp_ptr[c]; k < t.cp_ptr[c + 1]; ++k) {
-                ax += (double)s.gslot[2 * k];
-                ay += (double)s.gslot[2 * k + 1];
+    if (blockIdx.x < kCellBlocks) {
+        const int nc = s.pcnt[1];
+        const double g = gscale ? *gscale : 1.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += kCellBlocks * blockDim.x) {
+            const int c = s.pcells[i];
+            double ax = 0.0, ay = 0.0;
+            if (!t.cell_fixed[c]) {
+                for (int k = t.cp_ptr[c]; k < t.cp_ptr[c + 1]; ++k) {
+                    ax += (double)s.gslot[2 * k];
+                    ay += (double)s.gslot[2 * k + 1];
+                }
+                ax *= g;
+                ay *= g;
             }
-            ax *= g;
-            ay *= g;
+            gx[c] = (R)ax;
+            gy[c] = (R)ay;
         }
-        gx[c] = (R)ax;
-        gy[c] = (R)ay;
+        return;
+    }
+    const int c0 = ((blockIdx.x - kCellBlocks) * blockDim.x + threadIdx.x) * kZeroCells;
+    if (c0 >= t.n_cells) return;
+    // cell_pf holds 32 bytes of padding past n_cells, and c0 is a multiple of 8
+    const uint2 f = *reinterpret_cast<const uint2 *>(s.cell_pf + c0);
+#pragma unroll
+    for (int k = 0; k < kZeroCells; ++k) {
+        const unsigned b = ((k < 4 ? f.x : f.y) >> (8 * (k & 3))) & 0xffu;
+        if (c0 + k < t.n_cells && b == 0u) {
+            gx[c0 + k] = R(0);
+            gy[c0 + k] = R(0);
+        }
     }
 }
 
@@ -233,15 +245,14 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
                          R *gx, R *gy) {
     Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    TDP_CUDA(cudaMemsetAsync(gx, 0, sizeof(R) * t.n_cells, g->stream));
-    TDP_CUDA(cudaMemsetAsync(gy, 0, sizeof(R) * t.n_cells, g->stream));
     {
         LaunchScope ls(g, KID_PP_BWD_NET);
         k_pp_bwd_net<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind);
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
-        k_pp_bwd_cell<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
+        const int zero_blocks = div_up(div_up(std::max(t.n_cells, 1), kZeroCells), 256);
+        k_pp_bwd_cell<R><<<kCellBlocks + zero_blocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
     }
     TDP_LAUNCH_CHECK();
     return TDP_OK;

@@ -252,13 +252,52 @@ void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const in
     k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, map, out);
 }
 
+// The loss's pair records (State::pr_*), a thread per sink of P: what the
+// loss passes read per pair in two rounds of loads (the record, then the two
+// cells' positions) instead of walking pin -> net -> driver -> cell.  The
+// first pair of a net finds the net's pairs (the records are ascending by
+// pin, and the net's pins end at net_ptr[e + 1]) by a binary search over at
+// most the net's fanout records.
+template <typename R>
+__global__ void k_pair_records(Topo t, State<R> s) {
+    const int np = s.pcnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const int p = s.ppins[i];
+        const int e = t.pin_net[p];
+        const int a = t.net_ptr[e], b = t.net_ptr[e + 1];
+        const bool big = b - a - 1 > kBigFanout;
+        int dslot = -1;
+        if (i == 0 || t.pin_net[s.ppins[i - 1]] != e) {
+            int lo = i + 1, hi = min(np, i + (b - a - 1));
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.ppins[mid] < b) lo = mid + 1;
+                else hi = mid;
+            }
+            const int cnt = lo - i;
+            s.pr_n[i] = cnt;
+            if (big) s.pr_big[atomicAdd(s.pr_nbig, 1)] = make_int4(i, cnt, t.slot_of_pin[a], 0);
+            else dslot = t.slot_of_pin[a];
+        }
+        s.pr_a[i] = make_int4(t.pin_cell[p], t.pin_cell[a], t.slot_of_pin[p], dslot);
+        R *o = s.pr_o + 4 * (size_t)i;
+        o[0] = s.pin_dx[p];
+        o[1] = s.pin_dy[p];
+        o[2] = s.pin_dx[a];
+        o[3] = s.pin_dy[a];
+        s.pr_w[i] = s.w[p];
+    }
+}
+
 template <typename R>
 tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
     compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt);
     compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1);
-    g->n_launch += 6;
+    TDP_CUDA(cudaMemsetAsync(s.pr_nbig, 0, sizeof(int32_t), g->stream));
+    k_pair_records<R><<<148 * 4, 256, 0, g->stream>>>(t, s);
+    g->n_launch += 7;
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
@@ -397,6 +436,7 @@ static tdp_status reset_pairs_impl(tdp_graph *g) {
     TDP_CUDA(cudaMemsetAsync(s.net_pf, 0, g->topo.n_nets, g->stream));
     TDP_CUDA(cudaMemsetAsync(s.cell_pf, 0, g->topo.n_cells, g->stream));
     TDP_CUDA(cudaMemsetAsync(s.pcnt, 0, 2 * sizeof(int32_t), g->stream));
+    TDP_CUDA(cudaMemsetAsync(s.pr_nbig, 0, sizeof(int32_t), g->stream));
     TDP_CUDA(cudaMemsetAsync(s.gslot, 0, 2 * sizeof(R) * (size_t)np, g->stream));
     return TDP_OK;
 }
