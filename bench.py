@@ -160,21 +160,27 @@ def workload_desc(cfg, nl):
 LAUNCH_UNIT = {"fwd_sweep": "one forward sweep over all logic levels (a single cooperative launch)",
                "bwd_sweep": "one backward sweep over all logic levels (a single cooperative launch)"}
 
-# DRAM bytes (read + write) per launch from an ncu capture of the 1.2M-cell
-# workload, with the SHA-256 of the sources the kernel was built from when it
-# was taken; the figure is reported only while those sources are unchanged.
+# DRAM bytes (read + write) per launch from ncu captures, by (workload, K),
+# with the SHA-256 of the sources the kernel was built from when it was
+# taken; a figure is reported only for its workload and while those sources
+# are unchanged.
 SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
+PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
-    "fwd_sweep": {"bytes": 455568128, "sources": SWEEP_SOURCES,
-                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a"},
-    "bwd_sweep": {"bytes": 127864576, "sources": SWEEP_SOURCES,
-                  "sha256": "db090ff34913870de507b5da7283c71163fe1dda32f0036a24c3264010305c2a"},
+    ("1.2M", 16): {
+        "fwd_sweep": {"bytes": 455400448, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
+        "bwd_sweep": {"bytes": 127428352, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
+        "pair_walk": {"bytes": 22964736, "sources": PAIR_SOURCES, "sha256": "7715ca6d89d8aa0b9a4c9dc7f83751e955eb98c0a18b3056372ef12a6195620e"},
+    },
+    ("stress", 32): {
+        "fwd_sweep": {"bytes": 2455318528, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
+    },
 }
 
 
-def profiled_traffic(kernel: str):
+def profiled_traffic(kernel: str, workload=("1.2M", 16)):
     import hashlib
-    rec = PROFILED_TRAFFIC.get(kernel)
+    rec = PROFILED_TRAFFIC.get(tuple(workload), {}).get(kernel)
     if rec is None:
         return None
     h = hashlib.sha256()
@@ -469,7 +475,7 @@ def run_ours(args):
     stages = None
     if args.stages:
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
-    ktab = kernel_table(G, step, args.warmup + args.steps, nl, info)
+    ktab = kernel_table(G, step, args.warmup + args.steps, nl, info, (cfg.name, K))
     lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
     ploop = {"every_10_of_500": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=500, every=10),
              "every_15_of_150": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15)}
@@ -499,7 +505,7 @@ def run_ours(args):
             achieved = bytes_ / (per_launch_ms / 1000.0) / 1e9
             roof = {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                    "peak_source": peak_src, "traffic": profiled_traffic(kern),
+                    "peak_source": peak_src, "traffic": profiled_traffic(kern, (cfg.name, K)),
                     "algorithmic_bytes_per_launch": int(bytes_),
                     "bytes_basis": (f"the method's traffic model, step {MODEL_STEPS[kern]} (per-element "
                                     "figures in bench.model_bytes)") if in_model else "this design's own count",
@@ -649,7 +655,7 @@ KERNEL_TABLE = ["net_rc", "fwd_sweep", "ep_wns", "bwd_sweep", "topk", "pair_walk
                 "pp_bwd_cell"]
 
 
-def kernel_table(G, step, k0, nl, info, reps=10):
+def kernel_table(G, step, k0, nl, info, workload, reps=10):
     """Live duration of every kernel of the iteration in the steady state (CUDA
     events on the kernel's own stream, one kernel at a time), its algorithmic
     bytes and the GB/s they make.  The backward sweep runs beside extraction,
@@ -669,6 +675,10 @@ def kernel_table(G, step, k0, nl, info, reps=10):
         per = ms / n
         by = own_bytes(name, nl, info)
         out[name] = {"ms": round(per, 4), "own_bytes": int(by), "own_gbs": round(by / (per / 1e3) / 1e9, 1)}
+        tr = profiled_traffic(name, workload)
+        if tr is not None:
+            out[name]["dram_traffic"] = tr
+            out[name]["dram_gbs"] = round(tr / (per / 1e3) / 1e9, 1)
     return out
 
 

@@ -640,6 +640,8 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
         // TDP_SERIAL_BWD=1: the backward sweep on the graph's stream, in order
         const char *ser = getenv("TDP_SERIAL_BWD");
         g->overlap_bwd = !(ser && ser[0] == '1');
+        const char *share = getenv("TDP_BWD_SHARE");
+        if (share) g->bwd_share = std::min(16, std::max(1, atoi(share)));
     }
     if (st == TDP_OK)
         st = precision == TDP_FP32 ? build_state<float>(g, netlist) : build_state<double>(g, netlist);

@@ -473,6 +473,9 @@ struct tdp_graph {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_bwd_go = nullptr, ev_bwd = nullptr;
     bool overlap_bwd = true, bwd_pending = false;
+    // the overlapped backward sweep's share of its resident grid, in 16ths
+    // (TDP_BWD_SHARE at sta_build, 1 to 16)
+    int bwd_share = 9;
     tdp::Topo topo;
     tdp::Levels lv;
     tdp::State<float> s32;

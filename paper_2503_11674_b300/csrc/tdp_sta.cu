@@ -1405,7 +1405,7 @@ static tdp_status backward(tdp_graph *g) {
         // blocks; measured at 1.2M cells, a step took 1.189, 1.157, 1.111,
         // 1.135, 1.171 and 1.270 ms for 7/16 to 12/16)
         int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
-        if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * kBwdOverlapNum / 16);
+        if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * g->bwd_share / 16);
         if (grid > 0) {
             State<R> &s = state<R>(g);
             ++g->n_launch;
