@@ -119,6 +119,14 @@ def _compare(nl, tm, T, tol, P, R, n, keep_nonneg):
     gset, rset = set(gseq), set(rseq)
     assert sure_r <= gset, len(sure_r - gset)
     assert sure_g <= rset, len(sure_g - rset)
+    # order: where the oracle's neighbouring slacks are separated beyond the
+    # tolerance, the same path at the same rank (equal slacks may come in
+    # another order: the GPU orders them by its expansion, not by R5)
+    for i in range(m):
+        sep_prev = i == 0 or rs[i] - rs[i - 1] > 4 * tolp
+        sep_next = i == m - 1 or rs[i + 1] - rs[i] > 4 * tolp
+        if sep_prev and sep_next and rs[i] < lim:
+            assert gseq[i] == rseq[i], i
     return len(sure_r)
 
 
