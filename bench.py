@@ -477,6 +477,7 @@ def run_ours(args):
         stages = time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, 20)
     ktab = kernel_table(G, step, args.warmup + args.steps, nl, info, (cfg.name, K))
     lonly = loss_only(G, xs, ys, loss_buf, gx, gy, stream)
+    lonly_fused = loss_only(G, xs, ys, loss_buf, gx, gy, stream, fused=True)
     ploop = {"every_10_of_500": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=500, every=10),
              "every_15_of_150": placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15)}
     netw = net_weighting(G, xs, ys, T, stream)
@@ -543,6 +544,7 @@ def run_ours(args):
         result["kernels"] = ktab
         result["roofline_per_kernel"] = roofline_per_kernel(ktab, nl, info, hbm)
         result["loss_only"] = lonly
+        result["loss_only_fused"] = lonly_fused
         result["placement_loop"] = ploop
         result["net_weighting"] = netw
         if incr:
@@ -705,14 +707,22 @@ def roofline_per_kernel(ktab, nl, info, hbm):
     return rows
 
 
-def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100):
+def loss_step(G, x, y, loss_buf, gx, gy, fused):
+    """The loss and its gradient: two calls (attraction_loss_fwd, _bwd) or the
+    fused one (attraction_loss_fwd_bwd, the same bits in two launches)."""
+    if fused:
+        G.attraction_loss_fwd_bwd(x, y, BETA, out=loss_buf, gx=gx, gy=gy)
+    else:
+        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
+        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+
+
+def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100, fused=False):
     """Steps of the attraction loss alone (forward + backward) on the current
     pair set, as a placement step between two timing iterations runs it."""
     import torch
     def one(k):
-        x, y = xs[k % len(xs)], ys[k % len(ys)]
-        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
-        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+        loss_step(G, xs[k % len(xs)], ys[k % len(ys)], loss_buf, gx, gy, fused)
     for k in range(5):
         one(k)
     torch.cuda.synchronize()
@@ -723,10 +733,11 @@ def loss_only(G, xs, ys, loss_buf, gx, gy, stream, steps=100):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return {"value": round(1000.0 / ms, 1), "unit": "loss fwd+bwd steps/s", "ms_per_step": round(ms, 4)}
+    return {"value": round(1000.0 / ms, 1), "unit": "loss fwd+bwd steps/s", "ms_per_step": round(ms, 4),
+            "call": "attraction_loss_fwd_bwd" if fused else "attraction_loss_fwd + attraction_loss_bwd"}
 
 
-def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15):
+def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=15, fused=True):
     """The hot path as placement uses it: the loss forward + backward every
     step, a timing iteration (STA, extraction, pair update) every `every`
     steps.  The 1.2M-cell workload is configured as one timing iteration
@@ -739,8 +750,7 @@ def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=1
             G.sta_propagate(x, y, T, sync=False)
             G.extract_critical_paths(-1, K, False, sync=False)
             G.attraction_update_pairs(W0, W1, sync=False)
-        G.attraction_loss_fwd(x, y, BETA, out=loss_buf)
-        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+        loss_step(G, x, y, loss_buf, gx, gy, fused)
     for k in range(every):
         one(k)
     G.sta_join()
@@ -754,7 +764,8 @@ def placement_loop(G, xs, ys, T, K, loss_buf, gx, gy, stream, steps=150, every=1
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     return {"value": round(1000.0 / ms, 1), "unit": "placement steps/s", "steps": steps, "timing_every": every,
-            "ms_per_step": round(ms, 4)}
+            "ms_per_step": round(ms, 4),
+            "loss_call": "attraction_loss_fwd_bwd" if fused else "attraction_loss_fwd + attraction_loss_bwd"}
 
 
 def net_weighting(G, xs, ys, T, stream, alpha=0.5, gamma=4.0, steps=20):

@@ -327,6 +327,22 @@ TDP_API tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const vo
                                const double *grad_scale_dev, void *gx_dev, void *gy_dev);
 
 /*
+ * attraction_loss_fwd_bwd: attraction_loss_fwd and attraction_loss_bwd in one
+ * call, for callers that need the loss and its gradient every step (a
+ * placer's step; the paper adds beta PP to the placement objective, Section
+ * III-A): the same loss and gradient, bit for bit, in two launches instead
+ * of three (the per-pair pass computes the terms with the pin gradients).
+ * Arguments as the two calls: x_dev, y_dev positions; beta; grad_scale_dev a
+ * device double scaling the gradient (NULL: 1); loss_dev one device double;
+ * gx_dev, gy_dev overwritten.  Stream-ordered, no host synchronisation.
+ * Errors: TDP_ERR_INVALID (NULL graph or argument, non-finite beta),
+ * TDP_ERR_CUDA.
+ */
+TDP_API tdp_status attraction_loss_fwd_bwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
+                                           const double *grad_scale_dev, double *loss_dev, void *gx_dev,
+                                           void *gy_dev);
+
+/*
  * attraction_set_loss_kind: the pair term Q(i, j) of later
  * attraction_loss_fwd / _bwd calls on g.  TDP_LOSS_QUADRATIC (the default)
  * is Eq. (9).  TDP_LOSS_HPWL (|dx| + |dy|, pin gradient beta w_s sign(dx),
@@ -411,7 +427,7 @@ TDP_API tdp_status attraction_loss_fwd_noalloc(int32_t n_nets, const int32_t *ne
  * the forward level kernels), "bwd_sweep" (the backward level kernels and
  * WNS / TNS), "viol_sort" (the whole endpoint sort), "topk", "pair_walk",
  * "pair_finish", "pp_fwd", "pp_bwd_net", "pp_bwd_cell", "rt_expand",
- * "ep_wns", "inc_moved", "fwd_inc", "net_weights"; NULL or "" stops.
+ * "ep_wns", "inc_moved", "fwd_inc", "net_weights", "pp_fwd_bwd"; NULL or "" stops.
  * tdp_profile_read: synchronise the stream, return the number of timed
  * launches and their summed device time in ms, and reset both.
  */

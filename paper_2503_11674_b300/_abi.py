@@ -21,7 +21,7 @@ EXPORTS = ["sta_build", "sta_destroy", "sta_propagate", "sta_get_timing", "sta_g
            "extract_critical_paths", "sta_get_paths_size", "sta_get_paths",
            "attraction_update_pairs", "attraction_reset_pairs", "attraction_set_pairs",
            "attraction_get_pairs", "attraction_loss_fwd", "attraction_loss_bwd",
-           "attraction_loss_fwd_noalloc", "tdp_get_launch_count",
+           "attraction_loss_fwd_noalloc", "attraction_loss_fwd_bwd", "tdp_get_launch_count",
            "tdp_profile_kernel", "tdp_profile_read", "tdp_selftest_grid_wait", "attraction_set_loss_kind", "report_timing", "sta_join",
            "sta_propagate_incremental", "sta_incremental_stats", "net_weights_update",
            "net_weights_get", "net_weights_reset", "tdp_debug_fail_alloc",
@@ -72,6 +72,7 @@ def load() -> C.CDLL:
         "attraction_loss_fwd": [P, P, P, D, P],
         "attraction_loss_bwd": [P, P, P, D, P, P, P],
         "attraction_loss_fwd_noalloc": [I32, P, P, P, P, P, P, P, D, P, P],
+        "attraction_loss_fwd_bwd": [P, P, P, D, P, P, P, P],
         "tdp_get_launch_count": [P, P],
         "tdp_profile_kernel": [P, C.c_char_p],
         "tdp_profile_read": [P, P, P],

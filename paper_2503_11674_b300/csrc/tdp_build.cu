@@ -469,7 +469,7 @@ namespace tdp {
 const char *const kKernelNames[KID_COUNT] = {"net_rc",    "fwd_sweep",   "bwd_sweep", "viol_sort",
                                               "topk",      "pair_walk",   "pair_finish", "pp_fwd",
                                               "pp_bwd_net", "pp_bwd_cell", "rt_expand", "ep_wns",
-                                              "inc_moved", "fwd_inc",     "net_weights"};
+                                              "inc_moved", "fwd_inc",     "net_weights", "pp_fwd_bwd"};
 
 static cudaEvent_t prof_event(tdp_graph *g) {
     if (!g->prof_free.empty()) {

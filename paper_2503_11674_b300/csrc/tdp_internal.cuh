@@ -62,7 +62,7 @@ constexpr int kKindPrev = 0x10, kKindMask = 0x0f;
 enum KernelId {
     KID_NET_RC, KID_FWD_SWEEP, KID_BWD_SWEEP, KID_VIOL_SORT, KID_TOPK, KID_PAIR_WALK,
     KID_PAIR_FINISH, KID_PP_FWD, KID_PP_BWD_NET, KID_PP_BWD_CELL, KID_RT_EXPAND, KID_EP_WNS,
-    KID_INC_MOVED, KID_FWD_INC, KID_NET_WEIGHTS, KID_COUNT
+    KID_INC_MOVED, KID_FWD_INC, KID_NET_WEIGHTS, KID_PP_FWD_BWD, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 

@@ -19,6 +19,8 @@
 //                  larger net holding a pair is a warp's (lanes strided over
 //                  its pairs, then a butterfly), in a fixed order either way.
 //                  Slots outside P stay zero
+//   (attraction_loss_fwd_bwd runs k_pp_bwd_net with the loss terms added,
+//   the total formed as k_pp_fwd forms it, then k_pp_bwd_cell: two launches)
 //   k_pp_bwd_cell  per cell of the compacted list pcells, the FP64 sum of its
 //                  pins' slots times the incoming gradient scale (fixed cells
 //                  0); in the same launch, 0 for every other cell
@@ -53,6 +55,18 @@ __device__ __forceinline__ void pair_grad(R dx, R dy, int kind, R &gx, R &gy) {
     }
 }
 
+// a pin's gradient slot (x, y) as one vector access
+__device__ __forceinline__ void put_slot(float *g, int slot, float a, float b) {
+    reinterpret_cast<float2 *>(g)[slot] = make_float2(a, b);
+}
+__device__ __forceinline__ void put_slot(double *g, int slot, double a, double b) {
+    reinterpret_cast<double2 *>(g)[slot] = make_double2(a, b);
+}
+__device__ __forceinline__ float2 get_slot(const float *g, int slot) { return reinterpret_cast<const float2 *>(g)[slot]; }
+__device__ __forceinline__ double2 get_slot(const double *g, int slot) {
+    return reinterpret_cast<const double2 *>(g)[slot];
+}
+
 // the four offsets of pair record i (sink x, y, driver x, y)
 __device__ __forceinline__ void pair_offsets(const float *o, int i, float (&v)[4]) {
     const float4 q = __ldg(reinterpret_cast<const float4 *>(o) + i);
@@ -82,21 +96,15 @@ __device__ __forceinline__ void pair_vec(const State<R> &s, const R *x, const R 
     dy = y[r.x] + o[1] - yd;
 }
 
+// The loss total from each thread's FP64 partial, in a fixed order: a
+// butterfly in the warp, the warps of the block in order, then the last
+// block to finish adds the blocks' partials (lanes strided over them, a
+// butterfly), so the result depends on neither scheduling nor timing.
 template <typename R>
-__global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
-                                                         const R *__restrict__ y, double beta,
-                                                         int kind, double *loss) {
+__device__ __forceinline__ void loss_total(const State<R> &s, double acc, double beta, double *loss) {
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int np = s.pcnt[0];
-    double acc = 0.0;
-    for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
-        const int4 r = __ldg(&s.pr_a[i]);
-        R dx, dy;
-        pair_vec(s, x, y, i, r, dx, dy);
-        acc += (double)(__ldg(&s.pr_w[i]) * pair_term(dx, dy, kind));
-    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) sh[wib] = acc;
     __syncthreads();
@@ -121,38 +129,69 @@ __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, con
     }
 }
 
-// Gradient of pair record i's term with respect to the sink's position,
-// beta w dQ/dp_s.
 template <typename R>
-__device__ __forceinline__ void rec_grad(const State<R> &s, const R *x, const R *y, int i, const int4 &r,
-                                         double beta, int kind, R &gx, R &gy) {
-    R dx, dy, ux, uy;
-    pair_vec(s, x, y, i, r, dx, dy);
-    const R k = (R)beta * __ldg(&s.pr_w[i]);
+__global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
+                                                         const R *__restrict__ y, double beta,
+                                                         int kind, double *loss) {
+    const int np = s.pcnt[0];
+    double acc = 0.0;
+    for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
+        const int4 r = __ldg(&s.pr_a[i]);
+        R dx, dy;
+        pair_vec(s, x, y, i, r, dx, dy);
+        acc += (double)(__ldg(&s.pr_w[i]) * pair_term(dx, dy, kind));
+    }
+    loss_total(s, acc, beta, loss);
+}
+
+// beta w dQ/dp_s of a pair from its pin vector (dx, dy) and weight
+template <typename R>
+__device__ __forceinline__ void vec_grad(R dx, R dy, R w, double beta, int kind, R &gx, R &gy) {
+    R ux, uy;
+    const R k = (R)beta * w;
     pair_grad(dx, dy, kind, ux, uy);
     gx = k * ux;
     gy = k * uy;
 }
 
-// warp tasks: warps [0, npw) take 32 consecutive pair records (a lane per
-// pair), warps [npw, npw + pr_nbig) one larger net each
+// Gradient of pair record i's term with respect to the sink's position,
+// beta w dQ/dp_s.
 template <typename R>
-__global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
-                                                    const R *__restrict__ y, double beta, int kind) {
+__device__ __forceinline__ void rec_grad(const State<R> &s, const R *x, const R *y, int i, const int4 &r,
+                                         double beta, int kind, R &gx, R &gy) {
+    R dx, dy;
+    pair_vec(s, x, y, i, r, dx, dy);
+    vec_grad(dx, dy, __ldg(&s.pr_w[i]), beta, kind, gx, gy);
+}
+
+// warp tasks: warps [0, npw) take 32 consecutive pair records (a lane per
+// pair), warps [npw, npw + pr_nbig) one larger net each.  FWD (the fused
+// forward + backward call): each lane also adds its record's term to the
+// loss, and the grid forms the total as k_pp_fwd does.  Launched on the same
+// grid (kLossBlocks x kLossThreads), a thread visits its records in the
+// order k_pp_fwd's thread of the same index does, so the total has the
+// same bits.
+template <typename R, bool FWD>
+__global__ void __launch_bounds__(kLossThreads) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
+                                                             const R *__restrict__ y, double beta, int kind,
+                                                             double *loss) {
     const int lane = threadIdx.x & 31;
     const int np = s.pcnt[0];
     const int npw = (np + 31) >> 5;
     const int tasks = npw + *s.pr_nbig;
     const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    double acc = 0.0;
     for (int task = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); task < tasks; task += nwarps) {
         if (task < npw) {
             const int i = task * 32 + lane;
             if (i >= np) continue;
             const int4 r = __ldg(&s.pr_a[i]);
-            R gx, gy;
-            rec_grad(s, x, y, i, r, beta, kind, gx, gy);
-            s.gslot[2 * r.z] = gx;
-            s.gslot[2 * r.z + 1] = gy;
+            R dx, dy, gx, gy;
+            pair_vec(s, x, y, i, r, dx, dy);
+            const R w = __ldg(&s.pr_w[i]);
+            if constexpr (FWD) acc += (double)(w * pair_term(dx, dy, kind));
+            vec_grad(dx, dy, w, beta, kind, gx, gy);
+            put_slot(s.gslot, r.z, gx, gy);
             if (r.w < 0) continue;
             // the first pair of a net of at most kBigFanout sinks: the driver's
             // gradient, minus the sum of the net's pin gradients in pin order
@@ -165,8 +204,7 @@ __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R 
                 sx += (double)qx;
                 sy += (double)qy;
             }
-            s.gslot[2 * r.w] = (R)(-sx);
-            s.gslot[2 * r.w + 1] = (R)(-sy);
+            put_slot(s.gslot, r.w, (R)(-sx), (R)(-sy));
         } else {
             const int4 big = __ldg(&s.pr_big[task - npw]);  // (first record, pairs, driver slot)
             double sx = 0.0, sy = 0.0;
@@ -182,18 +220,17 @@ __global__ void __launch_bounds__(256) k_pp_bwd_net(Topo t, State<R> s, const R 
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane != 0) continue;
-            s.gslot[2 * big.z] = (R)(-sx);
-            s.gslot[2 * big.z + 1] = (R)(-sy);
+            put_slot(s.gslot, big.z, (R)(-sx), (R)(-sy));
         }
     }
+    if constexpr (FWD) loss_total(s, acc, beta, loss);
 }
 
 // Two roles in one launch, on disjoint cells: blocks [0, kCellBlocks) take
 // the compacted list pcells (the cells with a pin in a pair) densely, so that
 // the FP64 sums run on full warps; the other blocks write zero gradients to
-// every cell without a pin in a pair, eight cells a thread.
+// every cell without a pin in a pair, a cell a thread.
 constexpr int kCellBlocks = 148 * 4;
-constexpr int kZeroCells = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const double *gscale,
@@ -206,8 +243,9 @@ __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const d
             double ax = 0.0, ay = 0.0;
             if (!t.cell_fixed[c]) {
                 for (int k = t.cp_ptr[c]; k < t.cp_ptr[c + 1]; ++k) {
-                    ax += (double)s.gslot[2 * k];
-                    ay += (double)s.gslot[2 * k + 1];
+                    const auto v = get_slot(s.gslot, k);
+                    ax += (double)v.x;
+                    ay += (double)v.y;
                 }
                 ax *= g;
                 ay *= g;
@@ -217,17 +255,11 @@ __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const d
         }
         return;
     }
-    const int c0 = ((blockIdx.x - kCellBlocks) * blockDim.x + threadIdx.x) * kZeroCells;
-    if (c0 >= t.n_cells) return;
-    // cell_pf holds 32 bytes of padding past n_cells, and c0 is a multiple of 8
-    const uint2 f = *reinterpret_cast<const uint2 *>(s.cell_pf + c0);
-#pragma unroll
-    for (int k = 0; k < kZeroCells; ++k) {
-        const unsigned b = ((k < 4 ? f.x : f.y) >> (8 * (k & 3))) & 0xffu;
-        if (c0 + k < t.n_cells && b == 0u) {
-            gx[c0 + k] = R(0);
-            gy[c0 + k] = R(0);
-        }
+    // one cell a thread: a warp's stores cover 32 consecutive cells
+    const int c = (blockIdx.x - kCellBlocks) * blockDim.x + threadIdx.x;
+    if (c < t.n_cells && !s.cell_pf[c]) {
+        gx[c] = R(0);
+        gy[c] = R(0);
     }
 }
 
@@ -247,11 +279,32 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
     State<R> &s = state<R>(g);
     {
         LaunchScope ls(g, KID_PP_BWD_NET);
-        k_pp_bwd_net<R><<<kLossBlocks, 256, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind);
+        k_pp_bwd_net<R, false><<<kLossBlocks, kLossThreads, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind,
+                                                                             nullptr);
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
-        const int zero_blocks = div_up(div_up(std::max(t.n_cells, 1), kZeroCells), 256);
+        const int zero_blocks = div_up(std::max(t.n_cells, 1), 256);
+        k_pp_bwd_cell<R><<<kCellBlocks + zero_blocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
+    }
+    TDP_LAUNCH_CHECK();
+    return TDP_OK;
+}
+
+// attraction_loss_fwd_bwd: the per-pair pass computes the loss terms with
+// the pin gradients (k_pp_bwd_net<R, true>), then the cell pass
+template <typename R>
+static tdp_status loss_fwd_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, const double *gs,
+                                    double *loss, R *gx, R *gy) {
+    Topo &t = g->topo;
+    State<R> &s = state<R>(g);
+    {
+        LaunchScope ls(g, KID_PP_FWD_BWD);
+        k_pp_bwd_net<R, true><<<kLossBlocks, kLossThreads, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind, loss);
+    }
+    {
+        LaunchScope ls(g, KID_PP_BWD_CELL);
+        const int zero_blocks = div_up(std::max(t.n_cells, 1), 256);
         k_pp_bwd_cell<R><<<kCellBlocks + zero_blocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
     }
     TDP_LAUNCH_CHECK();
@@ -378,6 +431,20 @@ extern "C" tdp_status attraction_loss_bwd(tdp_graph *g, const void *x_dev, const
                                       grad_scale_dev, (float *)gx_dev, (float *)gy_dev)
                : loss_bwd_impl<double>(g, (const double *)x_dev, (const double *)y_dev, beta,
                                        grad_scale_dev, (double *)gx_dev, (double *)gy_dev);
+}
+
+extern "C" tdp_status attraction_loss_fwd_bwd(tdp_graph *g, const void *x_dev, const void *y_dev, double beta,
+                                              const double *grad_scale_dev, double *loss_dev, void *gx_dev,
+                                              void *gy_dev) {
+    if (!g || !x_dev || !y_dev || !loss_dev || !gx_dev || !gy_dev || !std::isfinite(beta)) {
+        set_error("attraction_loss_fwd_bwd: NULL argument or non-finite beta");
+        return TDP_ERR_INVALID;
+    }
+    return g->prec == TDP_FP32
+               ? loss_fwd_bwd_impl<float>(g, (const float *)x_dev, (const float *)y_dev, beta, grad_scale_dev,
+                                          loss_dev, (float *)gx_dev, (float *)gy_dev)
+               : loss_fwd_bwd_impl<double>(g, (const double *)x_dev, (const double *)y_dev, beta, grad_scale_dev,
+                                           loss_dev, (double *)gx_dev, (double *)gy_dev);
 }
 
 extern "C" tdp_status attraction_set_loss_kind(tdp_graph *g, tdp_loss_kind kind) {

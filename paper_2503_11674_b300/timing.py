@@ -256,6 +256,21 @@ class TimingGraph:
     def net_weights_reset(self):
         _abi.check("net_weights_reset", self.lib.net_weights_reset(self.handle))
 
+    def attraction_loss_fwd_bwd(self, x: torch.Tensor, y: torch.Tensor, beta: float,
+                                grad_scale: torch.Tensor | None = None, out=None, gx=None, gy=None):
+        """attraction_loss_fwd and attraction_loss_bwd in one call (two launches);
+        returns (loss device scalar, gx, gy)."""
+        x, y = self._pos(x), self._pos(y)
+        out = torch.empty((), dtype=torch.float64, device=self.device) if out is None else out
+        gx = torch.empty_like(x) if gx is None else gx
+        gy = torch.empty_like(y) if gy is None else gy
+        if grad_scale is not None:
+            grad_scale = grad_scale.detach().to(device=self.device, dtype=torch.float64).contiguous()
+        _abi.check("attraction_loss_fwd_bwd",
+                   self.lib.attraction_loss_fwd_bwd(self.handle, _ptr(x), _ptr(y), float(beta), _ptr(grad_scale),
+                                                    _ptr(out), _ptr(gx), _ptr(gy)))
+        return out, gx, gy
+
     # ---------------------------------------------------- instrumentation --
     def tdp_get_launch_count(self) -> int:
         n = C.c_int64()

@@ -116,6 +116,10 @@ def test_loss_and_gradient(run):
     g = np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]).astype(np.float64)
     gr = np.concatenate([gx_r, gy_r])
     assert np.linalg.norm(g - gr) / np.linalg.norm(gr) <= 1e-5
+    # the fused call, with the high-fanout nets' warps: the same bits
+    l2, gx2, gy2 = G.attraction_loss_fwd_bwd(x, y, beta)
+    assert l2.item() == G.attraction_loss_fwd(x, y, beta).item()
+    assert torch.equal(gx2, gx) and torch.equal(gy2, gy)
 
 
 def test_net_weights_at_full_size(run):

@@ -246,6 +246,29 @@ def test_loss_parity(cfg, seed, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["quadratic", "hpwl", "euclid"])
+def test_fused_loss_call_matches_separate_calls(kind, prec):
+    """attraction_loss_fwd_bwd gives the loss and gradient of
+    attraction_loss_fwd + attraction_loss_bwd bit for bit, with and without
+    a gradient scale, after a pair update from extracted paths."""
+    nl = netgen.generate("diff", 3)
+    T = oracle.clock_period(nl, 0.9)
+    G = _graph(nl, prec)
+    x, y = _pos(nl, G.dtype)
+    G.sta_propagate(x, y, T)
+    G.extract_critical_paths(-1, 8, False)
+    assert G.attraction_update_pairs(10.0, 0.2) > 0
+    G.attraction_set_loss_kind(kind)
+    beta = 2.5e-5
+    for scale in (None, torch.tensor(0.75, dtype=torch.float64, device="cuda")):
+        loss = G.attraction_loss_fwd(x, y, beta).item()
+        gx, gy = (t.clone() for t in G.attraction_loss_bwd(x, y, beta, grad_scale=scale))
+        l2, gx2, gy2 = G.attraction_loss_fwd_bwd(x, y, beta, grad_scale=scale)
+        assert l2.item() == loss
+        assert torch.equal(gx2, gx) and torch.equal(gy2, gy)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("kind", ["hpwl", "euclid", "quadratic"])
 def test_loss_kind_parity(kind, prec):
     """HPWL and linear Euclidean pair distances (the ablation's losses) against
