@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 455400448, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
-        "bwd_sweep": {"bytes": 127428352, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
-        "pair_walk": {"bytes": 22964736, "sources": PAIR_SOURCES, "sha256": "7715ca6d89d8aa0b9a4c9dc7f83751e955eb98c0a18b3056372ef12a6195620e"},
+        "fwd_sweep": {"bytes": 456165376, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
+        "bwd_sweep": {"bytes": 127699712, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
+        "pair_walk": {"bytes": 22996224, "sources": PAIR_SOURCES, "sha256": "7fe9d02640caca45dde9ed7a8f5b432754c5c0e8b86626205d295a5856759ad3"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2455318528, "sources": SWEEP_SOURCES, "sha256": "fb77ba18a85401bf4b9d454d0d23a79262b53eae988169a96afc855f96338e20"},
+        "fwd_sweep": {"bytes": 2453452032, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
     },
 }
 
