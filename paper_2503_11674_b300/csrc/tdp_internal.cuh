@@ -223,10 +223,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The barrier in two halves: grid_arrive (every thread; this block's writes
 // become visible before its arrival is counted) and grid_wait (every
 // thread); work that needs no other block's results of this step can run in
-// between.
+// between.  One thread of the block arrives and polls: lane 0 of its last
+// warp (blockDim.x a multiple of 32).  The sweeps give their work to the
+// first warps, so this thread's poll loads do not queue behind the loads
+// the working warps issue between arrival and wait (measured: the forward
+// sweep at 1.2M cells took 0.469 ms polling from thread 0, 0.426 ms from
+// the last warp).
+__device__ __forceinline__ bool grid_thread() { return threadIdx.x == blockDim.x - 32u; }
+
 __device__ __forceinline__ void grid_arrive(const GridSync &gs) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (grid_thread()) {
         // release at GPU scope: this block's writes (ordered before by the
         // block barrier) become visible before the arrival is counted
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gs.count) : "memory");
@@ -235,7 +242,7 @@ __device__ __forceinline__ void grid_arrive(const GridSync &gs) {
 
 __device__ __forceinline__ bool grid_wait(const GridSync &gs, unsigned target) {
     __shared__ int ok;
-    if (threadIdx.x == 0) {
+    if (grid_thread()) {
         int good = 1;
         unsigned long long t0 = 0;
         for (unsigned it = 1; ld_acquire(gs.count) < target; ++it) {

@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep_inc(Topo t, State<
         if (lane == 0 && dc > 0) atomicAdd(&blk_chg, (int)dc);
         __syncthreads();
         if (threadIdx.x == 0) {
-            // before this thread's release arrival below
+            // ordered before the block's release arrival below by its block barrier
             if (blk_hi > 0) atomicMax(&inc.lohi[1], blk_hi);
             if (blk_chg > 0) atomicAdd(&inc.lvchg[l], blk_chg);
             blk_hi = blk_chg = 0;
