@@ -276,12 +276,12 @@ __device__ __forceinline__ bool grid_sync(const GridSync &gs, unsigned target) {
 }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
+inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
                                Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -376,6 +376,155 @@ __device__ __forceinline__ void list_put(BEnt<double> *dst, const LEnt<double> (
     for (int j = 0; j < L; ++j) dst[j] = BEnt<double>{li[j].d, lreg_pin<double>(li[j])};
 }
 
+// Lists moved by a whole warp.  With per-thread vector I/O (list_load,
+// list_put) every load or store instruction of a warp touches 32 lists, one
+// 16-byte piece of each: 32 L2 requests for 512 bytes, each sector fetched
+// twice.  Here each instruction moves 512 / B whole lists of B bytes, the
+// pieces of one list on consecutive lanes (B >= 128: four requests of a full
+// 128-byte line), and the pieces pass between the lanes through a per-warp
+// staging area in shared memory (32 * C pieces).  The lists and their bits
+// are those of list_load / list_put.
+template <typename R, int L>
+struct WarpList {
+    static constexpr int G = list_group(L);
+    static constexpr int B = G * (int)sizeof(BEnt<R>);  // bytes of a list block
+    static constexpr int C = B / 16;                     // 16-byte pieces of a list
+    static constexpr int LPI = 32 / C;                   // lists per instruction
+    static constexpr int SPREAD = C >= 8 ? 1 : 8 / C;
+    static_assert(B % 16 == 0 && C >= 2 && C <= 32, "list block of 2 to 32 pieces");
+    // staging slot of piece q of lane i's list: the pieces of a list are
+    // rotated within its C slots so that the eight lanes of a quarter warp
+    // reading piece q of their own lists meet eight different 16-byte bank
+    // groups (the writes of an instruction cover consecutive slots)
+    static __device__ __forceinline__ int slot(int i, int q) { return i * C + (q + i / SPREAD) % C; }
+};
+
+// the 16-byte piece q of a list in registers, as list_put stores it
+template <int L>
+__device__ __forceinline__ float4 list_piece(const uint64_t (&li)[L], int q) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < list_group(L) / 2; ++r) {
+        if (r == q) {
+            const uint64_t x = 2 * r < L ? li[2 * r] : LReg<float>::none();
+            const uint64_t y = 2 * r + 1 < L ? li[2 * r + 1] : LReg<float>::none();
+            v = make_float4(LReg<float>::cost(x), __int_as_float(lreg_pin<float>(x)), LReg<float>::cost(y),
+                            __int_as_float(lreg_pin<float>(y)));
+        }
+    }
+    return v;
+}
+template <int L>
+__device__ __forceinline__ float4 list_piece(const LEnt<double> (&li)[L], int q) {
+    double d = r_inf<double>();
+    int32_t pin = -1;
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+        if (r == q) {
+            d = li[r].d;
+            pin = lreg_pin<double>(li[r]);
+        }
+    }
+    const double2 v = make_double2(d, __longlong_as_double((long long)(uint32_t)pin));
+    return *reinterpret_cast<const float4 *>(&v);
+}
+// piece q of a list into registers, as list_load reads it
+template <int L>
+__device__ __forceinline__ void list_unpiece(float4 v, int q, uint64_t (&li)[L]) {
+#pragma unroll
+    for (int r = 0; r < list_group(L) / 2; ++r) {
+        if (r == q) {
+            if (2 * r < L) li[2 * r] = lreg_of<float>(v.x, __float_as_int(v.y));
+            if (2 * r + 1 < L) li[2 * r + 1] = lreg_of<float>(v.z, __float_as_int(v.w));
+        }
+    }
+}
+template <int L>
+__device__ __forceinline__ void list_unpiece(float4 v, int q, LEnt<double> (&li)[L]) {
+    const double2 w = *reinterpret_cast<const double2 *>(&v);
+#pragma unroll
+    for (int r = 0; r < L; ++r)
+        if (r == q) li[r] = lreg_of<double>(w.x, (int32_t)(__double_as_longlong(w.y) & 0xffffffffll));
+}
+
+// Every lane of the warp calls these.  src / dst: the net whose list the
+// lane reads / writes (< 0: none; a lane without a list to read gets
+// sentinels).  The staging area is free again when they return.  The loads
+// go from L2 to the staging area as asynchronous copies (cp.async.cg: read
+// from L2 like ld.global.cg, so COH makes no difference here, and no
+// registers held while they are in flight); the staging area is addressed in
+// the shared window (32-bit addresses).
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// the lane index read afresh at each call, so that the compiler recomputes
+// the staging offsets (a few integer operations) instead of holding them in
+// registers across the whole sweep
+__device__ __forceinline__ int lane_now() {
+    int l;
+    asm volatile("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+__device__ __forceinline__ float4 lds16(unsigned a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts16(unsigned a, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+template <typename R, int L, bool COH>
+__device__ __forceinline__ void warp_list_load(const BEnt<R> *blist, int src, float4 *stage,
+                                               typename LReg<R>::E (&li)[L]) {
+    using W = WarpList<R, L>;
+    const int lane = lane_now();
+    const unsigned st0 = smem_u32(stage);
+#pragma unroll
+    for (int t = 0; t < W::C; ++t) {
+        const int i = t * W::LPI + lane / W::C, q = lane % W::C;
+        const int n = __shfl_sync(0xffffffffu, src, i);
+        if (n >= 0) {
+            const float4 *g = reinterpret_cast<const float4 *>(blist + (size_t)n * W::G) + q;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(st0 + 16u * (unsigned)W::slot(i, q)),
+                         "l"(g)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    // every lane unpacks its slots; a lane without a list then takes sentinels
+    // (a select per entry, not a branch around the unpacking)
+#pragma unroll
+    for (int q = 0; q < W::C; ++q) list_unpiece<L>(lds16(st0 + 16u * (unsigned)W::slot(lane, q)), q, li);
+    const bool has = src >= 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) li[j] = has ? li[j] : LReg<R>::none();
+    __syncwarp();
+}
+template <typename R, int L>
+__device__ __forceinline__ void warp_list_put(BEnt<R> *blist, int dst, float4 *stage,
+                                              const typename LReg<R>::E (&li)[L]) {
+    using W = WarpList<R, L>;
+    const int lane = lane_now();
+    const unsigned st0 = smem_u32(stage);
+#pragma unroll
+    for (int q = 0; q < W::C; ++q) sts16(st0 + 16u * (unsigned)W::slot(lane, q), list_piece<L>(li, q));
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < W::C; ++t) {
+        const int i = t * W::LPI + lane / W::C, q = lane % W::C;
+        const int n = __shfl_sync(0xffffffffu, dst, i);
+        const float4 v = lds16(st0 + 16u * (unsigned)W::slot(i, q));
+        if (n >= 0) reinterpret_cast<float4 *>(blist + (size_t)n * W::G)[q] = v;
+    }
+    __syncwarp();
+}
+
+// bytes of the staging area a block of `threads` threads needs for lists of L
+template <typename R>
+__host__ __device__ constexpr size_t warp_list_smem(int L, int threads) {
+    return L == 0 ? 0 : (size_t)threads * (size_t)list_group(L) * sizeof(BEnt<R>);
+}
+
 // whether the stored list at dst holds, bit for bit, what list_put(dst, li)
 // would write
 template <int L>
@@ -480,77 +629,93 @@ __device__ __forceinline__ void cell_vals(const State<R> &s, CellPre<R> &c) {
 // input, chain length or list differs, bit for bit, from what was stored
 // before (a cell of more than kPre inputs always counts as changed).
 
-template <typename R, int L, bool COH, bool CMP = false>
-__device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellPre<R> &c) {
+// WARP: every lane of the warp calls it (a lane without a cell passes
+// k < 0) and the lists move as whole lists (warp_list_load / _put, staging
+// area `stage`); else the lane alone, with per-thread list I/O.
+template <typename R, int L, bool COH, bool CMP = false, bool WARP = false>
+__device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellPre<R> &c,
+                                         float4 *stage = nullptr) {
+    static_assert(!(CMP && WARP), "the comparing form runs lane by lane");
     using AC = Acc<R>;
     using A = typename AC::T;
     using LR = LReg<R>;
-    if (c.k < 0) return false;
+    bool act = c.k >= 0;
+    if constexpr (!WARP) {
+        if (!act) return false;
+    }
     const int nin = c.b - c.a;
-    if (nin > kPre) {
+    if (act && nin > kPre) {
         fwd_cell_wide<R, L, COH>(t, s, c.k, c.a, c.b);
-        return true;
+        if constexpr (!WARP) return true;
+        act = false;  // its list is built; the lane only joins the warp's list moves
     }
     // every load first, then the arithmetic, then the stores
-    const R dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
-    A av[kPre];
-    R tv[kPre];
-    int pl[kPre];
-#pragma unroll
-    for (int u = 0; u < kPre; ++u) {
-        if (u < nin) {
-            tv[u] = c.vals ? c.tv[u] : ldg(&s.tnet[c.ip[u]]);
-            if ((c.old >> u) & 1u) {
-                av[u] = c.ad[u];
-                pl[u] = c.pl[u];
-            } else {
-                av[u] = ldd<COH>(&s.arr[c.dv[u]]);
-                pl[u] = ldd<COH>(&s.plen[c.in[u]]);
-            }
-        }
-    }
-    // inputs ascending by pin: strict > keeps the lowest pin on ties (and the
-    // first input if arrivals are not comparable)
     int bi = -1, bn = -1, bl = 0, bu = 0;
     A best = AC::ninf();
+    A av[kPre];
+    bool chg = false;
+    if (act) {
+        const R dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
+        R tv[kPre];
+        int pl[kPre];
 #pragma unroll
-    for (int u = 0; u < kPre; ++u) {
-        if (u < nin) {
-            av[u] = AC::add(av[u], tv[u]);
-            if (bi < 0 || AC::gt(av[u], best)) {
-                best = av[u];
-                bi = c.ip[u];
-                bn = c.in[u];
-                bl = pl[u];
-                bu = u;
+        for (int u = 0; u < kPre; ++u) {
+            if (u < nin) {
+                tv[u] = c.vals ? c.tv[u] : ldg(&s.tnet[c.ip[u]]);
+                if ((c.old >> u) & 1u) {
+                    av[u] = c.ad[u];
+                    pl[u] = c.pl[u];
+                } else {
+                    av[u] = ldd<COH>(&s.arr[c.dv[u]]);
+                    pl[u] = ldd<COH>(&s.plen[c.in[u]]);
+                }
             }
         }
+        // inputs ascending by pin: strict > keeps the lowest pin on ties (and
+        // the first input if arrivals are not comparable)
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (u < nin) {
+                av[u] = AC::add(av[u], tv[u]);
+                if (bi < 0 || AC::gt(av[u], best)) {
+                    best = av[u];
+                    bi = c.ip[u];
+                    bn = c.in[u];
+                    bl = pl[u];
+                    bu = u;
+                }
+            }
+        }
+        if constexpr (CMP) {
+            const int2 op = ldcg(&s.pred[c.e]);
+            chg = !same_bits(ldcg(&s.arr[c.o]), AC::add(best, dcell)) || op.x != bi || op.y != bn ||
+                  ldcg(&s.plen[c.e]) != bl + 2;
+        }
+        s.arr[c.o] = AC::add(best, dcell);
+        s.pred[c.e] = make_int2(bi, bn);
+        s.plen[c.e] = bl + 2;
     }
-    bool chg = false;
-    if constexpr (CMP) {
-        const int2 op = ldcg(&s.pred[c.e]);
-        chg = !same_bits(ldcg(&s.arr[c.o]), AC::add(best, dcell)) || op.x != bi || op.y != bn ||
-              ldcg(&s.plen[c.e]) != bl + 2;
-    }
-    s.arr[c.o] = AC::add(best, dcell);
-    s.pred[c.e] = make_int2(bi, bn);
-    s.plen[c.e] = bl + 2;
     if constexpr (L > 0) {
         constexpr int G = list_group(L);
         typename LR::E li[L];
-        if (nin > 0 && ((c.fl >> (8 * bu)) & kInComb)) {
+        const bool from = act && nin > 0 && ((c.fl >> (8 * bu)) & kInComb);
+        if constexpr (WARP) {
+            warp_list_load<R, L, COH>(s.blist, from ? bn : -1, stage, li);
+        } else if (from) {
             list_load<L, COH>(s.blist + (size_t)bn * G, li);
         } else {
 #pragma unroll
             for (int j = 0; j < L; ++j) li[j] = LR::none();
         }
-        // every thread inserts kPre entries (absent ones as no-op sentinels),
-        // so that the threads of a warp do not diverge
+        if (act) {
+            // every thread inserts kPre entries (absent ones as no-op
+            // sentinels), so that the threads of a warp do not diverge
 #pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            const bool own = u < nin && u != bu;
-            const uint32_t key = ((c.ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)c.ip[u];
-            list_insert<R, L>(li, own ? LR::make(AC::diff(best, av[u]), key) : LR::none());
+            for (int u = 0; u < kPre; ++u) {
+                const bool own = u < nin && u != bu;
+                const uint32_t key = ((c.ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)c.ip[u];
+                list_insert<R, L>(li, own ? LR::make(AC::diff(best, av[u]), key) : LR::none());
+            }
         }
         if constexpr (CMP) {
             int m = 0;
@@ -558,11 +723,14 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
             for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
             chg = chg || ldcg(&s.bcnt[c.e]) != m || !list_same<L>(s.blist + (size_t)c.e * G, li);
         }
-        list_put<L>(s.blist + (size_t)c.e * G, li);
-        int m = 0;
+        if constexpr (WARP) warp_list_put<R, L>(s.blist, act ? c.e : -1, stage, li);
+        else list_put<L>(s.blist + (size_t)c.e * G, li);
+        if (act) {
+            int m = 0;
 #pragma unroll
-        for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
-        s.bcnt[c.e] = m;
+            for (int j = 0; j < L; ++j) m += LR::key(li[j]) == kNoneKey ? 0 : 1;
+            s.bcnt[c.e] = m;
+        }
     }
     return chg;
 }
@@ -618,6 +786,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s
         const int k = ldg(&t.lvl_ptr[l - 1]) + chunk * 32 + lane;
         return k < ldg(&t.lvl_ptr[l]) ? k : -1;
     };
+    // staging area of this warp's list moves (warp_list_smem bytes a block)
+    extern __shared__ float4 lstage[];
+    float4 *stage = lstage + (size_t)(threadIdx.x >> 5) * 32 * (L > 0 ? WarpList<R, L>::C : 0);
     const int l0 = from ? max(ldcg(from), 1) : 1;
     if (l0 > t.depth) return;
     CellPre<R> cur, nxt;
@@ -625,12 +796,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s
     cell_topo(t, cell_of(l0 + 1, w0), nxt);
     for (int l = l0; l <= t.depth; ++l) {
         const int nch = div_up_dev(ldg(&t.lvl_ptr[l]) - ldg(&t.lvl_ptr[l - 1]), 32);
-        if (w0 < nch) {
-            fwd_cell<R, L, true>(t, s, cur);
+        if (w0 < nch) {  // the same in every lane of the warp
+            fwd_cell<R, L, true, false, true>(t, s, cur, stage);
             for (int ch = w0 + wstride; ch < nch; ch += wstride) {
                 CellPre<R> c;
                 cell_topo(t, cell_of(l, ch), c);
-                fwd_cell<R, L, true>(t, s, c);
+                fwd_cell<R, L, true, false, true>(t, s, c, stage);
             }
         }
         if (l == t.depth) break;
@@ -1291,15 +1462,18 @@ static tdp_status capture(tdp_graph *g, cudaGraphExec_t *exec, int *n_kernels, b
     return TDP_OK;
 }
 
-// Blocks of a cooperative launch of `kernel` that are resident at once (at
-// most kCoopMaxBlocks), cached per kernel; 0 if none.
+// Blocks of a cooperative launch of `kernel` (smem bytes of dynamic shared
+// memory a block) that are resident at once (at most kCoopMaxBlocks), cached
+// per kernel; 0 if none.
 template <typename K>
-static int coop_grid(tdp_graph *g, K kernel, int threads) {
+static int coop_grid(tdp_graph *g, K kernel, int threads, size_t smem = 0) {
     const void *key = reinterpret_cast<const void *>(kernel);
     for (auto &pr : g->coop_grid)
         if (pr.first == key) return pr.second;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess) {
+    if ((smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                         cudaSuccess) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         nb = 0;
     }
@@ -1322,7 +1496,7 @@ static tdp_status launch_sweep(tdp_graph *g, void (*kernel)(Topo, State<R>, Grid
     gs.timeout_ns = kSyncTimeoutNs;
     LaunchScope ls(g, id, 1, st);
     if (reset_count) TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), st));
-    TDP_CUDA(launch_coop(kernel, grid, threads, st, g->topo, s, gs));
+    TDP_CUDA(launch_coop(kernel, grid, threads, 0, st, g->topo, s, gs));
     return TDP_OK;
 }
 
@@ -1347,7 +1521,8 @@ static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev) 
     gs.timeout_ns = kSyncTimeoutNs;
     LaunchScope ls(g, KID_FWD_SWEEP, 1, g->stream);
     TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
-    TDP_CUDA(launch_coop(fwd_kernel<R>(g->list_L), grid, kFwdThreads, g->stream, g->topo, s, gs, from_dev));
+    TDP_CUDA(launch_coop(fwd_kernel<R>(g->list_L), grid, kFwdThreads, warp_list_smem<R>(g->list_L, kFwdThreads),
+                         g->stream, g->topo, s, gs, from_dev));
     return TDP_OK;
 }
 
@@ -1360,7 +1535,8 @@ tdp_status forward_lists(tdp_graph *g) {
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * kMaxK));
     if (g->single_launch) {
         if (g->topo.depth == 0) return TDP_OK;
-        const int grid = coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads);
+        const int grid =
+            coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads, warp_list_smem<R>(g->list_L, kFwdThreads));
         if (grid > 0) return launch_fwd_sweep<R>(g, grid, nullptr);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
@@ -1523,7 +1699,9 @@ static tdp_status propagate_incremental_impl(tdp_graph *g, const R *x, const R *
         default: kernel = k_fwd_sweep_inc<R, 31>; break;
     }
     const int grid = g->single_launch ? coop_grid(g, kernel, kFwdThreads) : 0;
-    const int grid_full = g->single_launch ? coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads) : 0;
+    const int grid_full = g->single_launch ? coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads,
+                                                       warp_list_smem<R>(g->list_L, kFwdThreads))
+                                           : 0;
     if (!g->inc_valid || !g->propagated || grid == 0 || grid_full == 0 || g->lists_valid_L != g->list_L ||
         t.depth == 0)
         return propagate_impl<R>(g, x, y, T);
@@ -1559,7 +1737,7 @@ static tdp_status propagate_incremental_impl(tdp_graph *g, const R *x, const R *
         gs.timeout_ns = kSyncTimeoutNs;
         LaunchScope ls(g, KID_FWD_INC, 1, g->stream);
         TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
-        TDP_CUDA(launch_coop(kernel, grid, kFwdThreads, g->stream, t, s, gs, inc));
+        TDP_CUDA(launch_coop(kernel, grid, kFwdThreads, 0, g->stream, t, s, gs, inc));
     }
     // the levels after saturation, if the changes saturated (else it returns at once)
     TDP_TRY(launch_fwd_sweep<R>(g, grid_full, inc.lohi + 2));
@@ -1823,7 +2001,7 @@ extern "C" tdp_status tdp_selftest_grid_wait(double timeout_ms, int32_t *gave_up
     gs.timeout_ns = (unsigned long long)(timeout_ms * 1e6);
     unsigned h[2] = {0u, 0u};
     cudaError_t e = cudaMemset(w, 0, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = launch_coop(k_wait_selftest, 2, 32, (cudaStream_t)0, gs);
+    if (e == cudaSuccess) e = launch_coop(k_wait_selftest, 2, 32, 0, (cudaStream_t)0, gs);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost);
     cudaFree(w);
