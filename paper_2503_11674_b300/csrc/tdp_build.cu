@@ -78,14 +78,12 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
     // pin pairs
     TDP_TRY(dalloc(g, &s.sumq, t.n_pins));
     TDP_TRY(dalloc(g, &s.maxq, t.n_pins));
-    TDP_TRY(dalloc(g, &s.touch, t.n_pins));
     TDP_TRY(dalloc(g, &s.in_p, t.n_pins));
     TDP_TRY(dalloc(g, &s.w, t.n_pins));
     TDP_TRY(dalloc(g, &s.n_pairs, 1));
     TDP_CUDA(cudaMemset(s.sumq, 0, sizeof(long long) * t.n_pins));
     std::vector<long long> mq(t.n_pins, INT64_MIN);
     TDP_CUDA(cudaMemcpy(s.maxq, mq.data(), sizeof(long long) * t.n_pins, cudaMemcpyHostToDevice));
-    TDP_CUDA(cudaMemset(s.touch, 0, t.n_pins));
     TDP_CUDA(cudaMemset(s.in_p, 0, t.n_pins));
     TDP_CUDA(cudaMemset(s.w, 0, sizeof(R) * t.n_pins));
     TDP_CUDA(cudaMemset(s.n_pairs, 0, sizeof(long long)));
@@ -642,6 +640,8 @@ extern "C" tdp_status sta_build(const tdp_netlist_desc *netlist, tdp_precision p
         g->overlap_bwd = !(ser && ser[0] == '1');
         const char *share = getenv("TDP_BWD_SHARE");
         if (share) g->bwd_share = std::min(16, std::max(1, atoi(share)));
+        const char *bsms = getenv("TDP_BWD_SMS");
+        if (bsms) g->bwd_sms = atoi(bsms);
     }
     if (st == TDP_OK)
         st = precision == TDP_FP32 ? build_state<float>(g, netlist) : build_state<double>(g, netlist);

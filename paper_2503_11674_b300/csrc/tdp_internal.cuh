@@ -417,7 +417,7 @@ struct State {
     long long *n_paths = nullptr; // device total
     // pin pairs
     long long *sumq = nullptr, *maxq = nullptr;  // [n_pins] fixed-point slack/WNS
-    uint8_t *touch = nullptr, *in_p = nullptr;   // [n_pins]
+    uint8_t *in_p = nullptr;   // [n_pins]
     R *w = nullptr;                               // [n_pins]
     long long *n_pairs = nullptr;
     // pairs, compacted for the loss: the sink pins of P, and the cells with
@@ -483,6 +483,12 @@ struct tdp_graph {
     // the overlapped backward sweep's share of its resident grid, in 16ths
     // (TDP_BWD_SHARE at sta_build, 1 to 16)
     int bwd_share = 9;
+    // a full propagation starts the backward sweep right after net RC on
+    // bwd_sms blocks (one an SM) and runs the forward sweep on the other SMs
+    // (0: chosen by bwd_split at the first propagation; TDP_BWD_SMS at
+    // sta_build sets it, a negative value there: the backward sweep after
+    // the forward sweep, beside the rest, as incremental propagation runs it)
+    int bwd_sms = 0;
     tdp::Topo topo;
     tdp::Levels lv;
     tdp::State<float> s32;
@@ -566,8 +572,10 @@ inline State<double> &state<double>(tdp_graph *g) { return g->s64; }
 
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T);
+// the forward sweep building the lists; leave_sms: SMs to leave to a
+// backward sweep that runs at the same time (single launch)
 template <typename R>
-tdp_status forward_lists(tdp_graph *g);
+tdp_status forward_lists(tdp_graph *g, int leave_sms = 0);
 template <typename R>
 tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg);
 template <typename R>

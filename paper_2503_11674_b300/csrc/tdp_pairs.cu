@@ -6,7 +6,8 @@
 // as 64-bit fixed point (2^-24), so the integer atomics are exact and the
 // result does not depend on the order of the paths.
 //
-// k_pair_finish applies the rule to every touched sink.  Traversing the paths
+// k_pair_finish applies the rule to every touched sink (one whose maximum a
+// walk raised above its initial LLONG_MIN).  Traversing the paths
 // worst first, the first path through a new pair sets w0 and every later one
 // adds w1 * q; the first one is the path with the largest q (most negative
 // slack), so
@@ -68,7 +69,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
             }
             atomicAdd((unsigned long long *)&s.sumq[ep], (unsigned long long)sum);
             atomicMax(&s.maxq[ep], mx);
-            s.touch[ep] = 1;
         }
         int e = on ? t.pin_net[ep] : 0;
         int j = ns - 1;  // sides[] holds the deepest sidetrack first
@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
                 }
                 atomicAdd((unsigned long long *)&s.sumq[pin], (unsigned long long)last_sum);
                 atomicMax(&s.maxq[pin], last_max);
-                s.touch[pin] = 1;
             }
         }
         __syncwarp();
@@ -135,7 +134,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
 template <typename R>
 __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pins || !s.touch[p]) return;
+    // a sink is touched when a walk raised its maximum (every q is finite)
+    if (p >= n_pins || s.maxq[p] == LLONG_MIN) return;
     const double sq = (double)s.sumq[p] / kQScale;
     if (s.in_p[p]) {
         s.w[p] = (R)((double)s.w[p] + w1 * sq);
@@ -153,7 +153,6 @@ __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double 
     }
     s.sumq[p] = 0;
     s.maxq[p] = LLONG_MIN;
-    s.touch[p] = 0;
 }
 
 // ------------------------------------------------------- compaction ---

@@ -339,7 +339,6 @@ __global__ void k_rt_pair_walk(Topo t, State<R> s, RtNodes<R> acc, const int32_t
         if (!is_sink) return;
         atomicAdd((unsigned long long *)&s.sumq[pin], (unsigned long long)Q);
         atomicMax(&s.maxq[pin], Q);
-        s.touch[pin] = 1;
     });
 }
 

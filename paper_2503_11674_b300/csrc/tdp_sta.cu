@@ -1530,14 +1530,14 @@ static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev) 
 // cooperative launch, or one graph replay of the level launches.  Run again,
 // it writes the same arrival times.
 template <typename R>
-tdp_status forward_lists(tdp_graph *g) {
+tdp_status forward_lists(tdp_graph *g, int leave_sms) {
     State<R> &s = state<R>(g);
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * kMaxK));
     if (g->single_launch) {
         if (g->topo.depth == 0) return TDP_OK;
         const int grid =
             coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads, warp_list_smem<R>(g->list_L, kFwdThreads));
-        if (grid > 0) return launch_fwd_sweep<R>(g, grid, nullptr);
+        if (grid > 0) return launch_fwd_sweep<R>(g, std::max(1, grid - leave_sms), nullptr);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
@@ -1562,13 +1562,15 @@ __global__ void k_bwd_reset(unsigned long long *reqkey, int n, unsigned *count) 
 
 // Backward sweep: one cooperative launch, or one graph replay.  Nothing
 // later in a timing iteration reads what it writes, so with the overlap on
-// it runs on the graph's second stream from the end of the forward sweep
-// (ev_bwd_go), beside the endpoints, extraction, the pair update and the
-// loss, on kBwdOverlapNum / 16 of its resident grid; serialised, on the
-// graph's stream after the endpoints.  sta_join and every call that needs
-// its results wait for it.
+// it runs on the graph's second stream from ev_bwd_go: in a full
+// propagation, from the end of net RC on `sms` blocks (one an SM) beside the
+// forward sweep on the other SMs, and on beside the endpoints, extraction,
+// the pair update and the loss; else from the end of the forward sweep on
+// bwd_share / 16 of its resident grid.  Serialised, on the graph's stream
+// after the endpoints.  sta_join and every call that needs its results wait
+// for it.
 template <typename R>
-static tdp_status backward(tdp_graph *g) {
+static tdp_status backward(tdp_graph *g, int sms = 0) {
     cudaStream_t st = g->stream;
     if (g->overlap_bwd) {
         TDP_CUDA(cudaStreamWaitEvent(g->side, g->ev_bwd_go, 0));
@@ -1581,7 +1583,7 @@ static tdp_status backward(tdp_graph *g) {
         // blocks; measured at 1.2M cells, a step took 1.189, 1.157, 1.111,
         // 1.135, 1.171 and 1.270 ms for 7/16 to 12/16)
         int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
-        if (grid > 0 && g->overlap_bwd) grid = std::max(1, grid * g->bwd_share / 16);
+        if (grid > 0 && g->overlap_bwd) grid = sms > 0 ? std::min(grid, sms) : std::max(1, grid * g->bwd_share / 16);
         if (grid > 0) {
             State<R> &s = state<R>(g);
             ++g->n_launch;
@@ -1608,19 +1610,46 @@ static tdp_status backward(tdp_graph *g) {
 // After the forward sweep: the endpoints and WNS / TNS, and the backward
 // sweep (which reads no arrival and starts at once on the second stream).
 template <typename R>
-static tdp_status finish_sweeps(tdp_graph *g) {
-    if (g->overlap_bwd) TDP_CUDA(cudaEventRecord(g->ev_bwd_go, g->stream));
+static tdp_status finish_sweeps(tdp_graph *g, bool bwd = true) {
+    if (g->overlap_bwd && bwd) TDP_CUDA(cudaEventRecord(g->ev_bwd_go, g->stream));
     {
         LaunchScope ls(g, KID_EP_WNS);
         const int chunks = div_up(std::max(g->topo.n_ep, 1), kRedChunk);
         k_ep_wns<R><<<div_up(chunks, kRedThreads / 32), kRedThreads, 0, g->stream>>>(g->topo, state<R>(g));
     }
     TDP_LAUNCH_CHECK();
-    return backward<R>(g);
+    return bwd ? backward<R>(g) : TDP_OK;
 }
 
-template tdp_status forward_lists<float>(tdp_graph *);
-template tdp_status forward_lists<double>(tdp_graph *);
+// SMs for a backward sweep that starts with the forward sweep: the fewest
+// with which its warps (kBwdThreads / 32 a block, one block an SM) take the
+// tasks of all levels in at most kBwdRounds rounds a level on average, so
+// that it ends about when the forward sweep and the rest of the iteration
+// do; at most as many as leave every forward block at most two more chunks
+// of a level than on all SMs.  Measured at 1.2M cells (K = 16; 32 SMs here):
+// a step took 0.899, 0.855, 0.847, 0.851 ms with 24, 28, 32, 36 SMs, and
+// 0.931 ms with the backward sweep after the forward sweep; at 3.3M cells
+// (K = 32; 45 SMs here), 2.97-3.05 ms with 32 to 56 SMs against 3.14 ms.
+constexpr double kBwdRounds = 2.3;
+static int bwd_split(const tdp_graph *g) {
+    const Levels &lv = g->lv;
+    const int n = std::max(g->n_sm, 2);
+    int maxc = 1;
+    for (size_t l = 1; l < lv.lvl_ptr.size(); ++l) maxc = std::max(maxc, div_up(lv.lvl_ptr[l] - lv.lvl_ptr[l - 1], 32));
+    const int base = div_up(maxc, n);
+    const int cap = std::max(1, std::min(n / 2, n - div_up(maxc, base + 2)));
+    const int warps = kBwdThreads / 32;
+    const double budget = kBwdRounds * (double)lv.bw_s_n.size();
+    for (int x = 1; x < cap; ++x) {
+        double rounds = 0.0;
+        for (size_t l = 0; l < lv.bw_s_n.size(); ++l) rounds += div_up(lv.bw_s_n[l] + lv.bw_b_n[l], warps * x);
+        if (rounds <= budget) return x;
+    }
+    return cap;
+}
+
+template tdp_status forward_lists<float>(tdp_graph *, int);
+template tdp_status forward_lists<double>(tdp_graph *, int);
 
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
@@ -1636,8 +1665,18 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
     }
     TDP_LAUNCH_CHECK();
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)t.n_nets * kMaxK));
-    TDP_TRY(forward_lists<R>(g));
-    TDP_TRY(finish_sweeps<R>(g));
+    if (g->single_launch && g->overlap_bwd && t.depth > 0 && g->bwd_sms >= 0) {
+        // required times need no arrival: the backward sweep starts now, on
+        // its own SMs, and the forward sweep takes the others
+        if (g->bwd_sms == 0) g->bwd_sms = bwd_split(g);
+        TDP_CUDA(cudaEventRecord(g->ev_bwd_go, g->stream));
+        TDP_TRY(backward<R>(g, g->bwd_sms));
+        TDP_TRY(forward_lists<R>(g, g->bwd_sms));
+        TDP_TRY(finish_sweeps<R>(g, false));
+    } else {
+        TDP_TRY(forward_lists<R>(g));
+        TDP_TRY(finish_sweeps<R>(g));
+    }
     if (s.yprev) {  // incremental propagation is in use: keep these positions
         TDP_CUDA(cudaMemcpyAsync(s.xprev, x, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
         TDP_CUDA(cudaMemcpyAsync(s.yprev, y, sizeof(R) * t.n_cells, cudaMemcpyDeviceToDevice, g->stream));
