@@ -296,10 +296,11 @@ def own_bytes(kernel: str, nl, g_info: dict) -> float:
     if kernel == "pair_walk":
         occ = g_info["path_pins"] / 2.0                 # sink pins on paths = net arcs
         paths = g_info["paths"]
-        # per net arc: pred_in + pred_net of the driver (8), two 8-byte
-        # read-modify-writes (32) and the touch flag (1); per path: its
-        # endpoint, slack, cost, count and parent / sidetrack records (24)
-        return occ * 41.0 + paths * 24.0
+        # per net arc: pred_in + pred_net of the driver (8) and two 8-byte
+        # read-modify-writes (32; the raised maximum marks the sink touched);
+        # per path: its endpoint, slack, cost, count and parent / sidetrack
+        # records (24)
+        return occ * 40.0 + paths * 24.0
     if kernel == "pp_fwd":
         # per pair: its list entry (4), its net and the net's driver (8), the
         # two pins' cells (8), offsets (16) and the weight (4), the two cells'
