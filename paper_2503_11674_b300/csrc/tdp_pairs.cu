@@ -131,16 +131,32 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
     }
 }
 
+// The sinks already in P first, from the list of P's sinks of the last
+// compaction (a thread a listed sink), so that the FP64 arithmetic of the
+// update runs on dense warps; their accumulators are reset, so k_pair_finish,
+// which then scans every pin, finds only the new pairs.
 template <typename R>
-__global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    // a sink is touched when a walk raised its maximum (every q is finite)
-    if (p >= n_pins || s.maxq[p] == LLONG_MIN) return;
+__global__ void k_pair_finish_p(State<R> s, double w1) {
+    const int np = s.pcnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const int p = s.ppins[i];
+        if (s.maxq[p] == LLONG_MIN) continue;
+        const double sq = (double)s.sumq[p] / kQScale;
+        s.w[p] = (R)((double)s.w[p] + w1 * sq);
+        s.sumq[p] = 0;
+        s.maxq[p] = LLONG_MIN;
+    }
+}
+
+// The update of one touched sink p (the rule above).
+template <typename R>
+__device__ __forceinline__ void pair_finish_one(const Topo &t, State<R> &s, int p, long long mx, double w0,
+                                                double w1) {
     const double sq = (double)s.sumq[p] / kQScale;
     if (s.in_p[p]) {
         s.w[p] = (R)((double)s.w[p] + w1 * sq);
     } else {
-        const double mq = (double)s.maxq[p] / kQScale;
+        const double mq = (double)mx / kQScale;
         s.w[p] = (R)(w0 + w1 * (sq - mq));
         s.in_p[p] = 1;
         atomicAdd((unsigned long long *)s.n_pairs, 1ull);
@@ -153,6 +169,23 @@ __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double 
     }
     s.sumq[p] = 0;
     s.maxq[p] = LLONG_MIN;
+}
+
+// Every pin, two a 16-byte load of the maxima, on a resident grid: a sink is
+// touched when a walk raised its maximum (every q is finite).
+template <typename R>
+__global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
+    const longlong2 *m2 = reinterpret_cast<const longlong2 *>(s.maxq);
+    const int half = n_pins / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < half; i += gridDim.x * blockDim.x) {
+        const longlong2 m = m2[i];
+        if (m.x != LLONG_MIN) pair_finish_one(t, s, 2 * i, m.x, w0, w1);
+        if (m.y != LLONG_MIN) pair_finish_one(t, s, 2 * i + 1, m.y, w0, w1);
+    }
+    if ((n_pins & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long m = s.maxq[n_pins - 1];
+        if (m != LLONG_MIN) pair_finish_one(t, s, n_pins - 1, m, w0, w1);
+    }
 }
 
 // ------------------------------------------------------- compaction ---
@@ -319,8 +352,9 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
         k_pair_walk<R><<<blocks, kWalkWarps * 32, 0, g->stream>>>(t, s, g->K, KP, n_cap);
     }
     {
-        LaunchScope ls(g, KID_PAIR_FINISH);
-        k_pair_finish<R><<<div_up(t.n_pins, 256), 256, 0, g->stream>>>(t, s, t.n_pins, w0, w1);
+        LaunchScope ls(g, KID_PAIR_FINISH, 2);
+        k_pair_finish_p<R><<<148 * 4, 256, 0, g->stream>>>(s, w1);
+        k_pair_finish<R><<<148 * 8, 256, 0, g->stream>>>(t, s, t.n_pins, w0, w1);
     }
     TDP_LAUNCH_CHECK();
     return compact_pairs<R>(g);
