@@ -442,9 +442,9 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     if (t.n_ep > 0 && n_endpoints < 0) {
         // all failing endpoints: their order does not change the paths, so
         // they are listed by pin here and sorted when the paths are read
-        LaunchScope ls(g, KID_VIOL_SORT, 4);
+        LaunchScope ls(g, KID_VIOL_SORT, 2);
         k_viol_flags<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s);
-        compact_u8(g, s.ep_flag, 1, t.n_ep, t.ep, s.viol, s.nviol);
+        TDP_TRY(compact_u8(g, s.ep_flag, 1, t.n_ep, t.ep, s.viol, s.nviol));
         g->viol_sorted = false;
     } else if (t.n_ep > 0) {
         TDP_TRY(sort_failing<R>(g));

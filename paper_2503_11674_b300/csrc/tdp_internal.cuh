@@ -429,7 +429,10 @@ struct State {
     int32_t *ppins = nullptr;     // [n_pins]
     int32_t *pcells = nullptr;    // [n_cells]
     int32_t *pcnt = nullptr;      // [2]
-    int32_t *cmp_blk = nullptr;   // per-block counts of the compaction
+    // stream compaction (compact_u8): a state word per tile of flags and two
+    // counters (tiles taken, blocks done)
+    unsigned long long *cmp_tiles = nullptr;
+    unsigned *cmp_ctr = nullptr;
     // pair records, one per sink of P in the order of ppins, rebuilt after
     // every change of P: (sink's cell, driver's cell, sink's gradient slot,
     // driver's gradient slot for the first pair of a net of at most
@@ -489,6 +492,7 @@ struct tdp_graph {
     // sta_build sets it, a negative value there: the backward sweep after
     // the forward sweep, beside the rest, as incremental propagation runs it)
     int bwd_sms = 0;
+    unsigned cmp_epoch = 0;  // calls of the single-pass compaction (its tile states' tag)
     tdp::Topo topo;
     tdp::Levels lv;
     tdp::State<float> s32;
@@ -646,7 +650,7 @@ tdp_status check_sync_status(tdp_graph *g);
 // indices i < n (or map[i]) with flags[i] == val, ascending, into out, and
 // their number into the device word count (3 launches; flags padded to a
 // multiple of 32 bytes)
-void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
+tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
                 int32_t *count);
 
 // rebuild the compacted pair lists (ppins, pcells, pcnt) from in_p / cell_pf

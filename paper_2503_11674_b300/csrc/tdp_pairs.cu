@@ -189,10 +189,9 @@ __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double 
 }
 
 // ------------------------------------------------------- compaction ---
-// Indices i < n with flag[i] == val, ascending.  A thread takes 32
-// consecutive flags (two 16-byte loads), a block kCompactItems; each block
-// counts, one block scans the counts, and each block writes its indices in
-// order.
+// Indices i < n with flag[i] == val, ascending (k_compact, below).  A
+// thread takes 32 consecutive flags (two 16-byte loads), a block a tile of
+// kCompactItems.
 
 constexpr int kCmpThreads = kCompactItems / 32;
 
@@ -236,52 +235,98 @@ __device__ __forceinline__ int block_excl_sum(int v, int *sh, int &total) {
     return before;
 }
 
-__global__ void __launch_bounds__(kCmpThreads) k_cmp_count(const uint8_t *f, uint8_t val, int n, int32_t *blk) {
-    __shared__ int sh[32];
-    const int base = blockIdx.x * kCompactItems + threadIdx.x * 32;
-    int total;
-    block_excl_sum(__popc(match_bits(f, base, n, val)), sh, total);
-    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+// One pass (decoupled look-back): a block takes the next tile of
+// kCompactItems flags from a counter, so every earlier tile belongs to a
+// block that is running or done; it counts its matches, publishes the
+// count, adds the counts of the tiles before it back to the first that has
+// published its inclusive prefix, publishes its own inclusive prefix and
+// writes its indices.  A tile's state is one 64-bit word: the call's epoch
+// (30 bits, so that nothing is cleared between calls), a flag (count /
+// inclusive prefix) and the value.  The last block to finish resets the
+// counters for the next call.  A look-back that polls too long (2^22 polls)
+// sets the graph's sticky status (reported as TDP_ERR_TIMEOUT) and stops.
+constexpr unsigned kCmpAgg = 1u, kCmpIncl = 2u;
+__device__ __forceinline__ unsigned long long cmp_word(unsigned epoch, unsigned flag, unsigned v) {
+    return ((unsigned long long)(epoch & 0x3fffffffu) << 34) | ((unsigned long long)flag << 32) | v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// one block of kCmpScanThreads (small, so that it finds room on an SM beside
-// the backward sweep that may run on the library's second stream)
-constexpr int kCmpScanThreads = 256;
-
-__global__ void __launch_bounds__(kCmpScanThreads) k_cmp_scan(int32_t *blk, int nb, int32_t *total) {
+__global__ void __launch_bounds__(kCmpThreads) k_compact(const uint8_t *f, uint8_t val, int n, const int32_t *map,
+                                                        int32_t *out, int32_t *count, unsigned long long *tiles,
+                                                        unsigned *ctr, unsigned epoch, unsigned *status) {
     __shared__ int sh[32];
-    int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kCmpScanThreads) {
-        const int i = b0 + threadIdx.x;
-        int t;
-        const int ex = block_excl_sum(i < nb ? blk[i] : 0, sh, t);
-        if (i < nb) blk[i] = carry + ex;
-        carry += t;
+    __shared__ int s_tile, s_prefix;
+    const int nb = max(div_up_dev(n, kCompactItems), 1);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= nb) {  // the counters were not reset: no tile state to touch
+        if (threadIdx.x == 0) {
+            atomicExch(status, 1u);
+            if (atomicAdd(&ctr[1], 1u) == (unsigned)nb - 1u) {
+                ctr[0] = 0u;
+                ctr[1] = 0u;
+            }
+        }
+        return;
     }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void __launch_bounds__(kCmpThreads) k_cmp_write(const uint8_t *f, uint8_t val, int n, const int32_t *blk,
-                                                          const int32_t *map, int32_t *out) {
-    __shared__ int sh[32];
-    const int base = blockIdx.x * kCompactItems + threadIdx.x * 32;
+    const int base = tile * kCompactItems + threadIdx.x * 32;
     unsigned bits = match_bits(f, base, n, val);
     int total;
-    int pos = blk[blockIdx.x] + block_excl_sum(__popc(bits), sh, total);
+    const int before = block_excl_sum(__popc(bits), sh, total);
+    if (threadIdx.x == 0) {
+        int prefix = 0;
+        if (tile > 0) {
+            st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpAgg, (unsigned)total));
+            unsigned polls = 0;
+            for (int j = tile - 1; j >= 0;) {
+                const unsigned long long w = ld_relaxed_u64(&tiles[j]);
+                const unsigned flag = (unsigned)(w >> 32) & 3u;
+                if ((unsigned)(w >> 34) != (epoch & 0x3fffffffu) || flag == 0u) {
+                    if (++polls > (1u << 22)) {
+                        atomicExch(status, 1u);
+                        break;
+                    }
+                    continue;
+                }
+                prefix += (int)(unsigned)w;
+                if (flag == kCmpIncl) break;
+                --j;
+            }
+        }
+        st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpIncl, (unsigned)(prefix + total)));
+        s_prefix = prefix;
+        if (tile == nb - 1) *count = prefix + total;
+    }
+    __syncthreads();
+    int pos = s_prefix + before;
     while (bits) {
         const int k = __ffs(bits) - 1;
         out[pos++] = map ? map[base + k] : base + k;
         bits &= bits - 1u;
     }
+    if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1u) == (unsigned)nb - 1u) {
+        ctr[0] = 0u;
+        ctr[1] = 0u;
+    }
 }
 
-void compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
-                int32_t *count) {
-    int32_t *blk = g->prec == TDP_FP32 ? g->s32.cmp_blk : g->s64.cmp_blk;
+tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
+                      int32_t *count) {
+    unsigned long long *tiles = g->prec == TDP_FP32 ? g->s32.cmp_tiles : g->s64.cmp_tiles;
+    unsigned *ctr = g->prec == TDP_FP32 ? g->s32.cmp_ctr : g->s64.cmp_ctr;
+    unsigned *status = g->prec == TDP_FP32 ? g->s32.gsync + 1 : g->s64.gsync + 1;
     const int nb = std::max(div_up(n, kCompactItems), 1);
-    k_cmp_count<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk);
-    k_cmp_scan<<<1, kCmpScanThreads, 0, g->stream>>>(blk, nb, count);
-    k_cmp_write<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, blk, map, out);
+    const unsigned epoch = ++g->cmp_epoch;
+    k_compact<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, map, out, count, tiles, ctr, epoch, status);
+    return TDP_OK;
 }
 
 // The loss's pair records (State::pr_*), a thread per sink of P: what the
@@ -325,11 +370,11 @@ template <typename R>
 tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt);
-    compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1);
+    TDP_TRY(compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt));
+    TDP_TRY(compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1));
     TDP_CUDA(cudaMemsetAsync(s.pr_nbig, 0, sizeof(int32_t), g->stream));
     k_pair_records<R><<<148 * 4, 256, 0, g->stream>>>(t, s);
-    g->n_launch += 7;
+    g->n_launch += 3;
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }

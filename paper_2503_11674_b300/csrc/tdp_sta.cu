@@ -763,7 +763,9 @@ static void launch_fwd(const Topo &t, const State<R> &s, int lo, int hi, int L, 
 // a level's work cut into warp-sized chunks, chunk j on block j mod gridDim
 // so that a level is spread over every SM.
 constexpr int kFwdThreads = 256;
-constexpr int kBwdThreads = 512;
+// (the backward sweep: 28 warps a block, which its 68-72 registers allow,
+// so that fewer SMs take a level's tasks in one round)
+constexpr int kBwdThreads = 896;
 
 // The whole forward sweep in one cooperative launch: levels in order, a
 // thread per cell, a grid-wide barrier between levels.  A thread carries its
@@ -1626,11 +1628,12 @@ static tdp_status finish_sweeps(tdp_graph *g, bool bwd = true) {
 // tasks of all levels in at most kBwdRounds rounds a level on average, so
 // that it ends about when the forward sweep and the rest of the iteration
 // do; at most as many as leave every forward block at most two more chunks
-// of a level than on all SMs.  Measured at 1.2M cells (K = 16; 32 SMs here):
-// a step took 0.899, 0.855, 0.847, 0.851 ms with 24, 28, 32, 36 SMs, and
-// 0.931 ms with the backward sweep after the forward sweep; at 3.3M cells
-// (K = 32; 45 SMs here), 2.97-3.05 ms with 32 to 56 SMs against 3.14 ms.
-constexpr double kBwdRounds = 2.3;
+// of a level than on all SMs.  Measured with 28-warp blocks at 1.2M cells
+// (K = 16; 24 SMs here): a step took 0.953, 0.885, 0.837, 0.837 ms with 16,
+// 22, 24, 26 SMs (0.848 ms with 16-warp blocks on 32 SMs, 0.931 ms with the
+// backward sweep after the forward sweep); at 3.3M cells (K = 32; 45 SMs
+// here), 2.92, 2.94, 2.89 ms with 24, 28, 40 SMs against 3.14 ms.
+constexpr double kBwdRounds = 1.8;
 static int bwd_split(const tdp_graph *g) {
     const Levels &lv = g->lv;
     const int n = std::max(g->n_sm, 2);
