@@ -3,7 +3,7 @@
 
 One step = one timing iteration of the method on one synthetic netlist:
     sta_propagate -> extract_critical_paths (report_timing_endpoint(all, K))
-    -> attraction_update_pairs (Eq. w_ij) -> attraction_loss_fwd -> _bwd
+    -> attraction_update_pairs (Eq. w_ij) -> attraction_loss_fwd_bwd (Eq. 9, loss and gradient)
 at a new placement every step (seeded Gaussian moves, sigma = 2 um).  The
 workload is the 1.2M-cell netlist (1.3M nets, ~4.2M pins, depth 80, 0.5% nets
 of fanout 64-1000, clock at 0.85x the largest arrival, K = 16).
@@ -224,7 +224,7 @@ def netlist_counts(nl) -> dict:
 # reported on their own.
 MODEL_STEPS = {
     "net_rc": "a1+a2", "fwd_sweep": "a3+a4", "bwd_sweep": "a5", "ep_wns": "a6 (endpoints)",
-    "topk+pair_walk": "a7-a10", "pp_fwd": "a11 forward", "pp_bwd": "a11 backward",
+    "topk+pair_walk": "a7-a10", "pp_fwd_bwd": "a11 forward + backward",
 }
 
 
@@ -241,10 +241,8 @@ def model_bytes(step: str, nl, g_info: dict) -> float:
         return 12 * c["endpoints"]
     if step == "topk+pair_walk":
         return (20 + 32) * g_info["path_pins"] / 2.0
-    if step == "pp_fwd":
-        return 40 * g_info["pairs"]
-    if step == "pp_bwd":
-        return 40 * g_info["pairs"] + 8 * c["pins"] + 8 * c["cells"]
+    if step == "pp_fwd_bwd":
+        return 40 * g_info["pairs"] + 40 * g_info["pairs"] + 8 * c["pins"] + 8 * c["cells"]
     raise ValueError(step)
 
 
@@ -312,6 +310,11 @@ def own_bytes(kernel: str, nl, g_info: dict) -> float:
         # written); per pair net the driver's slot (4 + 8 written)
         nP = g_info["pairs"]
         return 68 * nP + 12 * min(nP, N)
+    if kernel == "pp_fwd_bwd":
+        # the loss and the per-pair gradients in one pass over the records:
+        # per pair as the backward pass (68), per pair net the driver's slot
+        nP = g_info["pairs"]
+        return 68 * nP + 12 * min(nP, N)
     if kernel == "pp_bwd_cell":
         return 4 * (C + 1) + 8 * P + C + 8 * C
     if kernel == "topk":
@@ -371,8 +374,7 @@ def run_ours(args):
         G.sta_propagate(xk, yk, T, sync=False)
         G.extract_critical_paths(-1, K, False, sync=False)
         G.attraction_update_pairs(W0, W1, sync=False)
-        G.attraction_loss_fwd(xk, yk, BETA, out=loss_buf)
-        G.attraction_loss_bwd(xk, yk, BETA, gx=gx, gy=gy)
+        G.attraction_loss_fwd_bwd(xk, yk, BETA, out=loss_buf, gx=gx, gy=gy)
 
     stream = torch.cuda.current_stream(dev)
     for k in range(args.warmup):
@@ -443,8 +445,7 @@ def run_ours(args):
             G.sta_propagate(xd[b], yd[b], T, sync=False)
             G.extract_critical_paths(-1, K, False, sync=False)
             G.attraction_update_pairs(W0, W1, sync=False)
-            G.attraction_loss_fwd(xd[b], yd[b], BETA, out=lossd[b])
-            G.attraction_loss_bwd(xd[b], yd[b], BETA, gx=gxd[b], gy=gyd[b])
+            G.attraction_loss_fwd_bwd(xd[b], yd[b], BETA, out=lossd[b], gx=gxd[b], gy=gyd[b])
             done[b].record(stream)
             with torch.cuda.stream(copy):
                 if k + 1 < n_steps:      # next positions, once step k - 1 is done with the buffers
@@ -470,7 +471,7 @@ def run_ours(args):
     e2e = {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
            "d2h_bytes_per_step": 2 * n * 4 + 8, "steps": e2e_steps,
            "api": "TimingGraph.sta_propagate/extract_critical_paths/attraction_update_pairs/"
-                  "attraction_loss_fwd/bwd; positions in from pinned host memory and loss + gradient "
+                  "attraction_loss_fwd_bwd; positions in from pinned host memory and loss + gradient "
                   "out to pinned host memory every step, on a second stream, double-buffered"}
 
     stages = None
@@ -585,8 +586,7 @@ def fp64_run(nl, xs, ys, T, K, dev, stream, wns32, tns32, steps=20):
         G.sta_propagate(x, y, T, sync=False)
         G.extract_critical_paths(-1, K, False, sync=False)
         G.attraction_update_pairs(W0, W1, sync=False)
-        G.attraction_loss_fwd(x, y, BETA, out=loss)
-        G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+        G.attraction_loss_fwd_bwd(x, y, BETA, out=loss, gx=gx, gy=gy)
 
     for k in range(3):
         step(k)
@@ -654,8 +654,7 @@ def time_stages(G, xs, ys, T, K, loss_buf, gx, gy, stream, reps):
     return out
 
 
-KERNEL_TABLE = ["net_rc", "fwd_sweep", "ep_wns", "bwd_sweep", "topk", "pair_walk", "pp_fwd", "pp_bwd_net",
-                "pp_bwd_cell"]
+KERNEL_TABLE = ["net_rc", "fwd_sweep", "ep_wns", "bwd_sweep", "topk", "pair_walk", "pp_fwd_bwd", "pp_bwd_cell"]
 
 
 def kernel_table(G, step, k0, nl, info, workload, reps=10):
@@ -698,13 +697,13 @@ def roofline_per_kernel(ktab, nl, info, hbm):
         rows[step] = {"step": MODEL_STEPS[step], "kernels": kernels, "ms": round(ms, 4), "model_bytes": int(b),
                       "gbs": round(g, 1), "frac": round(g / hbm, 4)}
 
-    for k in ("net_rc", "fwd_sweep", "bwd_sweep", "ep_wns", "pp_fwd"):
+    for k in ("net_rc", "fwd_sweep", "bwd_sweep", "ep_wns"):
         if k in ktab:
             add(k, ktab[k]["ms"], [k])
     if "topk" in ktab and "pair_walk" in ktab:
         add("topk+pair_walk", ktab["topk"]["ms"] + ktab["pair_walk"]["ms"], ["topk", "pair_walk"])
-    if "pp_bwd_net" in ktab and "pp_bwd_cell" in ktab:
-        add("pp_bwd", ktab["pp_bwd_net"]["ms"] + ktab["pp_bwd_cell"]["ms"], ["pp_bwd_net", "pp_bwd_cell"])
+    if "pp_fwd_bwd" in ktab and "pp_bwd_cell" in ktab:
+        add("pp_fwd_bwd", ktab["pp_fwd_bwd"]["ms"] + ktab["pp_bwd_cell"]["ms"], ["pp_fwd_bwd", "pp_bwd_cell"])
     return rows
 
 
@@ -849,8 +848,7 @@ def incremental(G, xs, ys, T, K, mv, stream, reps=20):
             else:
                 G.extract_critical_paths(-1, K, False, sync=False)
                 G.attraction_update_pairs(W0, W1, sync=False)
-                G.attraction_loss_fwd(x, y, BETA, out=buf)
-                G.attraction_loss_bwd(x, y, BETA, gx=gx, gy=gy)
+                G.attraction_loss_fwd_bwd(x, y, BETA, out=buf, gx=gx, gy=gy)
                 G.sta_join()
             ev[2].record(stream)
             torch.cuda.synchronize()

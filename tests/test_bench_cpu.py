@@ -71,7 +71,7 @@ def test_model_bytes_follow_the_per_element_figures():
     assert bench.model_bytes("net_rc", nl, info) == 32 * (c["sinks"] + nl.n_nets)
     assert bench.model_bytes("bwd_sweep", nl, info) == 12 * nl.n_pins
     assert bench.model_bytes("topk+pair_walk", nl, info) == 52 * 500
-    assert bench.model_bytes("pp_bwd", nl, info) == 40 * 50 + 8 * nl.n_pins + 8 * nl.n_cells
+    assert bench.model_bytes("pp_fwd_bwd", nl, info) == 80 * 50 + 8 * nl.n_pins + 8 * nl.n_cells
     assert bench.list_bytes(nl, info) == c["comb"] * 16 * 15
-    assert set(bench.MODEL_STEPS) == {"net_rc", "fwd_sweep", "bwd_sweep", "ep_wns", "topk+pair_walk", "pp_fwd",
-                                      "pp_bwd"}
+    assert set(bench.MODEL_STEPS) == {"net_rc", "fwd_sweep", "bwd_sweep", "ep_wns", "topk+pair_walk",
+                                      "pp_fwd_bwd"}
