@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 456165376, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
-        "bwd_sweep": {"bytes": 127699712, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
-        "pair_walk": {"bytes": 22996224, "sources": PAIR_SOURCES, "sha256": "7fe9d02640caca45dde9ed7a8f5b432754c5c0e8b86626205d295a5856759ad3"},
+        "fwd_sweep": {"bytes": 461119744, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
+        "bwd_sweep": {"bytes": 129061376, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
+        "pair_walk": {"bytes": 22058240, "sources": PAIR_SOURCES, "sha256": "07ab00a35b282f6aabdc1661bf32154af40c1941b66460b7c35639ec004187ae"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2453452032, "sources": SWEEP_SOURCES, "sha256": "b41429b692896bef44da6e00e125a017963df5e989feab375e5d57dddc1ffe2f"},
+        "fwd_sweep": {"bytes": 2478353920, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
     },
 }
 
