@@ -708,13 +708,17 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
             for (int j = 0; j < L; ++j) li[j] = LR::none();
         }
         if (act) {
-            // every thread inserts kPre entries (absent ones as no-op
-            // sentinels), so that the threads of a warp do not diverge
+            // the own deviations: every input but the worst, kPre - 1 slots
+            // (absent ones as no-op sentinels, so that the threads of a warp
+            // do not diverge), inserted in input order
+            typename LR::E prev = LR::none();
 #pragma unroll
             for (int u = 0; u < kPre; ++u) {
-                const bool own = u < nin && u != bu;
                 const uint32_t key = ((c.ip[u] < bi ? 0u : 2u) << 29) | (uint32_t)c.ip[u];
-                list_insert<R, L>(li, own ? LR::make(AC::diff(best, av[u]), key) : LR::none());
+                const typename LR::E e = u < nin && u != bu ? LR::make(AC::diff(best, av[u]), key) : LR::none();
+                // slot u - 1 takes input u - 1 below the worst input, input u from it on
+                if (u > 0) list_insert<R, L>(li, u - 1 < bu ? prev : e);
+                prev = e;
             }
         }
         if constexpr (CMP) {

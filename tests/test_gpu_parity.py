@@ -476,6 +476,20 @@ def test_overlapped_backward_sweep_matches_serial(prec, monkeypatch):
         _assert_same(a, b)
 
 
+@pytest.mark.parametrize("sms", ["1", "60", "-1"])
+def test_backward_sweep_split_does_not_change_results(sms, monkeypatch):
+    """The backward sweep started with net RC on its own SMs (one of them, 60
+    of them, or after the forward sweep with TDP_BWD_SMS=-1) gives the bits of
+    the default split: the SM split only moves work between the sweeps."""
+    nl = netgen.generate("mid", 7)
+    T = oracle.clock_period(nl, 0.85)
+    ref = _pipeline_async(nl, T, "fp32")
+    monkeypatch.setenv("TDP_BWD_SMS", sms)
+    got = _pipeline_async(nl, T, "fp32")
+    for a, b in zip(ref, got):
+        _assert_same(a, b)
+
+
 # --------------------------------------------------------- edge cases ------
 
 def test_no_violation_and_empty_pairs():
