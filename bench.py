@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 461119744, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
-        "bwd_sweep": {"bytes": 129061376, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
-        "pair_walk": {"bytes": 22058240, "sources": PAIR_SOURCES, "sha256": "07ab00a35b282f6aabdc1661bf32154af40c1941b66460b7c35639ec004187ae"},
+        "fwd_sweep": {"bytes": 461269504, "sources": SWEEP_SOURCES, "sha256": "61efedb002453cd0a97167cca47ab824c1a28f8a2f12f5cd1d5624e28ea16ff7"},
+        "bwd_sweep": {"bytes": 128757248, "sources": SWEEP_SOURCES, "sha256": "61efedb002453cd0a97167cca47ab824c1a28f8a2f12f5cd1d5624e28ea16ff7"},
+        "pair_walk": {"bytes": 22055552, "sources": PAIR_SOURCES, "sha256": "07ab00a35b282f6aabdc1661bf32154af40c1941b66460b7c35639ec004187ae"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2478353920, "sources": SWEEP_SOURCES, "sha256": "2868e9f9056c6fb43ef92213b15bc75caf54ee79ad1eb94b198ba78939172396"},
+        "fwd_sweep": {"bytes": 2478261248, "sources": SWEEP_SOURCES, "sha256": "61efedb002453cd0a97167cca47ab824c1a28f8a2f12f5cd1d5624e28ea16ff7"},
     },
 }
 
