@@ -472,12 +472,11 @@ __device__ __forceinline__ void sts16(unsigned a, float4 v) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                  : "memory");
 }
-template <typename R, int L, bool COH>
-__device__ __forceinline__ void warp_list_load(const BEnt<R> *blist, int src, float4 *stage,
-                                               typename LReg<R>::E (&li)[L]) {
+// the copies of the lists src (per lane) into the staging area, not waited for
+template <typename R, int L>
+__device__ __forceinline__ void warp_list_issue(const BEnt<R> *blist, int src, unsigned st0) {
     using W = WarpList<R, L>;
     const int lane = lane_now();
-    const unsigned st0 = smem_u32(stage);
 #pragma unroll
     for (int t = 0; t < W::C; ++t) {
         const int i = t * W::LPI + lane / W::C, q = lane % W::C;
@@ -489,16 +488,39 @@ __device__ __forceinline__ void warp_list_load(const BEnt<R> *blist, int src, fl
                          : "memory");
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
-    // every lane unpacks its slots; a lane without a list then takes sentinels
-    // (a select per entry, not a branch around the unpacking)
+}
+// every lane unpacks its list from the staging area at st0 (after the
+// copies were waited for); a lane without a list (has false) takes
+// sentinels (a select per entry, not a branch around the unpacking)
+template <typename R, int L>
+__device__ __forceinline__ void warp_list_take(unsigned st0, bool has, typename LReg<R>::E (&li)[L]) {
+    using W = WarpList<R, L>;
+    const int lane = lane_now();
 #pragma unroll
     for (int q = 0; q < W::C; ++q) list_unpiece<L>(lds16(st0 + 16u * (unsigned)W::slot(lane, q)), q, li);
-    const bool has = src >= 0;
 #pragma unroll
     for (int j = 0; j < L; ++j) li[j] = has ? li[j] : LReg<R>::none();
+}
+template <typename R, int L, bool COH>
+__device__ __forceinline__ void warp_list_load(const BEnt<R> *blist, int src, float4 *stage,
+                                               typename LReg<R>::E (&li)[L]) {
+    const unsigned st0 = smem_u32(stage);
+    warp_list_issue<R, L>(blist, src, st0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
+    warp_list_take<R, L>(st0, src >= 0, li);
+    __syncwarp();
+}
+
+// Whether a warp fetches the lists of all of a cell's inputs at once (one
+// staging area per input slot, kPre of them), issued right after the loads
+// of the inputs' arrivals, so that the worst input's list needs no load of
+// its own after the argmax: where kPre staging areas of a 256-thread block
+// fit in shared memory (lists of at most 128 bytes). Issued before the
+// arrival loads, the copies delay them and the sweep gets slower.
+template <typename R, int L>
+__host__ __device__ constexpr bool all_lists() {
+    return L > 0 && (size_t)list_group(L) * sizeof(BEnt<R>) <= 128;
 }
 template <typename R, int L>
 __device__ __forceinline__ void warp_list_put(BEnt<R> *blist, int dst, float4 *stage,
@@ -520,9 +542,12 @@ __device__ __forceinline__ void warp_list_put(BEnt<R> *blist, int dst, float4 *s
 }
 
 // bytes of the staging area a block of `threads` threads needs for lists of L
+// (kPre areas a warp where all_lists<R, L>() holds)
 template <typename R>
 __host__ __device__ constexpr size_t warp_list_smem(int L, int threads) {
-    return L == 0 ? 0 : (size_t)threads * (size_t)list_group(L) * sizeof(BEnt<R>);
+    return L == 0 ? 0
+                  : (size_t)threads * (size_t)list_group(L) * sizeof(BEnt<R>) *
+                        ((size_t)list_group(L) * sizeof(BEnt<R>) <= 128 ? kPre : 1);
 }
 
 // whether the stored list at dst holds, bit for bit, what list_put(dst, li)
@@ -654,10 +679,12 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
     A best = AC::ninf();
     A av[kPre];
     bool chg = false;
+    [[maybe_unused]] unsigned lst0 = 0;
+    R dcell = R(0);
+    R tv[kPre];
+    int pl[kPre];
     if (act) {
-        const R dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
-        R tv[kPre];
-        int pl[kPre];
+        dcell = c.vals ? c.dcell : ldg(&s.dnet[c.e]);
 #pragma unroll
         for (int u = 0; u < kPre; ++u) {
             if (u < nin) {
@@ -671,6 +698,19 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
                 }
             }
         }
+    }
+    if constexpr (WARP && all_lists<R, L>()) {
+        // the lists of every input from a combinational cell, into one
+        // staging area per input slot, right after the inputs' arrivals
+        constexpr unsigned kArea = 32u * WarpList<R, L>::C * 16u;
+        lst0 = smem_u32(stage);
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool lu = act && u < nin && ((c.fl >> (8 * u)) & kInComb);
+            warp_list_issue<R, L>(s.blist, lu ? c.in[u] : -1, lst0 + (unsigned)u * kArea);
+        }
+    }
+    if (act) {
         // inputs ascending by pin: strict > keeps the lowest pin on ties (and
         // the first input if arrivals are not comparable)
 #pragma unroll
@@ -699,7 +739,14 @@ __device__ __forceinline__ bool fwd_cell(const Topo &t, State<R> &s, const CellP
         constexpr int G = list_group(L);
         typename LR::E li[L];
         const bool from = act && nin > 0 && ((c.fl >> (8 * bu)) & kInComb);
-        if constexpr (WARP) {
+        if constexpr (WARP && all_lists<R, L>()) {
+            // the worst input's list from that input's staging area
+            constexpr unsigned kArea = 32u * WarpList<R, L>::C * 16u;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            warp_list_take<R, L>(lst0 + (unsigned)bu * kArea, from, li);
+            __syncwarp();
+        } else if constexpr (WARP) {
             warp_list_load<R, L, COH>(s.blist, from ? bn : -1, stage, li);
         } else if (from) {
             list_load<L, COH>(s.blist + (size_t)bn * G, li);
@@ -794,7 +841,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_sweep(Topo t, State<R> s
     };
     // staging area of this warp's list moves (warp_list_smem bytes a block)
     extern __shared__ float4 lstage[];
-    float4 *stage = lstage + (size_t)(threadIdx.x >> 5) * 32 * (L > 0 ? WarpList<R, L>::C : 0);
+    float4 *stage = lstage + (size_t)(threadIdx.x >> 5) * 32 * (L > 0 ? WarpList<R, L>::C : 0) *
+                                 (all_lists<R, L>() ? kPre : 1);
     const int l0 = from ? max(ldcg(from), 1) : 1;
     if (l0 > t.depth) return;
     CellPre<R> cur, nxt;
