@@ -105,10 +105,8 @@ static tdp_status build_state(tdp_graph *g, const tdp_netlist_desc *d) {
         TDP_CUDA(cudaMemset(s.pr_nbig, 0, sizeof(int32_t)));
     }
     TDP_TRY(dalloc(g, &s.pcnt, 2));
-    TDP_TRY(dalloc(g, &s.cmp_tiles, std::max(t.n_pins, std::max(t.n_nets, t.n_cells)) / kCompactItems + 2));
-    TDP_CUDA(cudaMemset(s.cmp_tiles, 0,
-                        sizeof(unsigned long long) *
-                            (std::max(t.n_pins, std::max(t.n_nets, t.n_cells)) / kCompactItems + 2)));
+    TDP_TRY(dalloc(g, &s.cmp_tiles, compact_tile_cap(t)));
+    TDP_CUDA(cudaMemset(s.cmp_tiles, 0, sizeof(unsigned long long) * compact_tile_cap(t)));
     TDP_TRY(dalloc(g, &s.cmp_ctr, 2));
     TDP_CUDA(cudaMemset(s.cmp_ctr, 0, 2 * sizeof(unsigned)));
     TDP_CUDA(cudaMemset(s.net_pf, 0, (size_t)t.n_nets + 32));

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -647,11 +648,30 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
 // stream); TDP_ERR_TIMEOUT if a wait gave up since the last check
 tdp_status check_sync_status(tdp_graph *g);
 
-// indices i < n (or map[i]) with flags[i] == val, ascending, into out, and
-// their number into the device word count (3 launches; flags padded to a
-// multiple of 32 bytes)
-tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
-                int32_t *count);
+// one flag array of a stream compaction: the indices i < n (or map[i]) with
+// f[i] == val, ascending, go to out and their number to the device word
+// count
+struct CmpPart {
+    const uint8_t *f;
+    const int32_t *map;
+    int32_t *out;
+    int32_t *count;
+    int n;
+    uint8_t val;
+};
+
+// the compaction of one flag array (b == nullptr) or of two in one launch
+// (flags padded to a multiple of 32 bytes)
+tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b = nullptr);
+inline tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map,
+                             int32_t *out, int32_t *count) {
+    return compact_flags(g, CmpPart{flags, map, out, count, n, val});
+}
+
+// tile states the compaction of the graph's largest flag arrays needs
+inline size_t compact_tile_cap(const Topo &t) {
+    return (size_t)std::max(t.n_pins + t.n_cells, t.n_nets) / kCompactItems + 4;
+}
 
 // rebuild the compacted pair lists (ppins, pcells, pcnt) from in_p / cell_pf
 template <typename R>

@@ -240,11 +240,13 @@ __device__ __forceinline__ int block_excl_sum(int v, int *sh, int &total) {
 // block that is running or done; it counts its matches, publishes the
 // count, adds the counts of the tiles before it back to the first that has
 // published its inclusive prefix, publishes its own inclusive prefix and
-// writes its indices.  A tile's state is one 64-bit word: the call's epoch
-// (30 bits, so that nothing is cleared between calls), a flag (count /
-// inclusive prefix) and the value.  The last block to finish resets the
-// counters for the next call.  A look-back that polls too long (2^22 polls)
-// sets the graph's sticky status (reported as TDP_ERR_TIMEOUT) and stops.
+// writes its indices.  Two flag arrays share a launch as two runs of tiles;
+// a look-back ends at the first tile of its own run.  A tile's state is one
+// 64-bit word: the call's epoch (30 bits, so that nothing is cleared between
+// calls), a flag (count / inclusive prefix) and the value.  The last block
+// to finish resets the counters for the next call.  A look-back that polls
+// too long (2^22 polls) sets the graph's sticky status (reported as
+// TDP_ERR_TIMEOUT) and stops.
 constexpr unsigned kCmpAgg = 1u, kCmpIncl = 2u;
 __device__ __forceinline__ unsigned long long cmp_word(unsigned epoch, unsigned flag, unsigned v) {
     return ((unsigned long long)(epoch & 0x3fffffffu) << 34) | ((unsigned long long)flag << 32) | v;
@@ -258,12 +260,51 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
-__global__ void __launch_bounds__(kCmpThreads) k_compact(const uint8_t *f, uint8_t val, int n, const int32_t *map,
-                                                        int32_t *out, int32_t *count, unsigned long long *tiles,
-                                                        unsigned *ctr, unsigned epoch, unsigned *status) {
+// The sum of the counts of tiles first .. tile - 1, by one warp: it reads the
+// states of the 32 tiles below j at once (lane l reads tile j - l) and, once
+// every tile down to the nearest inclusive prefix has published, adds their
+// values; without an inclusive prefix in the window it moves down 32 tiles.
+// A tile below first reads as an inclusive prefix of 0.
+__device__ __forceinline__ int cmp_look_back(unsigned long long *tiles, int tile, int first, unsigned epoch,
+                                             unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    const unsigned ep = epoch & 0x3fffffffu;
+    int prefix = 0;
+    unsigned polls = 0;
+    for (int j = tile - 1;;) {
+        const int jj = j - lane;
+        unsigned flag = kCmpIncl, v = 0u;
+        if (jj >= first) {
+            const unsigned long long w = ld_relaxed_u64(&tiles[jj]);
+            flag = (unsigned)(w >> 34) == ep ? (unsigned)(w >> 32) & 3u : 0u;
+            v = (unsigned)w;
+        }
+        const unsigned incl = __ballot_sync(0xffffffffu, flag == kCmpIncl);
+        const unsigned wait = __ballot_sync(0xffffffffu, flag == 0u);
+        const int stop = incl ? __ffs(incl) - 1 : 31;  // the last lane the sum takes
+        const unsigned need = stop == 31 ? 0xffffffffu : (2u << stop) - 1u;
+        if (wait & need) {
+            if (++polls > (1u << 22)) {
+                if (lane == 0) atomicExch(status, 1u);
+                break;
+            }
+            continue;
+        }
+        int x = lane <= stop ? (int)v : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        prefix += x;
+        if (incl) break;
+        j -= 32;
+    }
+    return prefix;
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_compact(CmpPart p0, CmpPart p1, int nb0, int nb,
+                                                        unsigned long long *tiles, unsigned *ctr, unsigned epoch,
+                                                        unsigned *status) {
     __shared__ int sh[32];
     __shared__ int s_tile, s_prefix;
-    const int nb = max(div_up_dev(n, kCompactItems), 1);
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], 1u);
     __syncthreads();
     const int tile = s_tile;
@@ -277,39 +318,27 @@ __global__ void __launch_bounds__(kCmpThreads) k_compact(const uint8_t *f, uint8
         }
         return;
     }
-    const int base = tile * kCompactItems + threadIdx.x * 32;
-    unsigned bits = match_bits(f, base, n, val);
+    const bool second = tile >= nb0;
+    const CmpPart p = second ? p1 : p0;
+    const int first = second ? nb0 : 0, last = second ? nb - 1 : nb0 - 1;
+    const int base = (tile - first) * kCompactItems + threadIdx.x * 32;
+    unsigned bits = match_bits(p.f, base, p.n, p.val);
     int total;
     const int before = block_excl_sum(__popc(bits), sh, total);
-    if (threadIdx.x == 0) {
-        int prefix = 0;
-        if (tile > 0) {
-            st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpAgg, (unsigned)total));
-            unsigned polls = 0;
-            for (int j = tile - 1; j >= 0;) {
-                const unsigned long long w = ld_relaxed_u64(&tiles[j]);
-                const unsigned flag = (unsigned)(w >> 32) & 3u;
-                if ((unsigned)(w >> 34) != (epoch & 0x3fffffffu) || flag == 0u) {
-                    if (++polls > (1u << 22)) {
-                        atomicExch(status, 1u);
-                        break;
-                    }
-                    continue;
-                }
-                prefix += (int)(unsigned)w;
-                if (flag == kCmpIncl) break;
-                --j;
-            }
+    if (threadIdx.x < 32) {
+        if (tile > first && threadIdx.x == 0) st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpAgg, (unsigned)total));
+        const int prefix = tile > first ? cmp_look_back(tiles, tile, first, epoch, status) : 0;
+        if (threadIdx.x == 0) {
+            st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpIncl, (unsigned)(prefix + total)));
+            s_prefix = prefix;
+            if (tile == last) *p.count = prefix + total;
         }
-        st_relaxed_u64(&tiles[tile], cmp_word(epoch, kCmpIncl, (unsigned)(prefix + total)));
-        s_prefix = prefix;
-        if (tile == nb - 1) *count = prefix + total;
     }
     __syncthreads();
     int pos = s_prefix + before;
     while (bits) {
         const int k = __ffs(bits) - 1;
-        out[pos++] = map ? map[base + k] : base + k;
+        p.out[pos++] = p.map ? p.map[base + k] : base + k;
         bits &= bits - 1u;
     }
     if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1u) == (unsigned)nb - 1u) {
@@ -318,14 +347,18 @@ __global__ void __launch_bounds__(kCmpThreads) k_compact(const uint8_t *f, uint8
     }
 }
 
-tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map, int32_t *out,
-                      int32_t *count) {
+tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b) {
     unsigned long long *tiles = g->prec == TDP_FP32 ? g->s32.cmp_tiles : g->s64.cmp_tiles;
     unsigned *ctr = g->prec == TDP_FP32 ? g->s32.cmp_ctr : g->s64.cmp_ctr;
     unsigned *status = g->prec == TDP_FP32 ? g->s32.gsync + 1 : g->s64.gsync + 1;
-    const int nb = std::max(div_up(n, kCompactItems), 1);
+    const int nb0 = std::max(div_up(a.n, kCompactItems), 1);
+    const int nb = nb0 + (b ? std::max(div_up(b->n, kCompactItems), 1) : 0);
+    if ((size_t)nb > compact_tile_cap(g->topo)) {
+        set_error("compaction: %d tiles, %zu tile states", nb, compact_tile_cap(g->topo));
+        return TDP_ERR_INVALID;
+    }
     const unsigned epoch = ++g->cmp_epoch;
-    k_compact<<<nb, kCmpThreads, 0, g->stream>>>(flags, val, n, map, out, count, tiles, ctr, epoch, status);
+    k_compact<<<nb, kCmpThreads, 0, g->stream>>>(a, b ? *b : a, nb0, nb, tiles, ctr, epoch, status);
     return TDP_OK;
 }
 
@@ -370,11 +403,11 @@ template <typename R>
 tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
-    TDP_TRY(compact_u8(g, s.in_p, 1, t.n_pins, nullptr, s.ppins, s.pcnt));
-    TDP_TRY(compact_u8(g, s.cell_pf, 1, t.n_cells, nullptr, s.pcells, s.pcnt + 1));
+    const CmpPart cells{s.cell_pf, nullptr, s.pcells, s.pcnt + 1, t.n_cells, 1};
+    TDP_TRY(compact_flags(g, CmpPart{s.in_p, nullptr, s.ppins, s.pcnt, t.n_pins, 1}, &cells));
     TDP_CUDA(cudaMemsetAsync(s.pr_nbig, 0, sizeof(int32_t), g->stream));
     k_pair_records<R><<<148 * 4, 256, 0, g->stream>>>(t, s);
-    g->n_launch += 3;
+    g->n_launch += 2;
     TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
