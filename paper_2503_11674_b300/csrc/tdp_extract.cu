@@ -126,13 +126,6 @@ __global__ void k_sort_finish(State<R> s, const SortItem *items) {
     if (i < *s.nviol) s.viol[i] = (int)items[i].pin;
 }
 
-// flag of endpoint i: it fails
-template <typename R>
-__global__ void k_viol_flags(Topo t, State<R> s) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.n_ep) s.ep_flag[i] = (double)s.slack[t.ep[i]] < 0.0 ? 1 : 0;
-}
-
 // sort items of the failing endpoints listed by pin
 template <typename R>
 __global__ void k_viol_items(State<R> s, SortItem *items) {
@@ -223,6 +216,7 @@ __global__ void __launch_bounds__(kTopkWarps * 32, 16) k_topk(Topo t, State<R> s
     const int per = 32 / KP, g = lane / KP, gl = lane % KP, gb = g * KP;
     const unsigned gmask = (KP == 32 ? FULL : ((1u << KP) - 1u)) << gb;
     const R INF = (R)__longlong_as_double(0x7ff0000000000000ll);
+    chain_enter();
     const int nv = min(*s.nviol, n_cap);
     const int n_tasks = (nv + per - 1) / per;
     for (int task = blockIdx.x * kTopkWarps + w; task < n_tasks; task += gridDim.x * kTopkWarps) {
@@ -437,17 +431,19 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
     cudaStream_t st = g->stream;
     TDP_TRY(ensure_path_buffers<R>(g, K));
     // 1. failing endpoints sorted by (slack, pin)
-    TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
-    TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
     if (t.n_ep > 0 && n_endpoints < 0) {
         // all failing endpoints: their order does not change the paths, so
-        // they are listed by pin here and sorted when the paths are read
-        LaunchScope ls(g, KID_VIOL_SORT, 2);
-        k_viol_flags<R><<<div_up(t.n_ep, 256), 256, 0, st>>>(t, s);
-        TDP_TRY(compact_u8(g, s.ep_flag, 1, t.n_ep, t.ep, s.viol, s.nviol));
+        // they are listed by pin here and sorted when the paths are read; the
+        // flags are k_ep_wns's (written with the endpoint slacks), and the
+        // compaction writes the count and zeroes the path count
+        LaunchScope ls(g, KID_VIOL_SORT, 1);
+        TDP_TRY(compact_flags(g, CmpPart{s.ep_flag, t.ep, s.viol, s.nviol, t.n_ep, 1}, nullptr, nullptr,
+                              s.n_paths));
         g->viol_sorted = false;
-    } else if (t.n_ep > 0) {
-        TDP_TRY(sort_failing<R>(g));
+    } else {
+        TDP_CUDA(cudaMemsetAsync(s.nviol, 0, sizeof(int32_t), st));
+        TDP_CUDA(cudaMemsetAsync(s.n_paths, 0, sizeof(long long), st));
+        if (t.n_ep > 0) TDP_TRY(sort_failing<R>(g));
     }
     TDP_LAUNCH_CHECK();
     // 2. sidetrack lists: the next sweeps build K - 1 entries per node; if the
@@ -467,9 +463,8 @@ tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg) {
         while (KP < K) KP *= 2;
         int blocks = std::min(div_up(div_up(t.n_ep, 32 / KP), kTopkWarps), 148 * 16);
         LaunchScope ls(g, KID_TOPK);
-        k_topk<R><<<blocks, kTopkWarps * 32, 0, st>>>(t, s, K, KP, list_group(g->lists_valid_L), keep_nonneg,
-                                                      n_cap);
-        TDP_LAUNCH_CHECK();
+        TDP_CUDA(launch_pdl(k_topk<R>, blocks, kTopkWarps * 32, st, t, s, K, KP, list_group(g->lists_valid_L),
+                            keep_nonneg, n_cap));
     }
     return TDP_OK;
 }

@@ -139,6 +139,19 @@ __device__ __forceinline__ fx2 ldg(const fx2 *p) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The kernels after the forward sweep (endpoints, extraction, pair update,
+// loss) run as a chain of programmatic dependent launches: each lets the next
+// launch once all of its blocks have started and then waits, before its
+// first memory access, for every earlier kernel of the stream to finish.  So
+// a kernel's launch and block dispatch overlap the tail of the one before,
+// and the order of memory accesses is that of plain stream order (no read or
+// write moves ahead of the wait).  Launched without the attribute (after a
+// memset or an event wait, or in the level-graph mode), both are no-ops.
+__device__ __forceinline__ void chain_enter() {
+    pdl_trigger();
+    pdl_wait();
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
                               Args... args) {
@@ -661,8 +674,12 @@ struct CmpPart {
 };
 
 // the compaction of one flag array (b == nullptr) or of two in one launch
-// (flags padded to a multiple of 32 bytes)
-tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b = nullptr);
+// (flags padded to a multiple of 32 bytes); the launch also sets the device
+// words clear32 and clear64 to 0 where given (counters of the kernels after
+// it, so that the stream needs no memset between them).  Launched as a
+// programmatic dependent of the kernel before it (launch_chain).
+tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b = nullptr, int32_t *clear32 = nullptr,
+                         long long *clear64 = nullptr);
 inline tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map,
                              int32_t *out, int32_t *count) {
     return compact_flags(g, CmpPart{flags, map, out, count, n, val});

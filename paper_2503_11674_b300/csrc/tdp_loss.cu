@@ -133,6 +133,7 @@ template <typename R>
 __global__ void __launch_bounds__(kLossThreads) k_pp_fwd(Topo t, State<R> s, const R *__restrict__ x,
                                                          const R *__restrict__ y, double beta,
                                                          int kind, double *loss) {
+    chain_enter();
     const int np = s.pcnt[0];
     double acc = 0.0;
     for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < np; i += gridDim.x * kLossThreads) {
@@ -175,6 +176,7 @@ template <typename R, bool FWD>
 __global__ void __launch_bounds__(kLossThreads) k_pp_bwd_net(Topo t, State<R> s, const R *__restrict__ x,
                                                              const R *__restrict__ y, double beta, int kind,
                                                              double *loss) {
+    chain_enter();
     const int lane = threadIdx.x & 31;
     const int np = s.pcnt[0];
     const int npw = (np + 31) >> 5;
@@ -235,6 +237,7 @@ constexpr int kCellBlocks = 148 * 4;
 template <typename R>
 __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const double *gscale,
                                                      R *__restrict__ gx, R *__restrict__ gy) {
+    chain_enter();
     if (blockIdx.x < kCellBlocks) {
         const int nc = s.pcnt[1];
         const double g = gscale ? *gscale : 1.0;
@@ -266,9 +269,8 @@ __global__ void __launch_bounds__(256) k_pp_bwd_cell(Topo t, State<R> s, const d
 template <typename R>
 tdp_status loss_fwd_impl(tdp_graph *g, const R *x, const R *y, double beta, double *loss) {
     LaunchScope ls(g, KID_PP_FWD);
-    k_pp_fwd<R><<<kLossBlocks, kLossThreads, 0, g->stream>>>(g->topo, state<R>(g), x, y, beta, g->loss_kind,
-                                                              loss);
-    TDP_LAUNCH_CHECK();
+    TDP_CUDA(launch_pdl(k_pp_fwd<R>, kLossBlocks, kLossThreads, g->stream, g->topo, state<R>(g), x, y, beta,
+                        g->loss_kind, loss));
     return TDP_OK;
 }
 
@@ -279,15 +281,14 @@ tdp_status loss_bwd_impl(tdp_graph *g, const R *x, const R *y, double beta, cons
     State<R> &s = state<R>(g);
     {
         LaunchScope ls(g, KID_PP_BWD_NET);
-        k_pp_bwd_net<R, false><<<kLossBlocks, kLossThreads, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind,
-                                                                             nullptr);
+        TDP_CUDA(launch_pdl(k_pp_bwd_net<R, false>, kLossBlocks, kLossThreads, g->stream, t, s, x, y, beta,
+                            g->loss_kind, (double *)nullptr));
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
         const int zero_blocks = div_up(std::max(t.n_cells, 1), 256);
-        k_pp_bwd_cell<R><<<kCellBlocks + zero_blocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
+        TDP_CUDA(launch_pdl(k_pp_bwd_cell<R>, kCellBlocks + zero_blocks, 256, g->stream, t, s, gs, gx, gy));
     }
-    TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
 
@@ -300,14 +301,14 @@ static tdp_status loss_fwd_bwd_impl(tdp_graph *g, const R *x, const R *y, double
     State<R> &s = state<R>(g);
     {
         LaunchScope ls(g, KID_PP_FWD_BWD);
-        k_pp_bwd_net<R, true><<<kLossBlocks, kLossThreads, 0, g->stream>>>(t, s, x, y, beta, g->loss_kind, loss);
+        TDP_CUDA(launch_pdl(k_pp_bwd_net<R, true>, kLossBlocks, kLossThreads, g->stream, t, s, x, y, beta,
+                            g->loss_kind, loss));
     }
     {
         LaunchScope ls(g, KID_PP_BWD_CELL);
         const int zero_blocks = div_up(std::max(t.n_cells, 1), 256);
-        k_pp_bwd_cell<R><<<kCellBlocks + zero_blocks, 256, 0, g->stream>>>(t, s, gs, gx, gy);
+        TDP_CUDA(launch_pdl(k_pp_bwd_cell<R>, kCellBlocks + zero_blocks, 256, g->stream, t, s, gs, gx, gy));
     }
-    TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
 

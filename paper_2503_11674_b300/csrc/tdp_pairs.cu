@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int per = 32 / KP, g = lane / KP, r = lane % KP;
+    chain_enter();
     const int nv = min(*s.nviol, n_cap);
     const double wns = s.wns_tns[0];
     if (!(wns < 0.0)) return;
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
 // which then scans every pin, finds only the new pairs.
 template <typename R>
 __global__ void k_pair_finish_p(State<R> s, double w1) {
+    chain_enter();
     const int np = s.pcnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         const int p = s.ppins[i];
@@ -175,6 +177,7 @@ __device__ __forceinline__ void pair_finish_one(const Topo &t, State<R> &s, int 
 // touched when a walk raised its maximum (every q is finite).
 template <typename R>
 __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
+    chain_enter();
     const longlong2 *m2 = reinterpret_cast<const longlong2 *>(s.maxq);
     const int half = n_pins / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < half; i += gridDim.x * blockDim.x) {
@@ -302,9 +305,14 @@ __device__ __forceinline__ int cmp_look_back(unsigned long long *tiles, int tile
 
 __global__ void __launch_bounds__(kCmpThreads) k_compact(CmpPart p0, CmpPart p1, int nb0, int nb,
                                                         unsigned long long *tiles, unsigned *ctr, unsigned epoch,
-                                                        unsigned *status) {
+                                                        unsigned *status, int32_t *clear32, long long *clear64) {
     __shared__ int sh[32];
     __shared__ int s_tile, s_prefix;
+    chain_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (clear32) *clear32 = 0;
+        if (clear64) *clear64 = 0;
+    }
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], 1u);
     __syncthreads();
     const int tile = s_tile;
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_compact(CmpPart p0, CmpPart p1,
     }
 }
 
-tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b) {
+tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b, int32_t *clear32, long long *clear64) {
     unsigned long long *tiles = g->prec == TDP_FP32 ? g->s32.cmp_tiles : g->s64.cmp_tiles;
     unsigned *ctr = g->prec == TDP_FP32 ? g->s32.cmp_ctr : g->s64.cmp_ctr;
     unsigned *status = g->prec == TDP_FP32 ? g->s32.gsync + 1 : g->s64.gsync + 1;
@@ -358,7 +366,8 @@ tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b) {
         return TDP_ERR_INVALID;
     }
     const unsigned epoch = ++g->cmp_epoch;
-    k_compact<<<nb, kCmpThreads, 0, g->stream>>>(a, b ? *b : a, nb0, nb, tiles, ctr, epoch, status);
+    TDP_CUDA(launch_pdl(k_compact, nb, kCmpThreads, g->stream, a, b ? *b : a, nb0, nb, tiles, ctr, epoch, status,
+                        clear32, clear64));
     return TDP_OK;
 }
 
@@ -370,6 +379,7 @@ tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b) {
 // most the net's fanout records.
 template <typename R>
 __global__ void k_pair_records(Topo t, State<R> s) {
+    chain_enter();
     const int np = s.pcnt[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         const int p = s.ppins[i];
@@ -404,11 +414,9 @@ tdp_status compact_pairs(tdp_graph *g) {
     const Topo &t = g->topo;
     State<R> &s = state<R>(g);
     const CmpPart cells{s.cell_pf, nullptr, s.pcells, s.pcnt + 1, t.n_cells, 1};
-    TDP_TRY(compact_flags(g, CmpPart{s.in_p, nullptr, s.ppins, s.pcnt, t.n_pins, 1}, &cells));
-    TDP_CUDA(cudaMemsetAsync(s.pr_nbig, 0, sizeof(int32_t), g->stream));
-    k_pair_records<R><<<148 * 4, 256, 0, g->stream>>>(t, s);
+    TDP_TRY(compact_flags(g, CmpPart{s.in_p, nullptr, s.ppins, s.pcnt, t.n_pins, 1}, &cells, s.pr_nbig));
+    TDP_CUDA(launch_pdl(k_pair_records<R>, 148 * 4, 256, g->stream, t, s));
     g->n_launch += 2;
-    TDP_LAUNCH_CHECK();
     return TDP_OK;
 }
 
@@ -427,14 +435,13 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
         int KP = 1;
         while (KP < g->K) KP *= 2;
         const int blocks = std::min(div_up(div_up(t.n_ep, 32 / KP), kWalkWarps), 148 * 16);
-        k_pair_walk<R><<<blocks, kWalkWarps * 32, 0, g->stream>>>(t, s, g->K, KP, n_cap);
+        TDP_CUDA(launch_pdl(k_pair_walk<R>, blocks, kWalkWarps * 32, g->stream, t, s, g->K, KP, n_cap));
     }
     {
         LaunchScope ls(g, KID_PAIR_FINISH, 2);
-        k_pair_finish_p<R><<<148 * 4, 256, 0, g->stream>>>(s, w1);
-        k_pair_finish<R><<<148 * 8, 256, 0, g->stream>>>(t, s, t.n_pins, w0, w1);
+        TDP_CUDA(launch_pdl(k_pair_finish_p<R>, 148 * 4, 256, g->stream, s, w1));
+        TDP_CUDA(launch_pdl(k_pair_finish<R>, 148 * 8, 256, g->stream, t, s, t.n_pins, w0, w1));
     }
-    TDP_LAUNCH_CHECK();
     return compact_pairs<R>(g);
 }
 

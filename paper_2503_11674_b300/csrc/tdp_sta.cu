@@ -8,9 +8,9 @@
 //                level by level (thread per combinational cell: max / argmax
 //                over its inputs), and, when asked, each cell's sidetrack list
 //                for report_timing_endpoint; grid-wide barrier between levels
-//   k_ep_wns     endpoints: arrival, required time (T) and slack, and WNS /
-//                TNS over them (FP64, fixed-order reduction); they need the
-//                forward sweep only
+//   k_ep_wns     endpoints: arrival, required time (T), slack and the
+//                failing flag, and WNS / TNS over them (FP64, fixed-order
+//                reduction); they need the forward sweep only
 //   k_bwd_sweep  the backward sweep in one cooperative launch: required times
 //                of the nets driven from each level, deepest first (a net of
 //                at most 8 sinks on an aligned group of 1, 2 or 4 lanes, a
@@ -1325,11 +1325,12 @@ __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, in
 constexpr int kRedThreads = 256;
 constexpr int kRedFinal = 1024;  // chunk partials the last block combines at once (a power of 2)
 constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
-constexpr int kBwdOverlapNum = 9;      // overlapped backward sweep: 9/16 of the resident grid
 
 // Endpoints (FF D and PO pins): arrival = the driver's arrival + the pin's
-// Elmore delay, required time = T, slack = T - arrival; then WNS = min over
-// endpoints with negative slack, TNS = their sum (FP64; Eqs. (2)-(4)).
+// Elmore delay, required time = T, slack = T - arrival, and whether the
+// endpoint fails (slack < 0, the flags the extraction compacts into its list
+// of failing endpoints); then WNS = min over endpoints with negative slack,
+// TNS = their sum (FP64; Eqs. (2)-(4)).
 // FP64 arithmetic is slow on this GPU, so the sums run as trees of fixed
 // shape: a warp takes a chunk of kRedChunk endpoints (two per lane, then a
 // butterfly over the lanes), and the last block to finish combines the
@@ -1343,6 +1344,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
     static_assert(kRedChunk == 64, "two endpoints per lane");
     __shared__ bool last;
     __shared__ double part[2 * kRedFinal];
+    chain_enter();
     const int lane = threadIdx.x & 31;
     const int n_chunks = div_up_dev(t.n_ep, kRedChunk);
     const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1375,6 +1377,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
             s.req[pd[u].x] = rq;
             s.slack[pd[u].x] = sl;
             const double v = (double)sl;
+            s.ep_flag[i] = v < 0.0 ? 1 : 0;
             if (v < 0.0) {
                 mn[u] = v;
                 sm[u] = v;
@@ -1632,10 +1635,11 @@ static tdp_status backward(tdp_graph *g, int sms = 0) {
     }
     bool done = false;
     if (g->single_launch) {
-        // beside extraction, the pair update and the loss, the sweep leaves
-        // SMs to them: kBwdOverlapNum / 16 of the resident grid (83 of 148
-        // blocks; measured at 1.2M cells, a step took 1.189, 1.157, 1.111,
-        // 1.135, 1.171 and 1.270 ms for 7/16 to 12/16)
+        // beside the forward sweep (sms, from bwd_split) or beside
+        // extraction, the pair update and the loss (bwd_share / 16 of the
+        // resident grid, 9/16 by default: 83 of 148 blocks; measured at 1.2M
+        // cells, a step took 1.189, 1.157, 1.111, 1.135, 1.171 and 1.270 ms
+        // for 7/16 to 12/16), the sweep leaves SMs to the rest
         int grid = coop_grid(g, k_bwd_sweep<R>, kBwdThreads);
         if (grid > 0 && g->overlap_bwd) grid = sms > 0 ? std::min(grid, sms) : std::max(1, grid * g->bwd_share / 16);
         if (grid > 0) {
@@ -1669,9 +1673,9 @@ static tdp_status finish_sweeps(tdp_graph *g, bool bwd = true) {
     {
         LaunchScope ls(g, KID_EP_WNS);
         const int chunks = div_up(std::max(g->topo.n_ep, 1), kRedChunk);
-        k_ep_wns<R><<<div_up(chunks, kRedThreads / 32), kRedThreads, 0, g->stream>>>(g->topo, state<R>(g));
+        TDP_CUDA(launch_pdl(k_ep_wns<R>, div_up(chunks, kRedThreads / 32), kRedThreads, g->stream, g->topo,
+                            state<R>(g)));
     }
-    TDP_LAUNCH_CHECK();
     return bwd ? backward<R>(g) : TDP_OK;
 }
 
@@ -1681,11 +1685,11 @@ static tdp_status finish_sweeps(tdp_graph *g, bool bwd = true) {
 // that it ends about when the forward sweep and the rest of the iteration
 // do; at most as many as leave every forward block at most two more chunks
 // of a level than on all SMs.  Measured with 28-warp blocks at 1.2M cells
-// (K = 16; 24 SMs here): a step took 0.953, 0.885, 0.837, 0.837 ms with 16,
-// 22, 24, 26 SMs (0.848 ms with 16-warp blocks on 32 SMs, 0.931 ms with the
-// backward sweep after the forward sweep); at 3.3M cells (K = 32; 45 SMs
-// here), 2.92, 2.94, 2.89 ms with 24, 28, 40 SMs against 3.14 ms.
-constexpr double kBwdRounds = 1.8;
+// (K = 16; 26 SMs here, 1.58 rounds a level): a step took 0.803, 0.789,
+// 0.791, 0.793, 0.796 ms with 24, 26, 28, 30, 32 SMs (0.931 ms once with the
+// backward sweep after the forward sweep); at 3.3M cells (K = 32; 43 SMs
+// here), 2.94, 2.82, 2.82, 2.84, 2.85 ms with 36, 41, 44, 48, 52 SMs.
+constexpr double kBwdRounds = 1.6;
 static int bwd_split(const tdp_graph *g) {
     const Levels &lv = g->lv;
     const int n = std::max(g->n_sm, 2);
