@@ -174,16 +174,29 @@ __device__ __forceinline__ void pair_finish_one(const Topo &t, State<R> &s, int 
 }
 
 // Every pin, two a 16-byte load of the maxima, on a resident grid: a sink is
-// touched when a walk raised its maximum (every q is finite).
+// touched when a walk raised its maximum (every q is finite).  A thread
+// issues kFinishLoads of those loads before it looks at any (the updates
+// between them would otherwise wait for each load in turn).
+constexpr int kFinishLoads = 4;
 template <typename R>
 __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
     chain_enter();
     const longlong2 *m2 = reinterpret_cast<const longlong2 *>(s.maxq);
     const int half = n_pins / 2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < half; i += gridDim.x * blockDim.x) {
-        const longlong2 m = m2[i];
-        if (m.x != LLONG_MIN) pair_finish_one(t, s, 2 * i, m.x, w0, w1);
-        if (m.y != LLONG_MIN) pair_finish_one(t, s, 2 * i + 1, m.y, w0, w1);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < half; i0 += kFinishLoads * stride) {
+        longlong2 m[kFinishLoads];
+#pragma unroll
+        for (int u = 0; u < kFinishLoads; ++u) {
+            const int i = i0 + u * stride;
+            m[u] = i < half ? __ldcg(m2 + i) : make_longlong2(LLONG_MIN, LLONG_MIN);
+        }
+#pragma unroll
+        for (int u = 0; u < kFinishLoads; ++u) {
+            const int i = i0 + u * stride;
+            if (m[u].x != LLONG_MIN) pair_finish_one(t, s, 2 * i, m[u].x, w0, w1);
+            if (m[u].y != LLONG_MIN) pair_finish_one(t, s, 2 * i + 1, m[u].y, w0, w1);
+        }
     }
     if ((n_pins & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const long long m = s.maxq[n_pins - 1];

@@ -1323,7 +1323,7 @@ __global__ void __launch_bounds__(kLvThreads) k_bwd_level(Topo t, State<R> s, in
 // ---------------------------------------------------------- WNS / TNS ---
 
 constexpr int kRedThreads = 256;
-constexpr int kRedFinal = 1024;  // chunk partials the last block combines at once (a power of 2)
+constexpr int kRedFinal = 4 * kRedThreads;  // chunk partials the last block combines a round
 constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
 
 // Endpoints (FF D and PO pins): arrival = the driver's arrival + the pin's
@@ -1334,16 +1334,18 @@ constexpr int kCoopMaxBlocks = 1024;  // cap on the grid of a cooperative launch
 // FP64 arithmetic is slow on this GPU, so the sums run as trees of fixed
 // shape: a warp takes a chunk of kRedChunk endpoints (two per lane, then a
 // butterfly over the lanes), and the last block to finish combines the
-// chunk partials in a pairwise tree over their index (kRedFinal at a time,
-// those in chunk order).  The result does not depend on the grid, the block
-// size or scheduling.  Needs the forward sweep only.
+// chunk partials in rounds of kRedFinal, in chunk order: in a round, thread
+// t adds chunks 4t .. 4t + 3 as pairs of pairs, a warp its lanes' sums by a
+// butterfly, and one thread the 8 warps' sums as a pairwise tree.  The
+// result does not depend on the grid or scheduling.  Needs the forward sweep only.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
     using AC = Acc<R>;
     using A = typename AC::T;
     static_assert(kRedChunk == 64, "two endpoints per lane");
+    static_assert(kRedThreads == 256, "8 warp sums in the last block's tree");
     __shared__ bool last;
-    __shared__ double part[2 * kRedFinal];
+    __shared__ double2 wsum[kRedThreads / 32];
     chain_enter();
     const int lane = threadIdx.x & 31;
     const int n_chunks = div_up_dev(t.n_ep, kRedChunk);
@@ -1402,23 +1404,32 @@ __global__ void __launch_bounds__(kRedThreads) k_ep_wns(Topo t, State<R> s) {
     if (!last) return;
     __threadfence();
     double bm = 0.0, bs = 0.0;
+    const double2 *parts = reinterpret_cast<const double2 *>(s.red_part);
     for (int k0 = 0; k0 < n_chunks; k0 += kRedFinal) {
-        for (int k = threadIdx.x; k < kRedFinal; k += blockDim.x) {
-            const bool in = k0 + k < n_chunks;
-            part[2 * k] = in ? ldcg(&s.red_part[2 * (k0 + k)]) : 0.0;
-            part[2 * k + 1] = in ? ldcg(&s.red_part[2 * (k0 + k) + 1]) : 0.0;
+        double2 q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + 4 * threadIdx.x + j;
+            q[j] = k < n_chunks ? __ldcg(parts + k) : make_double2(0.0, 0.0);
         }
+        double m = fmin(fmin(q[0].x, q[1].x), fmin(q[2].x, q[3].x));
+        double a = (q[0].y + q[1].y) + (q[2].y + q[3].y);
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+        }
+        if (lane == 0) wsum[threadIdx.x >> 5] = make_double2(m, a);
         __syncthreads();
-        for (int h = kRedFinal / 2; h > 0; h >>= 1) {  // pairwise tree: k with k + h
-            for (int k = threadIdx.x; k < h; k += blockDim.x) {
-                part[2 * k] = fmin(part[2 * k], part[2 * (k + h)]);
-                part[2 * k + 1] += part[2 * (k + h) + 1];
-            }
-            __syncthreads();
-        }
         if (threadIdx.x == 0) {
-            bm = fmin(bm, part[0]);
-            bs += part[1];
+            double2 w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] = wsum[k];
+#pragma unroll
+            for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                for (int k = 0; k < 8; k += 2 * h) w[k] = make_double2(fmin(w[k].x, w[k + h].x), w[k].y + w[k + h].y);
+            bm = fmin(bm, w[0].x);
+            bs += w[0].y;
         }
         __syncthreads();
     }
