@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 512392960, "sources": SWEEP_SOURCES, "sha256": "2316c6df2e70d718a54b3bda6dcc7f2bed5722b572ed1444dd3d1509669e3857"},
-        "bwd_sweep": {"bytes": 128860160, "sources": SWEEP_SOURCES, "sha256": "2316c6df2e70d718a54b3bda6dcc7f2bed5722b572ed1444dd3d1509669e3857"},
-        "pair_walk": {"bytes": 22055552, "sources": PAIR_SOURCES, "sha256": "07ab00a35b282f6aabdc1661bf32154af40c1941b66460b7c35639ec004187ae"},
+        "fwd_sweep": {"bytes": 511803904, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
+        "bwd_sweep": {"bytes": 129047552, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
+        "pair_walk": {"bytes": 22053632, "sources": PAIR_SOURCES, "sha256": "346f595efdd82c39ed3ed917aa03e5bf98c2a80b173fb5cd5de3abffc36b257f"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2478127320, "sources": SWEEP_SOURCES, "sha256": "2316c6df2e70d718a54b3bda6dcc7f2bed5722b572ed1444dd3d1509669e3857"},
+        "fwd_sweep": {"bytes": 2478406392, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
     },
 }
 
