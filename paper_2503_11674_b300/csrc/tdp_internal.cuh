@@ -411,7 +411,7 @@ struct State {
     int2 *pred = nullptr;         // [n_nets] worst input pin of the driving cell (-1: startpoint), its net
     int32_t *plen = nullptr;      // [n_nets] pins from the driver back to its startpoint
     double *T = nullptr;          // device clock period
-    unsigned *gsync = nullptr;    // [2] grid barrier counter, sticky timeout status
+    unsigned *gsync = nullptr;    // [4] forward barrier count, sticky timeout status, backward barrier count
     double *wns_tns = nullptr;    // [2]
     double *red_part = nullptr;   // [2 * chunks] WNS / TNS partials per kRedChunk endpoints
     unsigned *red_count = nullptr;
@@ -591,9 +591,10 @@ inline State<double> &state<double>(tdp_graph *g) { return g->s64; }
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T);
 // the forward sweep building the lists; leave_sms: SMs to leave to a
-// backward sweep that runs at the same time (single launch)
+// backward sweep that runs at the same time (single launch); after_rc: net RC
+// is the stream's last kernel and has zeroed the sweep's barrier word
 template <typename R>
-tdp_status forward_lists(tdp_graph *g, int leave_sms = 0);
+tdp_status forward_lists(tdp_graph *g, int leave_sms = 0, bool after_rc = false);
 template <typename R>
 tdp_status extract_impl(tdp_graph *g, int n_endpoints, int K, int keep_nonneg);
 template <typename R>

@@ -98,10 +98,13 @@ __device__ __forceinline__ void pair_vec(const State<R> &s, const R *x, const R 
 
 // The loss total from each thread's FP64 partial, in a fixed order: a
 // butterfly in the warp, the warps of the block in order, then the last
-// block to finish adds the blocks' partials (lanes strided over them, a
-// butterfly), so the result depends on neither scheduling nor timing.
+// block to finish adds the blocks' partials (thread t the partials t,
+// t + kLossThreads, ... in order, then a butterfly in the warp and the warps
+// in order), so the result depends on neither scheduling nor timing.  The
+// last block issues its loads of the partials before it adds any.
 template <typename R>
 __device__ __forceinline__ void loss_total(const State<R> &s, double acc, double beta, double *loss) {
+    constexpr int kPer = (kLossBlocks + kLossThreads - 1) / kLossThreads;  // partials a thread
     __shared__ double sh[kLossThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -116,16 +119,27 @@ __device__ __forceinline__ void loss_total(const State<R> &s, double acc, double
         last = atomicAdd(s.loss_count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x < 32) {
-        __threadfence();
-        const volatile double *part = s.loss_part;
-        double v = 0.0;
-        for (int k = lane; k < (int)gridDim.x; k += 32) v += part[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-            *loss = beta * v;
-            *s.loss_count = 0u;
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int k0 = 0; k0 < (int)gridDim.x; k0 += kPer * kLossThreads) {
+        double q[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int k = k0 + j * kLossThreads + (int)threadIdx.x;
+            q[j] = k < (int)gridDim.x ? __ldcg(&s.loss_part[k]) : 0.0;
         }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) v += q[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wib] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < kLossThreads / 32; ++k) b += sh[k];
+        *loss = beta * b;
+        *s.loss_count = 0u;
     }
 }
 

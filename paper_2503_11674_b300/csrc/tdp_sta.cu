@@ -96,7 +96,10 @@ template <typename R>
 __global__ void __launch_bounds__(kRcThreads) k_net_rc(Topo t, State<R> s, const R *__restrict__ x,
                                                        const R *__restrict__ y, double T, R r, R c,
                                                        R d0, int n_small_blocks, Inc inc) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *s.T = T;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *s.T = T;
+        s.gsync[0] = 0u;  // the forward sweep's barrier word (the sweep follows)
+    }
     const bool incr = inc.cur != 0;
     if ((int)blockIdx.x < n_small_blocks) {
         const int e = blockIdx.x * kRcThreads + threadIdx.x;
@@ -1579,16 +1582,18 @@ static void (*fwd_kernel(int L))(Topo, State<R>, GridSync, const int *) {
     }
 }
 
-// The single-launch forward sweep from level *from_dev (NULL: level 1).
+// The single-launch forward sweep from level *from_dev (NULL: level 1);
+// count_zeroed: the barrier word was set to 0 by the kernel before it (net
+// RC), so the stream needs no memset.
 template <typename R>
-static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev) {
+static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev, bool count_zeroed = false) {
     State<R> &s = state<R>(g);
     GridSync gs;
     gs.count = s.gsync;
     gs.status = s.gsync + 1;
     gs.timeout_ns = kSyncTimeoutNs;
     LaunchScope ls(g, KID_FWD_SWEEP, 1, g->stream);
-    TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
+    if (!count_zeroed) TDP_CUDA(cudaMemsetAsync(gs.count, 0, sizeof(unsigned), g->stream));
     TDP_CUDA(launch_coop(fwd_kernel<R>(g->list_L), grid, kFwdThreads, warp_list_smem<R>(g->list_L, kFwdThreads),
                          g->stream, g->topo, s, gs, from_dev));
     return TDP_OK;
@@ -1596,16 +1601,17 @@ static tdp_status launch_fwd_sweep(tdp_graph *g, int grid, const int *from_dev) 
 
 // Forward sweep, building sidetrack lists of length g->list_L (0: none): one
 // cooperative launch, or one graph replay of the level launches.  Run again,
-// it writes the same arrival times.
+// it writes the same arrival times.  after_rc: net RC was the stream's last
+// kernel (it zeroes the sweep's barrier word).
 template <typename R>
-tdp_status forward_lists(tdp_graph *g, int leave_sms) {
+tdp_status forward_lists(tdp_graph *g, int leave_sms, bool after_rc) {
     State<R> &s = state<R>(g);
     if (g->list_L > 0 && !s.blist) TDP_TRY(dalloc(g, &s.blist, (size_t)g->topo.n_nets * kMaxK));
     if (g->single_launch) {
         if (g->topo.depth == 0) return TDP_OK;
         const int grid =
             coop_grid(g, fwd_kernel<R>(g->list_L), kFwdThreads, warp_list_smem<R>(g->list_L, kFwdThreads));
-        if (grid > 0) return launch_fwd_sweep<R>(g, std::max(1, grid - leave_sms), nullptr);
+        if (grid > 0) return launch_fwd_sweep<R>(g, std::max(1, grid - leave_sms), nullptr, after_rc);
         g->single_launch = false;  // no resident grid: per-level launches from now on
     }
     if (!g->fwd_graph || g->fwd_graph_L != g->list_L) {
@@ -1718,8 +1724,8 @@ static int bwd_split(const tdp_graph *g) {
     return cap;
 }
 
-template tdp_status forward_lists<float>(tdp_graph *, int);
-template tdp_status forward_lists<double>(tdp_graph *, int);
+template tdp_status forward_lists<float>(tdp_graph *, int, bool);
+template tdp_status forward_lists<double>(tdp_graph *, int, bool);
 
 template <typename R>
 tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
@@ -1741,10 +1747,10 @@ tdp_status propagate_impl(tdp_graph *g, const R *x, const R *y, double T) {
         if (g->bwd_sms == 0) g->bwd_sms = bwd_split(g);
         TDP_CUDA(cudaEventRecord(g->ev_bwd_go, g->stream));
         TDP_TRY(backward<R>(g, g->bwd_sms));
-        TDP_TRY(forward_lists<R>(g, g->bwd_sms));
+        TDP_TRY(forward_lists<R>(g, g->bwd_sms, true));
         TDP_TRY(finish_sweeps<R>(g, false));
     } else {
-        TDP_TRY(forward_lists<R>(g));
+        TDP_TRY(forward_lists<R>(g, 0, true));
         TDP_TRY(finish_sweeps<R>(g));
     }
     if (s.yprev) {  // incremental propagation is in use: keep these positions
