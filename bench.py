@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 511803904, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
-        "bwd_sweep": {"bytes": 129047552, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
-        "pair_walk": {"bytes": 22053632, "sources": PAIR_SOURCES, "sha256": "346f595efdd82c39ed3ed917aa03e5bf98c2a80b173fb5cd5de3abffc36b257f"},
+        "fwd_sweep": {"bytes": 511739904, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
+        "bwd_sweep": {"bytes": 128792320, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
+        "pair_walk": {"bytes": 22066944, "sources": PAIR_SOURCES, "sha256": "a299f06ac0e327f11bb854c7a7bb95b52f1cbe2d0068de3334c37235860777d8"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2478406392, "sources": SWEEP_SOURCES, "sha256": "3a66172e18dbecdf9e73fd9fa91328194959557815a22c690459421ff519042b"},
+        "fwd_sweep": {"bytes": 2477957704, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
     },
 }
 
