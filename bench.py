@@ -170,7 +170,7 @@ PROFILED_TRAFFIC = {
     ("1.2M", 16): {
         "fwd_sweep": {"bytes": 511739904, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
         "bwd_sweep": {"bytes": 128792320, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
-        "pair_walk": {"bytes": 22066944, "sources": PAIR_SOURCES, "sha256": "a299f06ac0e327f11bb854c7a7bb95b52f1cbe2d0068de3334c37235860777d8"},
+        "pair_walk": {"bytes": 22054656, "sources": PAIR_SOURCES, "sha256": "a58e4cf53b8e4f91cbefcbff75dc1697e6b57f38c6b27b33b552721c394d7fbf"},
     },
     ("stress", 32): {
         "fwd_sweep": {"bytes": 2477957704, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},

@@ -132,59 +132,56 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 16) k_pair_walk(Topo t, State
     }
 }
 
-// The sinks already in P first, from the list of P's sinks of the last
-// compaction (a thread a listed sink), so that the FP64 arithmetic of the
-// update runs on dense warps; their accumulators are reset, so k_pair_finish,
-// which then scans every pin, finds only the new pairs.
+// The update of one touched sink p not yet in P (the rule above): it joins
+// P with w = w0 + w1 * (sum q - max q), and its net and cells get the loss's
+// flags.
 template <typename R>
-__global__ void k_pair_finish_p(State<R> s, double w1) {
-    chain_enter();
-    const int np = s.pcnt[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-        const int p = s.ppins[i];
-        if (s.maxq[p] == LLONG_MIN) continue;
-        const double sq = (double)s.sumq[p] / kQScale;
-        s.w[p] = (R)((double)s.w[p] + w1 * sq);
-        s.sumq[p] = 0;
-        s.maxq[p] = LLONG_MIN;
-    }
-}
-
-// The update of one touched sink p (the rule above).
-template <typename R>
-__device__ __forceinline__ void pair_finish_one(const Topo &t, State<R> &s, int p, long long mx, double w0,
-                                                double w1) {
+__device__ __forceinline__ void pair_new(const Topo &t, State<R> &s, int p, long long mx, double w0, double w1) {
     const double sq = (double)s.sumq[p] / kQScale;
-    if (s.in_p[p]) {
-        s.w[p] = (R)((double)s.w[p] + w1 * sq);
-    } else {
-        const double mq = (double)mx / kQScale;
-        s.w[p] = (R)(w0 + w1 * (sq - mq));
-        s.in_p[p] = 1;
-        atomicAdd((unsigned long long *)s.n_pairs, 1ull);
-        // flags for the loss lists (set only; threads of one net write the same value)
-        const int e = t.pin_net[p];
-        const int a = t.net_ptr[e];
-        s.net_pf[e] = t.net_ptr[e + 1] - a - 1 <= kBigFanout ? kPfSmall : kPfLarge;
-        s.cell_pf[t.pin_cell[p]] = 1;
-        s.cell_pf[t.pin_cell[a]] = 1;
-    }
+    const double mq = (double)mx / kQScale;
+    s.w[p] = (R)(w0 + w1 * (sq - mq));
+    s.in_p[p] = 1;
+    atomicAdd((unsigned long long *)s.n_pairs, 1ull);
+    // flags for the loss lists (set only; threads of one net write the same value)
+    const int e = t.pin_net[p];
+    const int a = t.net_ptr[e];
+    s.net_pf[e] = t.net_ptr[e + 1] - a - 1 <= kBigFanout ? kPfSmall : kPfLarge;
+    s.cell_pf[t.pin_cell[p]] = 1;
+    s.cell_pf[t.pin_cell[a]] = 1;
     s.sumq[p] = 0;
     s.maxq[p] = LLONG_MIN;
 }
 
-// Every pin, two a 16-byte load of the maxima, on a resident grid: a sink is
-// touched when a walk raised its maximum (every q is finite).  A thread
-// issues kFinishLoads of those loads before it looks at any (the updates
-// between them would otherwise wait for each load in turn).
+// The rule on every touched sink, in one launch with two roles on disjoint
+// sinks.  Blocks [0, p_blocks) take the sinks already in P from the list of
+// the last compaction (a thread a listed sink, so that the FP64 arithmetic
+// runs on dense warps): w += w1 * sum q.  The other blocks scan every pin's
+// maximum, two a 16-byte load, kFinishLoads loads issued before a thread
+// looks at any: a sink is touched when a walk raised its maximum (every q is
+// finite), and a touched sink not in P is new.  A sink in P is left to the
+// first role whichever of its maxima the scan reads (in_p does not change
+// for it here), so no sink is updated twice.
 constexpr int kFinishLoads = 4;
 template <typename R>
-__global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1) {
+__global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double w1, int p_blocks) {
     chain_enter();
+    if ((int)blockIdx.x < p_blocks) {
+        const int np = s.pcnt[0];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += p_blocks * blockDim.x) {
+            const int p = s.ppins[i];
+            if (s.maxq[p] == LLONG_MIN) continue;
+            const double sq = (double)s.sumq[p] / kQScale;
+            s.w[p] = (R)((double)s.w[p] + w1 * sq);
+            s.sumq[p] = 0;
+            s.maxq[p] = LLONG_MIN;
+        }
+        return;
+    }
+    const int bid = (int)blockIdx.x - p_blocks;
     const longlong2 *m2 = reinterpret_cast<const longlong2 *>(s.maxq);
     const int half = n_pins / 2;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < half; i0 += kFinishLoads * stride) {
+    const int stride = ((int)gridDim.x - p_blocks) * blockDim.x;
+    for (int i0 = bid * blockDim.x + threadIdx.x; i0 < half; i0 += kFinishLoads * stride) {
         longlong2 m[kFinishLoads];
 #pragma unroll
         for (int u = 0; u < kFinishLoads; ++u) {
@@ -194,13 +191,13 @@ __global__ void k_pair_finish(Topo t, State<R> s, int n_pins, double w0, double 
 #pragma unroll
         for (int u = 0; u < kFinishLoads; ++u) {
             const int i = i0 + u * stride;
-            if (m[u].x != LLONG_MIN) pair_finish_one(t, s, 2 * i, m[u].x, w0, w1);
-            if (m[u].y != LLONG_MIN) pair_finish_one(t, s, 2 * i + 1, m[u].y, w0, w1);
+            if (m[u].x != LLONG_MIN && !s.in_p[2 * i]) pair_new(t, s, 2 * i, m[u].x, w0, w1);
+            if (m[u].y != LLONG_MIN && !s.in_p[2 * i + 1]) pair_new(t, s, 2 * i + 1, m[u].y, w0, w1);
         }
     }
-    if ((n_pins & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const long long m = s.maxq[n_pins - 1];
-        if (m != LLONG_MIN) pair_finish_one(t, s, n_pins - 1, m, w0, w1);
+    if ((n_pins & 1) && bid == 0 && threadIdx.x == 0) {
+        const long long m = __ldcg(&s.maxq[n_pins - 1]);
+        if (m != LLONG_MIN && !s.in_p[n_pins - 1]) pair_new(t, s, n_pins - 1, m, w0, w1);
     }
 }
 
@@ -451,9 +448,9 @@ tdp_status update_pairs_impl(tdp_graph *g, double w0, double w1) {
         TDP_CUDA(launch_pdl(k_pair_walk<R>, blocks, kWalkWarps * 32, g->stream, t, s, g->K, KP, n_cap));
     }
     {
-        LaunchScope ls(g, KID_PAIR_FINISH, 2);
-        TDP_CUDA(launch_pdl(k_pair_finish_p<R>, 148 * 4, 256, g->stream, s, w1));
-        TDP_CUDA(launch_pdl(k_pair_finish<R>, 148 * 8, 256, g->stream, t, s, t.n_pins, w0, w1));
+        LaunchScope ls(g, KID_PAIR_FINISH);
+        constexpr int p_blocks = 148 * 2;
+        TDP_CUDA(launch_pdl(k_pair_finish<R>, p_blocks + 148 * 8, 256, g->stream, t, s, t.n_pins, w0, w1, p_blocks));
     }
     return compact_pairs<R>(g);
 }
