@@ -168,12 +168,12 @@ SWEEP_SOURCES = ["paper_2503_11674_b300/csrc/tdp_sta.cu", "paper_2503_11674_b300
 PAIR_SOURCES = ["paper_2503_11674_b300/csrc/tdp_pairs.cu", "paper_2503_11674_b300/csrc/tdp_internal.cuh"]
 PROFILED_TRAFFIC = {
     ("1.2M", 16): {
-        "fwd_sweep": {"bytes": 511739904, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
-        "bwd_sweep": {"bytes": 128792320, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
-        "pair_walk": {"bytes": 22054656, "sources": PAIR_SOURCES, "sha256": "a58e4cf53b8e4f91cbefcbff75dc1697e6b57f38c6b27b33b552721c394d7fbf"},
+        "fwd_sweep": {"bytes": 511739904, "sources": SWEEP_SOURCES, "sha256": "b8921e57515016b5f8badf95eb604b68446769a956cc9ad52825b0a4428d7111"},
+        "bwd_sweep": {"bytes": 128792320, "sources": SWEEP_SOURCES, "sha256": "b8921e57515016b5f8badf95eb604b68446769a956cc9ad52825b0a4428d7111"},
+        "pair_walk": {"bytes": 22054656, "sources": PAIR_SOURCES, "sha256": "79052c62d3f43c9ac0b1a3deaf7fe13d9affae0679230929a60ea0962ff4a9b3"},
     },
     ("stress", 32): {
-        "fwd_sweep": {"bytes": 2477957704, "sources": SWEEP_SOURCES, "sha256": "4f44531841833e605b8dc65c00e509f790fbdb59621e284fdccb34b77ca3ec47"},
+        "fwd_sweep": {"bytes": 2477957704, "sources": SWEEP_SOURCES, "sha256": "b8921e57515016b5f8badf95eb604b68446769a956cc9ad52825b0a4428d7111"},
     },
 }
 

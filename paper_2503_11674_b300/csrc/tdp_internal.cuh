@@ -132,10 +132,11 @@ __device__ __forceinline__ fx2 ldg(const fx2 *p) {
     return fx2{v.x, v.y};
 }
 
-// Programmatic dependent launch between the kernels of a sweep: a kernel lets
-// its successor launch as soon as it starts, and the successor reads only
-// static topology until pdl_wait() returns, which happens once every earlier
-// kernel of the stream has finished and its writes are visible.
+// Programmatic dependent launch (launch_pdl): a kernel lets its successor
+// launch as soon as it starts (pdl_trigger), and the successor waits in
+// pdl_wait() until every earlier kernel of the stream has finished and its
+// writes are visible.  The per-level kernels of a sweep read only static
+// topology before the wait.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
@@ -145,8 +146,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // first memory access, for every earlier kernel of the stream to finish.  So
 // a kernel's launch and block dispatch overlap the tail of the one before,
 // and the order of memory accesses is that of plain stream order (no read or
-// write moves ahead of the wait).  Launched without the attribute (after a
-// memset or an event wait, or in the level-graph mode), both are no-ops.
+// write moves ahead of the wait).  A kernel whose predecessor in the stream
+// is not a kernel (a memset, an event wait) starts as in plain stream order,
+// and in a launch without the attribute both calls are no-ops.
 __device__ __forceinline__ void chain_enter() {
     pdl_trigger();
     pdl_wait();
@@ -678,7 +680,7 @@ struct CmpPart {
 // (flags padded to a multiple of 32 bytes); the launch also sets the device
 // words clear32 and clear64 to 0 where given (counters of the kernels after
 // it, so that the stream needs no memset between them).  Launched as a
-// programmatic dependent of the kernel before it (launch_chain).
+// programmatic dependent of the kernel before it (launch_pdl, chain_enter).
 tdp_status compact_flags(tdp_graph *g, const CmpPart &a, const CmpPart *b = nullptr, int32_t *clear32 = nullptr,
                          long long *clear64 = nullptr);
 inline tdp_status compact_u8(tdp_graph *g, const uint8_t *flags, uint8_t val, int n, const int32_t *map,
